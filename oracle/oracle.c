@@ -1,0 +1,238 @@
+/*
+ * FP64 CPU oracle for the PDE dehazing method (arXiv 2506.08793).
+ *
+ * TEST INFRASTRUCTURE ONLY: see oracle.h.  Every loop below follows the
+ * definition it cites term by term; there is no blocking, fusion or
+ * reordering.  Per-pixel loops may run on several OpenMP threads because each
+ * output element is computed on its own; every reduction runs serially in
+ * index order, so results do not depend on the thread count.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+int or_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Half-sample symmetric extension (... c b a | a b c ... | z y x | x y z ...),
+ * the 'reflect' boundary of scipy.ndimage that App. A-B-2 names.  Period 2n. */
+static long reflect(long i, long n) {
+    long p = 2 * n;
+    long m = i % p;
+    if (m < 0) m += p;
+    return m < n ? m : p - 1 - m;
+}
+
+/* ---------------------------------------------------------------- Sec. II-D */
+
+void or_dark_channel(const float *I, int H, int W, int patch, const double *A, double *out) {
+    const int r = patch / 2;
+    const long N = (long)H * W;
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            double best = INFINITY;
+            for (int c = 0; c < 3; ++c) {
+                const double a = A ? A[c] : 1.0;
+                /* inner minimum over the patch Omega(x), clipped to the image */
+                double m = INFINITY;
+                for (int yy = y - r; yy <= y + r; ++yy) {
+                    if (yy < 0 || yy >= H) continue;
+                    for (int xx = x - r; xx <= x + r; ++xx) {
+                        if (xx < 0 || xx >= W) continue;
+                        const double v = (double)I[c * N + (long)yy * W + xx] / a;
+                        if (v < m) m = v;
+                    }
+                }
+                /* outer minimum over the colour channels */
+                if (m < best) best = m;
+            }
+            out[(long)y * W + x] = best;
+        }
+    }
+}
+
+/* ------------------------------------------------- atmospheric light (DCP) */
+
+static const double *g_sort_dc; /* qsort has no context argument */
+
+static int cmp_desc_dc_then_index(const void *pa, const void *pb) {
+    const long a = *(const long *)pa, b = *(const long *)pb;
+    const double da = g_sort_dc[a], db = g_sort_dc[b];
+    if (da > db) return -1;
+    if (da < db) return 1;
+    return (a > b) - (a < b);
+}
+
+int or_atmospheric_light(const float *I, const double *dc, int H, int W, int permille,
+                         double A[3], long *index) {
+    const long N = (long)H * W;
+    long k = (N * (long)permille) / 1000;
+    if (k < 1) k = 1;
+    if (k > N) k = N;
+    long *order = (long *)malloc(sizeof(long) * (size_t)N);
+    for (long i = 0; i < N; ++i) order[i] = i;
+    g_sort_dc = dc;
+    qsort(order, (size_t)N, sizeof(long), cmp_desc_dc_then_index);
+    /* among the k haziest pixels, the brightest; ties go to the lower index */
+    long best = -1;
+    double best_sum = -INFINITY;
+    for (long q = 0; q < k; ++q) {
+        const long i = order[q];
+        const double s = ((double)I[i] + (double)I[N + i]) + (double)I[2 * N + i];
+        if (best < 0 || s > best_sum || (s == best_sum && i < best)) {
+            best = i;
+            best_sum = s;
+        }
+    }
+    free(order);
+    int clamped = 0;
+    for (int c = 0; c < 3; ++c) {
+        A[c] = (double)I[c * N + best];
+        if (!(A[c] > 0.0)) {
+            A[c] = 1e-6;
+            clamped = 1;
+        }
+    }
+    if (index) *index = best;
+    return clamped;
+}
+
+/* ------------------------------------------------- Sec. II-D and Sec. II-A */
+
+void or_transmission(const float *I, const double A[3], const double *td, int H, int W,
+                     const or_params *p, double *t, double *lam, double *Phi) {
+    const long N = (long)H * W;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < N; ++i) {
+        const double ti = 1.0 - p->omega * td[i];
+        t[i] = ti;
+        lam[i] = p->lambda0 * exp(-p->beta * (1.0 - ti));
+        const double den = ti > p->t0 ? ti : p->t0;
+        for (int c = 0; c < 3; ++c)
+            Phi[c * N + i] = ((double)I[c * N + i] - A[c] * (1.0 - ti)) / den;
+    }
+}
+
+/* ------------------------------------------------------------- App. A-B-2 */
+
+void or_gauss_weights(double sigma, int radius, double *w) {
+    double s = 0.0;
+    for (int k = -radius; k <= radius; ++k) {
+        w[k + radius] = exp(-(double)(k * k) / (2.0 * sigma * sigma));
+        s += w[k + radius];
+    }
+    for (int k = 0; k <= 2 * radius; ++k) w[k] /= s;
+}
+
+void or_gauss(const double *u, int H, int W, double sigma, int radius, double *out) {
+    double w[64];
+    or_gauss_weights(sigma, radius, w);
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            /* G(u)(x) = sum_y K(x,y) u(y) with the separable normalised kernel */
+            double g = 0.0;
+            for (int b = -radius; b <= radius; ++b) {
+                const long yy = reflect(y + b, H);
+                for (int a = -radius; a <= radius; ++a) {
+                    const long xx = reflect(x + a, W);
+                    g += w[b + radius] * w[a + radius] * u[yy * W + xx];
+                }
+            }
+            out[(long)y * W + x] = g;
+        }
+    }
+}
+
+/* ------------------------------------------------------------- App. A-B-1 */
+
+/* u at column i, row j with the reflecting boundary */
+static double U(const double *u, int H, int W, long i, long j) {
+    return u[reflect(j, H) * W + reflect(i, W)];
+}
+
+/* D u_x on the x-face (i+1/2, j): forward difference in x, central difference
+ * in y at cell (i, j), D = (|grad u| + eps)^-1, Delta x = Delta y = 1. */
+static double flux_x(const double *u, int H, int W, long i, long j, double eps) {
+    const double ux = U(u, H, W, i + 1, j) - U(u, H, W, i, j);
+    const double uy = (U(u, H, W, i, j + 1) - U(u, H, W, i, j - 1)) / 2.0;
+    const double D = 1.0 / (sqrt(ux * ux + uy * uy) + eps);
+    return D * ux;
+}
+
+/* D u_y on the y-face (i, j+1/2): the same with the roles of x and y swapped. */
+static double flux_y(const double *u, int H, int W, long i, long j, double eps) {
+    const double uy = U(u, H, W, i, j + 1) - U(u, H, W, i, j);
+    const double ux = (U(u, H, W, i + 1, j) - U(u, H, W, i - 1, j)) / 2.0;
+    const double D = 1.0 / (sqrt(ux * ux + uy * uy) + eps);
+    return D * uy;
+}
+
+void or_div(const double *u, int H, int W, double eps, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < H; ++j) {
+        for (int i = 0; i < W; ++i) {
+            const double dx = flux_x(u, H, W, i, j, eps) - flux_x(u, H, W, i - 1, j, eps);
+            const double dy = flux_y(u, H, W, i, j, eps) - flux_y(u, H, W, i, j - 1, eps);
+            out[(long)j * W + i] = dx + dy;
+        }
+    }
+}
+
+void or_F(const double *u, const double *Phi, const double *lam, int H, int W,
+          const or_params *p, double *F) {
+    const long N = (long)H * W;
+    double *dv = (double *)malloc(sizeof(double) * (size_t)N);
+    double *g = (double *)malloc(sizeof(double) * (size_t)N);
+    for (int c = 0; c < 3; ++c) {
+        or_div(u + c * N, H, W, p->eps, dv);
+        or_gauss(u + c * N, H, W, p->sigma, p->radius, g);
+        for (long i = 0; i < N; ++i)
+            F[c * N + i] = dv[i] - lam[i] * g[i] + Phi[c * N + i];
+    }
+    free(dv);
+    free(g);
+}
+
+/* --------------------------------------------------------------- App. A-A */
+
+int or_solve(double *u, const double *Phi, const double *lam, int H, int W,
+             const or_params *p, int max_iter, double tol, double *rho) {
+    const long N = (long)H * W;
+    double *F = (double *)malloc(sizeof(double) * (size_t)(3 * N));
+    double phin[3];
+    for (int c = 0; c < 3; ++c) {
+        double s = 0.0;
+        for (long i = 0; i < N; ++i) s += Phi[c * N + i] * Phi[c * N + i];
+        phin[c] = sqrt(s);
+    }
+    int n = 0;
+    for (;; ++n) {
+        or_F(u, Phi, lam, H, W, p, F);
+        double worst = 0.0;
+        int finite = 1;
+        for (int c = 0; c < 3; ++c) {
+            double s = 0.0;
+            for (long i = 0; i < N; ++i) s += F[c * N + i] * F[c * N + i];
+            const double r = phin[c] > 0.0 ? sqrt(s) / phin[c] : sqrt(s);
+            rho[3 * n + c] = r;
+            if (!isfinite(r)) finite = 0; /* a non-finite residual never converges */
+            else if (r > worst) worst = r;
+        }
+        if ((finite && worst <= tol) || n == max_iter) break;
+        for (long i = 0; i < 3 * N; ++i) u[i] = u[i] + p->tau * F[i];
+    }
+    free(F);
+    return n;
+}
