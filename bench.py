@@ -1,0 +1,302 @@
+"""Benchmark: the whole dehazing method on synthetic hazy scenes at 1920x1080
+and 3840x2160, each solved to residual 1e-4 (stable preset), on N GPUs.
+
+One step = dehaze both images (dark channel, atmospheric light, t, lambda,
+Phi, fixed-point loop to tolerance, J = clamp(u)).  value = MPix*iterations
+per second over all ranks (pixels x fixed-point iterations / max-over-ranks
+time).  Each rank solves its own copy of the workload (independent images:
+weak scaling, no collective on the data path).
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload (the method has no other implementation to compare with).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = [(1080, 1920, 2000), (2160, 3840, 2001)]  # (H, W, seed)
+METRIC = "MPix*iter/s to residual 1e-4 (1080p + 4K scenes, full method)"
+UNIT = "MPix*iter/s"
+BYTES_PER_PX_ITER = 40  # read u 12, Phi 12, lambda 4, write u 12 (float32, one iteration)
+
+
+def env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def sweep_traffic():
+    """dram bytes per px*iter of the sweep from the committed ncu summary, or
+    None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "k_sweep_ncu.txt")
+    src = os.path.join(ROOT, "paper_2506_08793_gb300", "csrc", "solver.cu")
+    try:
+        txt = open(path).read()
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        fields = dict(l.split("=", 1) for l in txt.splitlines() if "=" in l and not l.startswith("#"))
+        if fields.get("solver_cu_sha256_16", "").strip() != h:
+            return None
+        return float(fields["dram_bytes_per_px_iter"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.p = None
+        self.path = os.path.join("/tmp", f"dh_clocks_{os.getpid()}.csv")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) != 7:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[3:]))
+            except ValueError:
+                pass
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": reasons}
+
+
+def cpu_sample(I, H, W, iters, n_gpu_iters):
+    """Oracle: front end once and `iters` fixed-point iterations of one image;
+    returns (seconds extrapolated to n_gpu_iters iterations, threads)."""
+    import oracle
+
+    op = oracle.params(**oracle.STABLE)
+    t0 = time.perf_counter()
+    dc = oracle.dark_channel(I, op.patch, None)
+    A, _, _ = oracle.atmospheric_light(I, dc, op.topk_permille)
+    td = oracle.dark_channel(I, op.patch, A)
+    _, lam, Phi = oracle.transmission(I, A, td, op)
+    t1 = time.perf_counter()
+    oracle.solve(Phi, Phi, lam, op, iters - 1, 0.0)  # iters evaluations of F, iters-1 updates
+    t2 = time.perf_counter()
+    per_iter = (t2 - t1) / iters
+    return (t1 - t0) + per_iter * n_gpu_iters, oracle.num_threads(), (t1 - t0), per_iter
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    from paper_2506_08793_gb300 import scenes
+
+    H, W, seed = WORKLOAD[0]
+    I = scenes.hazy_scene(seed, H, W)["I"]
+    op = oracle.params(**oracle.STABLE)
+    dc = oracle.dark_channel(I, op.patch, None)
+    A, _, _ = oracle.atmospheric_light(I, dc, op.topk_permille)
+    td = oracle.dark_channel(I, op.patch, A)
+    _, lam, Phi = oracle.transmission(I, A, td, op)
+    iters = 8
+    u = Phi.copy()
+    for _ in range(args.warmup):
+        u, _, _ = oracle.solve(u, Phi, lam, op, iters, 0.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u, _, _ = oracle.solve(u, Phi, lam, op, iters, 0.0)
+    dt = time.perf_counter() - t0
+    units = H * W * (iters + 1) * args.steps / 1e6  # F evaluated iters+1 times per call
+    value = units / dt
+    sample = (f"each step: {iters + 1} FP64 oracle evaluations of F (+{iters} updates) on the "
+              f"{H}x{W} scene (seed {seed}); front end excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"fixed point on a {H}x{W} synthetic hazy scene", "preset": "stable"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=12)
+    args = ap.parse_args()
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_08793_gb300 import _native as N
+    from paper_2506_08793_gb300 import api, scenes
+
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    N.lib()
+    p = api.params("stable")
+    imgs = []
+    for H, W, seed in WORKLOAD:
+        I = scenes.hazy_scene(seed, H, W)["I"]
+        Ih = torch.from_numpy(I).pin_memory()
+        imgs.append(dict(H=H, W=W, seed=seed, Inp=I, Ih=Ih, Id=Ih.cuda(), dz=api.Dehazer(H, W, p),
+                         Jh=torch.empty((3, H, W), dtype=torch.float32).pin_memory()))
+    stream = torch.cuda.current_stream()
+
+    def step(e2e=False):
+        out = []
+        for im in imgs:
+            if e2e:
+                im["Id"].copy_(im["Ih"], non_blocking=True)
+            rep = im["dz"](im["Id"], report=True)
+            if rep.status != N.DH_OK:
+                raise RuntimeError(f"dh_dehaze status {rep.status}: {N.dh_strerror(rep.status)}")
+            if e2e:
+                im["Jh"].copy_(im["dz"].J, non_blocking=True)
+            out.append(rep)
+        return out
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(e2e):
+        for _ in range(args.warmup):
+            step(e2e)
+        barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(torch.cuda.current_device()) if not e2e else None
+        ev0.record(stream)
+        reps = []
+        for _ in range(args.steps):
+            reps.append(step(e2e))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        barrier()
+        ms = ev0.elapsed_time(ev1)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, reps, clocks
+
+    ms, reps, clocks = timed(False)
+    units = sum(im["H"] * im["W"] * r.n_iter for rs in reps for im, r in zip(imgs, rs)) / 1e6
+    value = units * world / (ms / 1e3)
+    # sweep kernel: one launch = one iteration over all 3 channels of one image
+    loop_ms = sum(r.ms_loop for rs in reps for r in rs)
+    sweep_px_iter = sum(im["H"] * im["W"] * (r.n_iter + 1) for rs in reps for im, r in zip(imgs, rs))
+    sweep_launches = sum(r.n_iter + 1 for rs in reps for r in rs)
+    achieved = BYTES_PER_PX_ITER * sweep_px_iter / (loop_ms / 1e3) / 1e9
+    peaks = measured_peaks()
+    if peaks:
+        peak, peak_src = peaks["hbm_gbs"], "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    tr = sweep_traffic()
+    per_img = []
+    for k, im in enumerate(imgs):
+        rs = [r[k] for r in reps]
+        per_img.append({"size": f"{im['W']}x{im['H']}", "n_iter": rs[0].n_iter,
+                        "ms": statistics.median(r.ms for r in rs),
+                        "loop_ms": statistics.median(r.ms_loop for r in rs),
+                        "images_per_s": 1e3 / statistics.median(r.ms for r in rs),
+                        "sweep_us_per_launch": 1e3 * statistics.median(r.ms_loop for r in rs) / (rs[0].n_iter + 1),
+                        "rho": max(rs[0].rho), "A_index": rs[0].a_index})
+    e2e_ms, e2e_reps, _ = timed(True)
+    e2e_units = sum(im["H"] * im["W"] * r.n_iter for rs in e2e_reps for im, r in zip(imgs, rs)) / 1e6
+    h2d = sum(im["Ih"].numel() * 4 for im in imgs)
+    d2h = sum(im["Jh"].numel() * 4 for im in imgs)
+    launches = sum(r.launches for rs in reps for r in rs)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "1920x1080 (seed 2000) + 3840x2160 (seed 2001) synthetic hazy scenes, "
+                               "stable preset (eps = 1), to residual 1e-4",
+                   "images_per_step": len(imgs) * world, "l2": "inputs larger than L2 (about 0.7 GB touched per step)",
+                   "parallelism": f"replicas x{world}", "per_image": per_img,
+                   "images_per_s_1080p": per_img[0]["images_per_s"]},
+        "roofline": {"kernel": "k_sweep", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None if tr is None else tr * sweep_px_iter / sweep_launches,
+                     "algorithmic_bytes_per_launch": BYTES_PER_PX_ITER * sweep_px_iter / sweep_launches,
+                     "us_per_launch": 1e3 * loop_ms / sweep_launches},
+        "e2e": {"value": e2e_units * world / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        im = imgs[0]
+        secs, cores, fe, per_iter = cpu_sample(im["Inp"], im["H"], im["W"], args.cpu_iters, per_img[0]["n_iter"])
+        line["cpu_baseline"] = {
+            "value": im["H"] * im["W"] * per_img[0]["n_iter"] / 1e6 / secs, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": (f"1920x1080 scene: FP64 oracle front end ({fe:.1f} s) + {args.cpu_iters} fixed-point "
+                       f"iterations ({per_iter:.2f} s each), extrapolated to the GPU's {per_img[0]['n_iter']} "
+                       "iterations")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,166 @@
+/*
+ * dehaze.h -- C ABI of the GB300 (sm_103a) CUDA library for the PDE-based
+ * dehazing method of Hu, Wang, Gao, Wang and Zheng, "A PDE-Based Image
+ * Dehazing Method via Atmospheric Scattering Theory" (arXiv 2506.08793).
+ *
+ * The method (Sec. II and App. A):
+ *   dark channel      t_d(x) = min_c min_{y in Omega(x)} I^c(y)/A^c      (Sec. II-D)
+ *   transmission      t = 1 - omega*t_d, lambda(t) = lambda0*exp(-beta(1-t)) (Sec. II-D)
+ *   data term         Phi^c = (I^c - A^c (1-t)) / max(t, t0)             (Sec. II-A)
+ *   PDE, per channel  -div(D(grad u) grad u) + lambda(t) G(u) = Phi      (Sec. II-A, eq. main_pde)
+ *                     D = (|grad u| + eps)^-1 (Sec. II-B), G = 5x5 Gaussian, sigma 2 (Sec. II-C)
+ *   solver            u <- u + tau [div(D_n grad u) - lambda G(u) + Phi] (App. A-A)
+ *                     flux-form stencil of App. A-B-1, separable Gaussian of App. A-B-2
+ * The atmospheric light A is not defined by the paper; the library uses the
+ * dark-channel-prior rule of He et al. that the paper cites: the brightest
+ * (largest R+G+B) of the 0.1 % pixels with the largest dark channel.
+ *
+ * Conventions for every call below
+ *   - Images are planar float32, row-major: channel c, row y, column x at
+ *     [(c*H + y)*W + x].  Maps (t, lambda, dark channel) are HxW.
+ *   - Every array argument is a DEVICE pointer owned by the caller, unless
+ *     marked "host".  The library allocates no device memory: scratch space
+ *     is the caller's workspace (size from dh_workspace_bytes, 256-byte
+ *     aligned).  Pointers passed in one call must not overlap unless stated.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     queued asynchronously; a call with a non-NULL host `report` waits for
+ *     the stream and fills the report.
+ *   - Return value: DH_OK (0), a positive warning (outputs valid) or a
+ *     negative error (outputs unspecified).  Errors found on the host
+ *     (shapes, parameters, workspace) are returned before any work is queued.
+ *   - 1 <= H, W <= 32768 and H*W <= 2^28.  There is no CPU fallback: on a
+ *     machine without a usable GB300 every compute call returns DH_ECUDA.
+ */
+#ifndef DEHAZE_H
+#define DEHAZE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DH_VERSION 1
+
+/* status codes */
+#define DH_OK 0
+#define DH_WDEGENERATE 1  /* warning: some A^c <= 0 was clamped to 1e-6 */
+#define DH_WNOCONV 2      /* warning: max_iter reached with residual above tol */
+#define DH_EINVAL (-1)    /* bad shape, pointer, alignment or parameter */
+#define DH_ENONFINITE (-2)/* a non-finite residual appeared; iteration stopped */
+#define DH_EWORKSPACE (-3)/* workspace missing, too small or misaligned */
+#define DH_ECUDA (-4)     /* a CUDA runtime call failed (no GPU, launch error ...) */
+#define DH_ETIMEOUT (-5)  /* a bounded device-side wait ran out */
+
+/* presets for dh_params_default */
+#define DH_PRESET_PAPER 0  /* the paper's constants (Sec. IV-B), eps = 1e-3 */
+#define DH_PRESET_STABLE 1 /* the same with eps = 1.0, which satisfies App. A-A's step bound */
+
+/* iterate storage (u and its halos); arithmetic is always float32 */
+#define DH_STORE_F32 0
+#define DH_STORE_BF16 1
+#define DH_STORE_F16 2
+
+/* ablation switches (Sec. IV-E, Table II), OR-ed into dh_params.variant */
+#define DH_VAR_NO_ADAPTIVE 1 /* lambda(t) == lambda0 */
+#define DH_VAR_NO_EDGE 2     /* D == 1 (linear diffusion) */
+#define DH_VAR_NO_NONLOCAL 4 /* lambda == 0 */
+
+typedef struct dh_params {
+    int patch;          /* dark-channel window side, odd, 1..31 (Sec. II-D: 15) */
+    int topk_permille;  /* A from the top max(1, H*W*p/1000) dark-channel pixels (1) */
+    float omega;        /* Sec. II-D: 0.95 */
+    float t0;           /* floor of t in Phi (Sec. II-A; no value given: 0.1) */
+    float lambda0;      /* Sec. II-D: 0.5 */
+    float beta;         /* Sec. II-D: 3.0 */
+    float eps;          /* Sec. II-B: 1e-3 (paper) / 1.0 (stable) */
+    float sigma;        /* Sec. II-C: 2.0 */
+    int radius;         /* Gaussian half-width; only 2 (5x5, App. A-B-2) is built */
+    float tau;          /* App. A-A: 0.2 */
+    float tol;          /* stop when max_c ||F^c(u^n)|| / ||Phi^c|| <= tol (1e-4) */
+    int max_iter;       /* at most this many updates (default 5000) */
+    int tb_depth;       /* iterations fused per sweep launch, 0 = library choice */
+    int storage;        /* DH_STORE_* */
+    int variant;        /* DH_VAR_* bits, 0 = the full method */
+    int use_graph;      /* 1: iteration loop in a CUDA graph with a device-side
+                           while condition (default); 0: host-queued launches */
+} dh_params;
+
+typedef struct dh_report {
+    int status;         /* as returned */
+    int n_iter;         /* updates applied: the returned u is u^n_iter */
+    float rho[3];       /* ||F^c(u^n_iter)|| / ||Phi^c|| (||F^c|| if ||Phi^c|| = 0) */
+    float A[3];         /* atmospheric light (dh_dehaze only) */
+    long long a_index;  /* row-major index of the pixel A was taken from, or -1 */
+    float ms;           /* device time of the call (CUDA events on `stream`) */
+    float ms_loop;      /* device time of the fixed-point loop alone */
+    int launches;       /* kernels the call ran (each loop iteration counts one) */
+} dh_report;
+
+/* Fill *p with a preset.  Returns DH_OK or DH_EINVAL (NULL p, unknown preset). */
+int dh_params_default(dh_params *p, int preset);
+
+/* Static description of a status code (never NULL). */
+const char *dh_strerror(int status);
+
+/* DH_VERSION of the built library. */
+int dh_version(void);
+
+/* Bytes of device workspace dh_dehaze / dh_fixed_point / dh_atmospheric_light
+ * need for an HxW image under *p (p may be NULL for the defaults); 0 when the
+ * shape or parameters are invalid. */
+size_t dh_workspace_bytes(int H, int W, const dh_params *p);
+
+/* Sec. II-D dark channel:
+ *   out(x) = min_c min_{|dy|,|dx| <= patch/2} I^c(x+(dx,dy)) / A^c,
+ * the window clipped at the image border.  A = NULL means A = (1,1,1) (the
+ * un-normalised dark channel that locates the atmospheric light); otherwise
+ * A is a device float[3] and each quotient is the IEEE float32 quotient.
+ * I: 3xHxW; out: HxW.  Bit-exact (no rounding beyond the quotient). */
+int dh_dark_channel(const float *I, int H, int W, int patch, const float *A, float *out,
+                    void *stream);
+
+/* Atmospheric light by the DCP rule (not defined by the paper; He et al.):
+ * k = max(1, H*W*topk_permille/1000) pixels with the largest dc (ties: lower
+ * row-major index), then the one with the largest
+ * ((double)I^R + (double)I^G) + (double)I^B (ties: lower index).
+ * I: 3xHxW; dc: HxW (from dh_dark_channel with A = NULL); A_out: device
+ * float[3] receives I at that pixel, each A^c <= 0 replaced by 1e-6;
+ * index_out: device long long[1] (may be NULL).  Needs workspace.  Returns
+ * DH_WDEGENERATE (with report) when a component was clamped. */
+int dh_atmospheric_light(const float *I, const float *dc, int H, int W, int topk_permille,
+                         float *A_out, long long *index_out, void *workspace,
+                         size_t workspace_bytes, void *stream, dh_report *report);
+
+/* Sec. II-D and II-A: from I and A (device float[3]) computes
+ *   t_d = dark channel of I/A (as dh_dark_channel), t = 1 - omega*t_d,
+ *   lambda = lambda0*exp(-beta(1-t)), Phi^c = (I^c - A^c(1-t))/max(t, t0).
+ * t, lam: HxW; Phi: 3xHxW; td may be NULL. */
+int dh_transmission(const float *I, const float *A, int H, int W, const dh_params *p,
+                    float *td, float *t, float *lam, float *Phi, void *stream);
+
+/* App. A-A fixed-point iteration, per channel, from u (in: u^0, out: u^n):
+ *   F(u) = div(D(grad u) grad u) - lambda G(u) + Phi   (App. A-B-1, A-B-2)
+ *   for n = 0, 1, ...: rho_n^c = ||F^c(u^n)|| / ||Phi^c||;
+ *   stop at the first n with max_c rho_n^c <= p->tol or n == p->max_iter,
+ *   else u^{n+1} = u^n + tau F(u^n).
+ * Boundary: half-sample symmetric reflection for both the flux stencil (zero
+ * flux across the border) and the Gaussian.
+ * u, Phi: 3xHxW; lam: HxW; rho_hist: device float[3*(max_iter+1)] or NULL,
+ * receives rho_n for every evaluated n.  Returns DH_WNOCONV when max_iter was
+ * reached (only known with a report), DH_ENONFINITE on a non-finite residual. */
+int dh_fixed_point(float *u, const float *Phi, const float *lam, int H, int W,
+                   const dh_params *p, float *rho_hist, void *workspace, size_t workspace_bytes,
+                   void *stream, dh_report *report);
+
+/* The whole method on one image: dark channel -> A -> t, lambda, Phi ->
+ * fixed point from u0 (NULL: u0 = Phi) -> J = clamp(u, 0, 1).
+ * I: 3xHxW; u0: 3xHxW or NULL; outputs J, u: 3xHxW; t: HxW; A: float[3]. */
+int dh_dehaze(const float *I, int H, int W, const dh_params *p, const float *u0, float *J,
+              float *u, float *t, float *A, void *workspace, size_t workspace_bytes,
+              void *stream, dh_report *report);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

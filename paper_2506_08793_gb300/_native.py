@@ -1,0 +1,183 @@
+"""ctypes binding of libdehaze.so, one Python function per C entry point of
+include/dehaze.h, with the same names.  Argument marshalling only: every step
+of the method runs in the library's CUDA kernels.  Array arguments are device
+pointers, given as torch tensors (their data_ptr()) or as integers.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "libdehaze.so")
+
+DH_OK = 0
+DH_WDEGENERATE = 1
+DH_WNOCONV = 2
+DH_EINVAL = -1
+DH_ENONFINITE = -2
+DH_EWORKSPACE = -3
+DH_ECUDA = -4
+DH_ETIMEOUT = -5
+DH_PRESET_PAPER = 0
+DH_PRESET_STABLE = 1
+DH_STORE_F32, DH_STORE_BF16, DH_STORE_F16 = 0, 1, 2
+DH_VAR_NO_ADAPTIVE, DH_VAR_NO_EDGE, DH_VAR_NO_NONLOCAL = 1, 2, 4
+
+# Every symbol include/dehaze.h declares.
+EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes",
+           "dh_dark_channel", "dh_atmospheric_light", "dh_transmission", "dh_fixed_point",
+           "dh_dehaze")
+
+
+class DhParams(ctypes.Structure):
+    _fields_ = [
+        ("patch", ctypes.c_int),
+        ("topk_permille", ctypes.c_int),
+        ("omega", ctypes.c_float),
+        ("t0", ctypes.c_float),
+        ("lambda0", ctypes.c_float),
+        ("beta", ctypes.c_float),
+        ("eps", ctypes.c_float),
+        ("sigma", ctypes.c_float),
+        ("radius", ctypes.c_int),
+        ("tau", ctypes.c_float),
+        ("tol", ctypes.c_float),
+        ("max_iter", ctypes.c_int),
+        ("tb_depth", ctypes.c_int),
+        ("storage", ctypes.c_int),
+        ("variant", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+    ]
+
+    def replace(self, **kw) -> "DhParams":
+        q = DhParams()
+        ctypes.memmove(ctypes.byref(q), ctypes.byref(self), ctypes.sizeof(self))
+        for k, v in kw.items():
+            setattr(q, k, v)
+        return q
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class DhReport(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int),
+        ("n_iter", ctypes.c_int),
+        ("rho", ctypes.c_float * 3),
+        ("A", ctypes.c_float * 3),
+        ("a_index", ctypes.c_longlong),
+        ("ms", ctypes.c_float),
+        ("ms_loop", ctypes.c_float),
+        ("launches", ctypes.c_int),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib(build_if_missing: bool = True):
+    """Loads libdehaze.so, building it first when it is missing or stale.
+    Raises when it cannot be built: there is no CPU fallback."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _build
+
+        if build_if_missing:
+            _build.build()
+        if not os.path.exists(SO):
+            raise RuntimeError(f"CUDA library not built: {SO} is missing")
+        L = ctypes.CDLL(SO)
+        P, I, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        PP = ctypes.POINTER(DhParams)
+        PR = ctypes.POINTER(DhReport)
+        sig = {
+            "dh_params_default": ([PP, I], I),
+            "dh_strerror": ([I], ctypes.c_char_p),
+            "dh_version": ([], I),
+            "dh_workspace_bytes": ([I, I, PP], S),
+            "dh_dark_channel": ([P, I, I, I, P, P, P], I),
+            "dh_atmospheric_light": ([P, P, I, I, I, P, P, P, S, P, PR], I),
+            "dh_transmission": ([P, P, I, I, PP, P, P, P, P, P], I),
+            "dh_fixed_point": ([P, P, P, I, I, PP, P, P, S, P, PR], I),
+            "dh_dehaze": ([P, I, I, PP, P, P, P, P, P, P, S, P, PR], I),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+        return L
+
+
+def _p(x):
+    """Device pointer of a tensor / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ref(x):
+    return None if x is None else ctypes.byref(x)
+
+
+def dh_params_default(preset: int = DH_PRESET_PAPER) -> DhParams:
+    p = DhParams()
+    rc = lib().dh_params_default(ctypes.byref(p), preset)
+    if rc != DH_OK:
+        raise ValueError(dh_strerror(rc))
+    return p
+
+
+def dh_strerror(status: int) -> str:
+    return lib().dh_strerror(status).decode()
+
+
+def dh_version() -> int:
+    return lib().dh_version()
+
+
+def dh_workspace_bytes(H: int, W: int, p: DhParams | None = None) -> int:
+    return lib().dh_workspace_bytes(H, W, _ref(p))
+
+
+def dh_dark_channel(I, H, W, patch, A, out, stream=None) -> int:
+    return lib().dh_dark_channel(_p(I), H, W, patch, _p(A), _p(out), _stream(stream))
+
+
+def dh_atmospheric_light(I, dc, H, W, topk_permille, A_out, index_out, workspace, workspace_bytes,
+                         stream=None, report: DhReport | None = None) -> int:
+    return lib().dh_atmospheric_light(_p(I), _p(dc), H, W, topk_permille, _p(A_out), _p(index_out),
+                                      _p(workspace), workspace_bytes, _stream(stream), _ref(report))
+
+
+def dh_transmission(I, A, H, W, p: DhParams, td, t, lam, Phi, stream=None) -> int:
+    return lib().dh_transmission(_p(I), _p(A), H, W, ctypes.byref(p), _p(td), _p(t), _p(lam), _p(Phi),
+                                 _stream(stream))
+
+
+def dh_fixed_point(u, Phi, lam, H, W, p: DhParams, rho_hist, workspace, workspace_bytes, stream=None,
+                   report: DhReport | None = None) -> int:
+    return lib().dh_fixed_point(_p(u), _p(Phi), _p(lam), H, W, ctypes.byref(p), _p(rho_hist),
+                                _p(workspace), workspace_bytes, _stream(stream), _ref(report))
+
+
+def dh_dehaze(I, H, W, p: DhParams, u0, J, u, t, A, workspace, workspace_bytes, stream=None,
+              report: DhReport | None = None) -> int:
+    return lib().dh_dehaze(_p(I), H, W, ctypes.byref(p), _p(u0), _p(J), _p(u), _p(t), _p(A),
+                           _p(workspace), workspace_bytes, _stream(stream), _ref(report))

@@ -1,0 +1,126 @@
+"""torch-tensor front end of the CUDA library (include/dehaze.h).
+
+torch provides device memory and streams only; every step runs in the
+library's kernels.  All functions raise on a library error and never fall back
+to another implementation.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _native as N
+from ._native import DhParams, DhReport
+
+
+class DehazeError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {N.dh_strerror(status)} (status {status})")
+        self.status = status
+
+
+def _check(rc: int, where: str, ok=(N.DH_OK, N.DH_WDEGENERATE, N.DH_WNOCONV)) -> int:
+    if rc not in ok:
+        raise DehazeError(rc, where)
+    return rc
+
+
+def params(preset: str = "stable", **kw) -> DhParams:
+    """Library parameters: preset 'paper' (the paper's constants) or 'stable'
+    (eps = 1.0), then field overrides."""
+    p = N.dh_params_default(N.DH_PRESET_PAPER if preset == "paper" else N.DH_PRESET_STABLE)
+    return p.replace(**kw) if kw else p
+
+
+def _img(I: torch.Tensor) -> tuple[int, int]:
+    if I.dim() != 3 or I.shape[0] != 3 or I.dtype != torch.float32 or not I.is_cuda or not I.is_contiguous():
+        raise ValueError("expected a contiguous float32 CUDA tensor of shape (3, H, W)")
+    return int(I.shape[1]), int(I.shape[2])
+
+
+def _stream(stream):
+    return torch.cuda.current_stream() if stream is None else stream
+
+
+def workspace(H: int, W: int, p: DhParams, device) -> torch.Tensor:
+    nb = N.dh_workspace_bytes(H, W, p)
+    if nb == 0:
+        raise ValueError("invalid shape or parameters")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
+def dark_channel(I: torch.Tensor, patch: int = 15, A: torch.Tensor | None = None, stream=None):
+    H, W = _img(I)
+    out = torch.empty((H, W), dtype=torch.float32, device=I.device)
+    _check(N.dh_dark_channel(I, H, W, patch, A, out, _stream(stream)), "dh_dark_channel")
+    return out
+
+
+def atmospheric_light(I: torch.Tensor, dc: torch.Tensor, topk_permille: int = 1, stream=None):
+    """Returns (A float32[3] on device, index int64[1] on device, report)."""
+    H, W = _img(I)
+    p = params("paper")
+    ws = workspace(H, W, p, I.device)
+    A = torch.empty(3, dtype=torch.float32, device=I.device)
+    idx = torch.empty(1, dtype=torch.int64, device=I.device)
+    rep = DhReport()
+    _check(N.dh_atmospheric_light(I, dc, H, W, topk_permille, A, idx, ws, ws.numel(), _stream(stream), rep),
+           "dh_atmospheric_light")
+    return A, idx, rep
+
+
+def transmission(I: torch.Tensor, A: torch.Tensor, p: DhParams | None = None, stream=None):
+    """Returns (td, t, lambda, Phi)."""
+    H, W = _img(I)
+    p = p or params()
+    td = torch.empty((H, W), dtype=torch.float32, device=I.device)
+    t = torch.empty_like(td)
+    lam = torch.empty_like(td)
+    Phi = torch.empty_like(I)
+    _check(N.dh_transmission(I, A, H, W, p, td, t, lam, Phi, _stream(stream)), "dh_transmission")
+    return td, t, lam, Phi
+
+
+def fixed_point(u: torch.Tensor, Phi: torch.Tensor, lam: torch.Tensor, p: DhParams | None = None,
+                history: bool = False, stream=None):
+    """Iterates u in place from u^0; returns (report, rho_hist or None)."""
+    H, W = _img(u)
+    p = p or params()
+    ws = workspace(H, W, p, u.device)
+    hist = torch.full((p.max_iter + 1, 3), float("nan"), device=u.device) if history else None
+    rep = DhReport()
+    _check(N.dh_fixed_point(u, Phi, lam, H, W, p, hist, ws, ws.numel(), _stream(stream), rep),
+           "dh_fixed_point")
+    return rep, hist
+
+
+class Dehazer:
+    """The whole method for images of one shape, with the workspace and the
+    outputs kept resident so that repeated calls reuse the cached loop graph."""
+
+    def __init__(self, H: int, W: int, p: DhParams | None = None, device="cuda"):
+        self.H, self.W = H, W
+        self.p = p or params()
+        self.device = torch.device(device)
+        self.ws = workspace(H, W, self.p, self.device)
+        self.J = torch.empty((3, H, W), dtype=torch.float32, device=self.device)
+        self.u = torch.empty_like(self.J)
+        self.t = torch.empty((H, W), dtype=torch.float32, device=self.device)
+        self.A = torch.empty(3, dtype=torch.float32, device=self.device)
+
+    def __call__(self, I: torch.Tensor, u0: torch.Tensor | None = None, report: bool = True, stream=None):
+        H, W = _img(I)
+        if (H, W) != (self.H, self.W):
+            raise ValueError("image shape differs from the Dehazer's")
+        rep = DhReport() if report else None
+        rc = N.dh_dehaze(I, H, W, self.p, u0, self.J, self.u, self.t, self.A, self.ws, self.ws.numel(),
+                         _stream(stream), rep)
+        _check(rc, "dh_dehaze")
+        return rep
+
+
+def dehaze(I: torch.Tensor, p: DhParams | None = None, u0: torch.Tensor | None = None):
+    """One image: returns dict(J, u, t, A, report)."""
+    H, W = _img(I)
+    d = Dehazer(H, W, p, I.device)
+    rep = d(I, u0)
+    return dict(J=d.J, u=d.u, t=d.t, A=d.A, report=rep)

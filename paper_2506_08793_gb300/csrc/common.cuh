@@ -1,0 +1,152 @@
+// Shared host/device helpers of the GB300 dehazing library: workspace layout,
+// solver state, reflection, compensated sums and error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dehaze.h"
+
+namespace dh {
+
+constexpr int kMaxDim = 32768;
+constexpr long long kMaxPixels = 1LL << 28;
+constexpr size_t kAlign = 256;
+
+// ---------------------------------------------------------------- sweep tiling
+// One CTA owns a TW x TH tile of one channel.  Each thread owns 4 adjacent
+// columns and walks R rows; a warp covers the 128 columns of the tile.
+constexpr int kTW = 128;
+
+// ---------------------------------------------------------------- device state
+// Iteration state of one image, in the workspace.
+struct SolveState {
+    unsigned arrive;   // CTAs of the current sweep launch that have finished
+    int n;             // index of the current iterate u^n
+    int cur;           // buffer (0 = caller's u, 1 = workspace) holding u^n
+    int done;          // 1 once the loop has stopped
+    int status;        // DH_OK / DH_WNOCONV / DH_ENONFINITE
+    int n_final;       // n of the returned iterate
+    float rho[3];      // residual of u^n_final
+    float phin2[3];    // ||Phi^c||^2
+    unsigned sel_arrive;
+    int pad[3];
+};
+
+// Everything the loop kernels need; written to the workspace by one tiny
+// kernel per call so that a cached CUDA graph can be relaunched unchanged.
+struct SolveDesc {
+    float *u[2];
+    const float *phi;
+    const float *lam;
+    float *rho_hist;     // [3*(max_iter+1)] or nullptr
+    float2 *part;        // per-CTA (sum, compensation) of sum F^2, [3][nblk][depth]
+    SolveState *st;
+    unsigned long long cond;  // cudaGraphConditionalHandle of the while node
+    int use_cond;
+    int vec;             // W % 4 == 0 and every plane 16-byte aligned
+    int H, W;
+    int max_iter;
+    int depth;           // iterations fused per sweep launch
+    int nblk;            // CTAs per channel
+    float tol, tau, eps;
+    float wg0, wg1, wg2; // Gaussian weights at offsets 0, +-1, +-2
+};
+
+// State of the atmospheric-light selection.
+struct SelectState {
+    unsigned prefix;   // key bits fixed so far
+    unsigned krem;     // rank still to find among keys with that prefix
+    unsigned key;      // the k-th largest key (after the 4 passes)
+    unsigned take;     // number of keys equal to `key` that are selected
+    int cutoff;        // largest index of a selected equal key
+    int best;          // chosen pixel
+    int clamped;
+    int pad;
+    double best_sum;
+};
+
+struct WsLayout {
+    size_t state, desc, sel, hist, blk, phin_part, part, dc, lam, phi, ub, total;
+    int nblk_sweep, nblk_dcp, nblk_sel, depth, tile_h;
+};
+
+static inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int sweep_tile_h(int depth);
+int sweep_depth(const dh_params *p);
+int dcp_blocks(int H, int W);
+constexpr int kSelBlocks = 1024;
+
+// Layout of the caller's workspace for an HxW image.
+static inline WsLayout ws_layout(int H, int W, int depth, int tile_h) {
+    WsLayout L;
+    const size_t N = (size_t)H * W;
+    L.depth = depth;
+    L.tile_h = tile_h;
+    L.nblk_sweep = ((W + kTW - 1) / kTW) * ((H + tile_h - 1) / tile_h);
+    L.nblk_dcp = dcp_blocks(H, W);
+    L.nblk_sel = kSelBlocks;
+    size_t o = 0;
+    L.state = o; o = align_up(o + sizeof(SolveState));
+    L.desc = o; o = align_up(o + sizeof(SolveDesc));
+    L.sel = o; o = align_up(o + sizeof(SelectState));
+    L.hist = o; o = align_up(o + 256 * sizeof(unsigned));
+    L.blk = o; o = align_up(o + (size_t)kSelBlocks * 16);
+    L.phin_part = o; o = align_up(o + (size_t)3 * L.nblk_dcp * sizeof(float2));
+    L.part = o; o = align_up(o + (size_t)3 * L.nblk_sweep * depth * sizeof(float2));
+    L.dc = o; o = align_up(o + N * sizeof(float));
+    L.lam = o; o = align_up(o + N * sizeof(float));
+    L.phi = o; o = align_up(o + 3 * N * sizeof(float));
+    L.ub = o; o = align_up(o + 3 * N * sizeof(float));
+    L.total = o;
+    return L;
+}
+
+static inline bool shape_ok(int H, int W) {
+    return H >= 1 && W >= 1 && H <= kMaxDim && W <= kMaxDim && (long long)H * W <= kMaxPixels;
+}
+
+// ---------------------------------------------------------------- device helpers
+// Half-sample symmetric extension with period 2n (scipy.ndimage 'reflect').
+__device__ __forceinline__ int reflect_idx(int i, int n) {
+    if (i >= 0 && i < n) return i;
+    const int p = 2 * n;
+    int m = i % p;
+    if (m < 0) m += p;
+    return m < n ? m : p - 1 - m;
+}
+
+// Neumaier step: (s, c) += v, with the rounding error of the add kept in c.
+__device__ __forceinline__ void neumaier_add(float &s, float &c, float v) {
+    const float t = s + v;
+    const float big = fabsf(s) >= fabsf(v) ? s : v;
+    const float small = fabsf(s) >= fabsf(v) ? v : s;
+    c += (big - t) + small;
+    s = t;
+}
+
+// (s, c) += (s2, c2)
+__device__ __forceinline__ void neumaier_merge(float &s, float &c, float s2, float c2) {
+    neumaier_add(s, c, s2);
+    c += c2;
+}
+
+// Order-preserving map from float bits to unsigned (larger float => larger key).
+__device__ __forceinline__ unsigned float_key(float f) {
+    const unsigned b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+}  // namespace dh
+
+// Host-side error plumbing.
+#define DH_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return dh::cuda_fail(e_);    \
+    } while (0)
+
+namespace dh {
+int cuda_fail(cudaError_t e);
+}

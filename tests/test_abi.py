@@ -1,0 +1,88 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds and loads,
+exports every entry point include/dehaze.h declares, and rejects bad
+arguments before touching the device."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2506_08793_gb300 import _native as N
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dehaze.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    return N.lib()
+
+
+def header_symbols():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(dh_\w+)\s*\(", txt, flags=re.M))
+
+
+def test_exports_every_declared_symbol(L):
+    decl = header_symbols()
+    assert decl == set(N.EXPORTS)
+    out = subprocess.run(["nm", "-D", "--defined-only", N.SO], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (dh_\w+)", out))
+    assert decl <= exported, decl - exported
+    for s in decl:
+        assert hasattr(L, s)
+
+
+def test_struct_sizes_match_header():
+    # dh_params: 16 4-byte fields; dh_report: 2 ints, 6 floats, long long, 2 floats, int (+pad)
+    assert ctypes.sizeof(N.DhParams) == 64
+    assert ctypes.sizeof(N.DhReport) == 56
+
+
+def test_defaults_are_the_paper_constants():
+    p = N.dh_params_default(N.DH_PRESET_PAPER)
+    assert (p.patch, p.radius, p.topk_permille) == (15, 2, 1)
+    for k, v in dict(omega=0.95, eps=1e-3, sigma=2.0, lambda0=0.5, beta=3.0, tau=0.2, t0=0.1).items():
+        assert getattr(p, k) == pytest.approx(v, rel=1e-7), k
+    s = N.dh_params_default(N.DH_PRESET_STABLE)
+    assert s.eps == 1.0
+    assert {k for k, _ in p._fields_ if getattr(p, k) != getattr(s, k)} == {"eps"}
+    with pytest.raises(ValueError):
+        N.dh_params_default(7)
+    assert N.dh_version() == 1
+
+
+def test_strerror_covers_codes():
+    for c in (0, 1, 2, -1, -2, -3, -4, -5):
+        assert N.dh_strerror(c) != "unknown status"
+    assert N.dh_strerror(99) == "unknown status"
+
+
+def test_workspace_bytes():
+    p = N.dh_params_default(N.DH_PRESET_STABLE)
+    b = N.dh_workspace_bytes(1080, 1920, p)
+    n = 1080 * 1920
+    assert b >= 4 * (8 * n) and b < 4 * (8 * n) + (1 << 22)
+    assert N.dh_workspace_bytes(0, 5, p) == 0
+    assert N.dh_workspace_bytes(5, 40000, p) == 0
+    assert N.dh_workspace_bytes(4, 4, p.replace(patch=4)) == 0
+    assert N.dh_workspace_bytes(4, 4, p.replace(radius=3)) == 0
+    assert N.dh_workspace_bytes(4, 4, p.replace(eps=0.0)) == 0
+    assert N.dh_workspace_bytes(4, 4, None) > 0
+
+
+def test_invalid_arguments_rejected_on_host():
+    p = N.dh_params_default(N.DH_PRESET_STABLE)
+    fake = 1 << 20  # never dereferenced: every call below fails validation first
+    assert N.dh_dark_channel(fake, 8, 8, 4, None, fake) == N.DH_EINVAL
+    assert N.dh_dark_channel(None, 8, 8, 15, None, fake) == N.DH_EINVAL
+    assert N.dh_dark_channel(fake, 0, 8, 15, None, fake) == N.DH_EINVAL
+    assert N.dh_transmission(fake, fake, 8, 8, p.replace(omega=2.0), None, fake, fake, fake) == N.DH_EINVAL
+    assert N.dh_fixed_point(fake, fake, fake, 8, 8, p, None, None, 0) == N.DH_EWORKSPACE
+    assert N.dh_fixed_point(fake, fake, fake, 8, 8, p, None, fake + 8, 1 << 30) == N.DH_EWORKSPACE
+    assert N.dh_fixed_point(fake, fake, fake, 8, 8, p.replace(max_iter=-1), None, fake, 1 << 30) == N.DH_EINVAL
+    assert N.dh_dehaze(fake, 8, 8, p, None, fake, fake, fake, fake, fake, 16) == N.DH_EWORKSPACE
+    assert N.dh_dehaze(fake, 8, 8, p.replace(storage=9), None, fake, fake, fake, fake, fake, 1 << 30) == N.DH_EINVAL
+    assert N.dh_atmospheric_light(fake, fake, 8, 8, 0, fake, None, fake, 1 << 30) == N.DH_EINVAL
