@@ -101,6 +101,13 @@ k_sweep(const SolveDesc *__restrict__ d) {
     __shared__ int s_last;
 
     SolveState *st = d->st;
+    // The loop ends unless this launch's last CTA sets the condition back to
+    // 1, so a launch that failed to count its CTAs cannot spin forever.  CTA
+    // (0,0,0) clears it before it arrives, hence before the last CTA decides.
+    if (d->use_cond && (blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) {
+        cudaGraphSetConditional(d->cond, 0);
+        __threadfence();
+    }
     if (ld_state_int(&st->done)) return;
     const int H = d->H, W = d->W;
     const int c = blockIdx.z;
@@ -401,6 +408,7 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
     v.max_iter = p->max_iter;
     v.depth = 1;
     v.nblk = grid.x * grid.y;
+    if (v.nblk > L.nblk_sweep) return DH_EINVAL;  // workspace sized for another tiling
     {
         auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
         v.vec = (W % 4 == 0) && a16(u_caller) && a16(v.u[1]) && a16(phi) && a16(lam);
