@@ -228,8 +228,12 @@ def test_graph_and_host_loop_identical_and_resume_exact(N, api, orc):
 def test_nonfinite_input_reported(N, api):
     I = scenes.hazy_scene(3, 64, 64)["I"].copy()
     I[1, 10, 10] = np.nan
-    out = api.dehaze(dev(I), api.params("stable", max_iter=50))
-    assert out["report"].status == N.DH_ENONFINITE
+    with pytest.raises(api.DehazeError) as e:
+        api.dehaze(dev(I), api.params("stable", max_iter=50))
+    assert e.value.status == N.DH_ENONFINITE
+    # the library stays usable after the error
+    out = api.dehaze(dev(scenes.hazy_scene(3, 64, 64)["I"]), api.params("stable"))
+    assert out["report"].status == N.DH_OK
 
 
 # ------------------------------------------------------------ whole method
@@ -261,7 +265,9 @@ def test_dehaze_256_paper_200_iterations(N, api, orc):
     assert rep.n_iter == 200 and rep.status == N.DH_WNOCONV and np.all(np.isfinite(rep.rho))
     r = orc.dehaze(I, oparams(orc, "paper"), 1, 0.0)
     one = api.dehaze(dev(I), api.params("paper", max_iter=1, tol=0.0))
-    assert np.max(np.abs(host(one["u"]) - r["u"])) <= 1e-5
+    # u^0 = Phi differs from the FP64 Phi by float32 rounding, which one update
+    # with eps = 1e-3 amplifies by up to 4*tau/eps = 800: held to U_TOL.
+    assert np.max(np.abs(host(one["u"]) - r["u"])) <= U_TOL
 
 
 # ------------------------------------------------------------ full sizes
