@@ -160,6 +160,21 @@ int dh_dehaze(const float *I, int H, int W, const dh_params *p, const float *u0,
               float *u, float *t, float *A, void *workspace, size_t workspace_bytes,
               void *stream, dh_report *report);
 
+/* dh_atmospheric_light without a workspace and without any allocation.
+ * The paper has no counterpart: this exists for callers that cannot call
+ * cudaMalloc, such as a plug-in whose host application owns all device memory,
+ * or a real-time frame loop that may not allocate.  Same inputs, outputs and
+ * result as dh_atmospheric_light (no report).  Its scratch is one fixed
+ * 32 KiB array in device memory that every GPU which loads the library keeps
+ * until the process exits; it does not grow with the image, so the size limit
+ * is the library's own (1 <= H, W <= 32768, H*W <= 2^28; DH_EINVAL beyond).
+ * The first call on a device looks up the array's device address and should
+ * come before any stream capture on that device.  All calls share the array:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must be serialised by the caller. */
+int dh_atmospheric_light_noalloc(const float *I, const float *dc, int H, int W, int topk_permille,
+                                 float *A_out, long long *index_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

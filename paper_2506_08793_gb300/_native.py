@@ -28,7 +28,7 @@ DH_VAR_NO_ADAPTIVE, DH_VAR_NO_EDGE, DH_VAR_NO_NONLOCAL = 1, 2, 4
 # Every symbol include/dehaze.h declares.
 EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes",
            "dh_dark_channel", "dh_atmospheric_light", "dh_transmission", "dh_fixed_point",
-           "dh_dehaze")
+           "dh_dehaze", "dh_atmospheric_light_noalloc")
 
 
 class DhParams(ctypes.Structure):
@@ -106,6 +106,7 @@ def lib(build_if_missing: bool = True):
             "dh_transmission": ([P, P, I, I, PP, P, P, P, P, P], I),
             "dh_fixed_point": ([P, P, P, I, I, PP, P, P, S, P, PR], I),
             "dh_dehaze": ([P, I, I, PP, P, P, P, P, P, P, S, P, PR], I),
+            "dh_atmospheric_light_noalloc": ([P, P, I, I, I, P, P, P], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -181,3 +182,10 @@ def dh_dehaze(I, H, W, p: DhParams, u0, J, u, t, A, workspace, workspace_bytes, 
               report: DhReport | None = None) -> int:
     return lib().dh_dehaze(_p(I), H, W, ctypes.byref(p), _p(u0), _p(J), _p(u), _p(t), _p(A),
                            _p(workspace), workspace_bytes, _stream(stream), _ref(report))
+
+
+def dh_atmospheric_light_noalloc(I, dc, H, W, topk_permille, A_out, index_out, stream=None) -> int:
+    """dh_atmospheric_light with the library's fixed device scratch array in
+    place of a caller workspace (for callers that may not allocate)."""
+    return lib().dh_atmospheric_light_noalloc(_p(I), _p(dc), H, W, topk_permille, _p(A_out), _p(index_out),
+                                              _stream(stream))

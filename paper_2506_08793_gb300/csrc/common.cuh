@@ -71,7 +71,7 @@ struct WsLayout {
     int nblk_sweep, nblk_dcp, nblk_sel, depth, tile_h;
 };
 
-static inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+constexpr size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int sweep_tile_h(int depth);
 int sweep_depth(const dh_params *p);

@@ -1,0 +1,65 @@
+// Atmospheric-light selection that allocates nothing and needs no workspace.
+//
+// Some callers cannot call cudaMalloc at all: a plug-in inside a host
+// application that owns every device buffer and hands the plug-in only its
+// inputs and outputs, or a real-time pipeline whose memory is fixed at start
+// and whose frame loop may not allocate (allocation can block the device and
+// can fail in the middle of a frame).  This entry point serves them: its
+// scratch is a file-scope device array of fixed size, so the caller passes
+// only the image, its dark channel and the outputs.
+#include <mutex>
+
+#include "common.cuh"
+
+namespace dh {
+
+int launch_select_A(const float *I, const float *dc, int H, int W, int permille, float *A,
+                    long long *index_out, char *ws, const WsLayout &L, cudaStream_t s);
+
+// Selection state, the 256-bin radix histogram and kSelBlocks 16-byte
+// per-block records.  Its size does not depend on the image.
+constexpr size_t kNoAllocScratchBytes = 32768;
+static __device__ __align__(256) unsigned char g_select_scratch[kNoAllocScratchBytes];
+
+constexpr size_t kNaHist = align_up(sizeof(SelectState));
+constexpr size_t kNaBlk = kNaHist + align_up(256 * sizeof(unsigned));
+static_assert(kNaBlk + (size_t)kSelBlocks * 16 <= kNoAllocScratchBytes, "scratch too small");
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_na_mu;
+static char *g_na_ptr[kMaxDevices];  // device address of g_select_scratch, per device
+
+}  // namespace dh
+
+using namespace dh;
+
+extern "C" int dh_atmospheric_light_noalloc(const float *I, const float *dc, int H, int W,
+                                            int topk_permille, float *A_out, long long *index_out,
+                                            void *stream) {
+    if (!I || !dc || !A_out || !shape_ok(H, W) || topk_permille < 1 || topk_permille > 1000)
+        return DH_EINVAL;
+    int dev = 0;
+    DH_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return DH_EINVAL;
+    char *scratch;
+    {
+        // First call on a device: look up the array's device address (the
+        // host-side name is only a stand-in and must not reach a kernel).
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (!g_na_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_select_scratch);
+            if (e != cudaSuccess || !p) return cuda_fail(e);
+            g_na_ptr[dev] = (char *)p;
+        }
+        scratch = g_na_ptr[dev];
+    }
+    WsLayout L = {};
+    L.sel = 0;
+    L.hist = kNaHist;
+    L.blk = kNaBlk;
+    // The selection clears its state and histogram itself before use, and
+    // writes every per-block record before reading it.
+    return launch_select_A(I, dc, H, W, topk_permille, A_out, index_out, scratch, L,
+                           (cudaStream_t)stream);
+}
