@@ -1,0 +1,33 @@
+"""A fixed, small workload for profilers: the whole method on one synthetic
+scene with a fixed number of fixed-point iterations (tol = 0), so the sweep
+kernel runs exactly iters + 1 times.
+
+    python -m paper_2506_08793_gb300.profile_case --H 1080 --W 1920 --iters 8
+"""
+import argparse
+
+import torch
+
+from . import api, scenes
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--H", type=int, default=1080)
+    ap.add_argument("--W", type=int, default=1920)
+    ap.add_argument("--seed", type=int, default=2000)
+    ap.add_argument("--iters", type=int, default=8)
+    ap.add_argument("--preset", default="stable")
+    ap.add_argument("--repeat", type=int, default=1)
+    a = ap.parse_args()
+    I = torch.from_numpy(scenes.hazy_scene(a.seed, a.H, a.W)["I"]).cuda()
+    d = api.Dehazer(a.H, a.W, api.params(a.preset, tol=0.0, max_iter=a.iters))
+    for _ in range(a.repeat):
+        rep = d(I)
+    torch.cuda.synchronize()
+    print(f"{a.H}x{a.W}: {rep.n_iter} iterations, {rep.ms:.3f} ms, loop {rep.ms_loop:.3f} ms, "
+          f"{rep.launches} launches")
+
+
+if __name__ == "__main__":
+    main()
