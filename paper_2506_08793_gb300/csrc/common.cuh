@@ -29,7 +29,7 @@ struct SolveState {
     int n_final;       // n of the returned iterate
     float rho[3];      // residual of u^n_final
     float phin2[3];    // ||Phi^c||^2
-    unsigned sel_arrive;
+    int err;           // error raised inside a sweep (DH_ETIMEOUT), 0 if none
     int pad[3];
 };
 
@@ -48,7 +48,7 @@ struct SolveDesc {
     int H, W;
     int max_iter;
     int depth;           // iterations fused per sweep launch
-    int nblk;            // CTAs per channel
+    int nblk;            // residual partials per channel (one per tile)
     float tol, tau, eps;
     float wg0, wg1, wg2; // Gaussian weights at offsets 0, +-1, +-2
 };

@@ -7,7 +7,12 @@
 #include <mutex>
 #include <vector>
 
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace dh {
 
@@ -26,16 +31,26 @@ __device__ __forceinline__ float rcp_approx(float x) {
 
 // D u_n on one face: a = difference across the face, b = the half central
 // difference along it, D = (sqrt(a^2 + b^2) + eps)^-1 (Sec. II-B, App. A-B-1).
+// Every rounding step is spelled out (__f*_rn, fmaf) so that no kernel
+// variant's contraction choices change the result: all variants agree bit for bit.
 template <bool EDGE>
 __device__ __forceinline__ float face_flux(float a, float b, float eps) {
     if (!EDGE) return a;  // ablation: D == 1
-    const float s = fmaf(a, a, b * b);
-    return a * rcp_approx(sqrt_approx(s) + eps);
+    const float s = fmaf(a, a, __fmul_rn(b, b));
+    return __fmul_rn(a, rcp_approx(__fadd_rn(sqrt_approx(s), eps)));
+}
+
+__device__ __forceinline__ float half_diff(float p, float m) { return __fmul_rn(0.5f, __fsub_rn(p, m)); }
+
+// 5-tap symmetric Gaussian: w2 (v-2 + v+2) + w1 (v-1 + v+1) + w0 v0
+__device__ __forceinline__ float gauss5(float vm2, float vm1, float v0, float vp1, float vp2, float wg0, float wg1,
+                                        float wg2) {
+    return fmaf(wg2, __fadd_rn(vm2, vp2), fmaf(wg1, __fadd_rn(vm1, vp1), __fmul_rn(wg0, v0)));
 }
 
 __device__ __forceinline__ int ld_state_int(const int *p) { return __ldcg(p); }
 
-// Reduces the per-CTA partials of the launch (last CTA only), decides whether
+// Reduces the per-tile partials of the launch (last CTA only), decides whether
 // to stop, advances the state and sets the graph's while condition.
 __device__ void finish_iteration(const SolveDesc *d, SolveState *st) {
     __shared__ float sq[3];
@@ -68,12 +83,13 @@ __device__ void finish_iteration(const SolveDesc *d, SolveState *st) {
         else worst = fmaxf(worst, rho[c]);
         if (d->rho_hist) d->rho_hist[3 * n + c] = rho[c];
     }
+    const int err = __ldcg(&st->err);
     const bool conv = finite && worst <= d->tol;
     unsigned cont = 1;
-    if (conv || !finite || n >= d->max_iter) {
+    if (err || conv || !finite || n >= d->max_iter) {
         st->done = 1;
         st->n_final = n;
-        st->status = !finite ? DH_ENONFINITE : (conv ? DH_OK : DH_WNOCONV);
+        st->status = err ? err : (!finite ? DH_ENONFINITE : (conv ? DH_OK : DH_WNOCONV));
         for (int c = 0; c < 3; ++c) st->rho[c] = rho[c];
         cont = 0;
     } else {
@@ -85,153 +101,33 @@ __device__ void finish_iteration(const SolveDesc *d, SolveState *st) {
     if (d->use_cond) cudaGraphSetConditional(d->cond, cont);
 }
 
-// One iteration for a TW x (R*NW) tile of one channel (blockIdx.z).
-// Shared memory holds the tile of u^n with a 2-row / 4-column halo; each warp
-// walks R rows, each lane owns 4 adjacent columns and keeps rolling registers
-// of the last rows of u, of the horizontally filtered rows and of the y-face
-// fluxes, so every face flux and every Gaussian row is computed once.
-template <int R, int NW, bool EDGE>
-__global__ void __launch_bounds__(NW * 32)
-k_sweep(const SolveDesc *__restrict__ d) {
-    constexpr int TH = R * NW;
-    constexpr int SW = kTW + 8;
-    constexpr int SH = TH + 4;
-    __shared__ __align__(16) float s[SH][SW];
-    __shared__ float2 red[NW];
-    __shared__ int s_last;
-
-    SolveState *st = d->st;
-    // The loop ends unless this launch's last CTA sets the condition back to
-    // 1, so a launch that failed to count its CTAs cannot spin forever.  CTA
-    // (0,0,0) clears it before it arrives, hence before the last CTA decides.
+// The loop ends unless a launch's last CTA sets the condition back to 1, so a
+// launch that failed to count its CTAs cannot spin forever.  CTA (0,0,0)
+// clears it before it arrives, hence before the last CTA decides.
+__device__ __forceinline__ void clear_condition(const SolveDesc *d) {
     if (d->use_cond && (blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) {
         cudaGraphSetConditional(d->cond, 0);
         __threadfence();
     }
-    if (ld_state_int(&st->done)) return;
-    const int H = d->H, W = d->W;
-    const int c = blockIdx.z;
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * TH;
-    const int cur = ld_state_int(&st->cur);
-    const size_t N = (size_t)H * W;
-    const float *__restrict__ u = d->u[cur] + c * N;
-    float *__restrict__ un = d->u[cur ^ 1] + c * N;
-    const float *__restrict__ phi = d->phi + c * N;
-    const float *__restrict__ lam = d->lam;
-    const float eps = d->eps, tau = d->tau;
-    const float wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
+}
 
-    // tile of u^n, rows y0-2 .. y0+TH+1, columns x0-4 .. x0+TW+3, reflected
-    for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
-        const int r = e / SW, q = e - r * SW;
-        const int gy = reflect_idx(y0 - 2 + r, H), gx = reflect_idx(x0 - 4 + q, W);
-        s[r][q] = u[(size_t)gy * W + gx];
+// Counts this CTA in and lets the last one finish the iteration.
+__device__ __forceinline__ void arrive_and_finish(const SolveDesc *d, SolveState *st, int *s_last) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned total = gridDim.x * gridDim.y * gridDim.z;
+        const unsigned prev = atomicAdd(&st->arrive, 1u);
+        *s_last = prev == total - 1u;
     }
     __syncthreads();
+    if (*s_last) finish_iteration(d, st);
+}
 
+// Deterministic block reduction of a (sum, compensation) pair; thread 0 gets it.
+template <int NW>
+__device__ __forceinline__ float2 block_pair_sum(float rs, float rc, float2 *red) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int sc = 4 * lane;      // smem column of x-4 for this lane's x
-    const int x = x0 + 4 * lane;  // first of the lane's 4 columns
-    const int r0 = w * R;         // first tile row of this warp
-    const bool vec = d->vec != 0;
-
-    // rolling registers: uu[k][j] = u at tile row (r0-1+k) (mod 4 ring),
-    // column x-1+j (j = 0..5); gh[k][j] = horizontal Gaussian at tile row
-    // (r0-2+k) (mod 5 ring), column x+j.
-    float uu[4][6];
-    float gh[5][4];
-    float fyu[4];
-
-    auto load_row = [&](int tr, float *v6, float *g4) {
-        // tr = tile row (may be -2 .. TH+1); smem row tr+2
-        const float4 L = *reinterpret_cast<const float4 *>(&s[tr + 2][sc]);
-        const float4 C = *reinterpret_cast<const float4 *>(&s[tr + 2][sc + 4]);
-        const float4 Rr = *reinterpret_cast<const float4 *>(&s[tr + 2][sc + 8]);
-        const float v[8] = {L.z, L.w, C.x, C.y, C.z, C.w, Rr.x, Rr.y};  // x-2 .. x+5
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            g4[j] = fmaf(wg2, v[j] + v[j + 4], fmaf(wg1, v[j + 1] + v[j + 3], wg0 * v[j + 2]));
-        if (v6) {
-#pragma unroll
-            for (int j = 0; j < 6; ++j) v6[j] = v[j + 1];
-        }
-    };
-
-    // prologue: Gaussian rows r0-2, r0-1, r0, r0+1; u rows r0-1, r0, r0+1
-    {
-        float dummy[6];
-        load_row(r0 - 2, dummy, gh[0]);
-        load_row(r0 - 1, uu[0], gh[1]);
-        load_row(r0, uu[1], gh[2]);
-        load_row(r0 + 1, uu[2], gh[3]);
-        // y-face flux at r0 - 1/2, tangential difference on row r0-1
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            fyu[j] = face_flux<EDGE>(uu[1][j + 1] - uu[0][j + 1], 0.5f * (uu[0][j + 2] - uu[0][j]), eps);
-    }
-
-    float rs = 0.f, rc = 0.f;  // compensated sum of F^2 over the lane's pixels
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        const int ty = r0 + i;
-        const int y = y0 + ty;
-        float *um = uu[(i + 0) & 3];
-        float *u0 = uu[(i + 1) & 3];
-        float *up = uu[(i + 2) & 3];
-        float *upp = uu[(i + 3) & 3];
-        load_row(ty + 2, upp, gh[(i + 4) % 5]);
-        const float *g_m2 = gh[(i + 0) % 5], *g_m1 = gh[(i + 1) % 5], *g_0 = gh[(i + 2) % 5];
-        const float *g_p1 = gh[(i + 3) % 5], *g_p2 = gh[(i + 4) % 5];
-
-        // x-face fluxes at x-1/2 .. x+3+1/2 (tangential difference at the face's left cell)
-        float fx[5];
-#pragma unroll
-        for (int j = 0; j < 5; ++j)
-            fx[j] = face_flux<EDGE>(u0[j + 1] - u0[j], 0.5f * (up[j] - um[j]), eps);
-        float fyd[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            fyd[j] = face_flux<EDGE>(up[j + 1] - u0[j + 1], 0.5f * (u0[j + 2] - u0[j]), eps);
-
-        float ph[4] = {0.f, 0.f, 0.f, 0.f}, la[4] = {0.f, 0.f, 0.f, 0.f};
-        const bool row_ok = y < H;
-        const size_t ro = (size_t)y * W;
-        if (row_ok) {
-            if (vec && x < W) {
-                const float4 p4 = __ldg(reinterpret_cast<const float4 *>(phi + ro + x));
-                const float4 l4 = __ldg(reinterpret_cast<const float4 *>(lam + ro + x));
-                ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
-                la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
-            } else if (!vec) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (x + j < W) { ph[j] = __ldg(phi + ro + x + j); la[j] = __ldg(lam + ro + x + j); }
-            }
-        }
-        float nu[4];
-        float q = 0.f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float G = fmaf(wg2, g_m2[j] + g_p2[j], fmaf(wg1, g_m1[j] + g_p1[j], wg0 * g_0[j]));
-            const float dv = (fx[j + 1] - fx[j]) + (fyd[j] - fyu[j]);
-            const float F = fmaf(-la[j], G, dv) + ph[j];
-            nu[j] = fmaf(tau, F, u0[j + 1]);
-            if (x + j < W) q = fmaf(F, F, q);
-            fyu[j] = fyd[j];
-        }
-        if (row_ok) {
-            neumaier_add(rs, rc, q);
-            if (vec && x < W) {
-                *reinterpret_cast<float4 *>(un + ro + x) = make_float4(nu[0], nu[1], nu[2], nu[3]);
-            } else if (!vec) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (x + j < W) un[ro + x + j] = nu[j];
-            }
-        }
-    }
-
-    // deterministic block reduction of the residual partial
     for (int off = 16; off; off >>= 1) {
         const float s2 = __shfl_down_sync(0xffffffffu, rs, off);
         const float c2 = __shfl_down_sync(0xffffffffu, rc, off);
@@ -239,18 +135,321 @@ k_sweep(const SolveDesc *__restrict__ d) {
     }
     if (lane == 0) red[w] = make_float2(rs, rc);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float a = red[0].x, b = red[0].y;
+    float a = red[0].x, b = red[0].y;
 #pragma unroll
-        for (int k = 1; k < NW; ++k) neumaier_merge(a, b, red[k].x, red[k].y);
-        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-        d->part[(size_t)c * d->nblk + blk] = make_float2(a, b);
-        __threadfence();
-        const unsigned prev = atomicAdd(&st->arrive, 1u);
-        s_last = prev == 3u * d->nblk - 1u;
+    for (int k = 1; k < NW; ++k) neumaier_merge(a, b, red[k].x, red[k].y);
+    return make_float2(a, b);
+}
+
+// One warp's walk over tile rows [r0, r0+R) for its lane's 4 columns.
+// `s` is the u^n tile in shared memory: row stride SW floats, tile row ty at
+// smem row ty+2, the lane's first column at smem column 4*lane+4.  Every x-
+// and y-face flux and every horizontally filtered row is computed once and
+// kept in rolling registers.  pl(ty, ph, la) supplies Phi and lambda for the
+// row; sink(ty, nu, F) consumes u^{n+1} and F.
+template <int R, int SW, bool EDGE, class PL, class SINK>
+__device__ __forceinline__ void walk_rows(const float *__restrict__ s, int r0, int lane, float eps, float tau,
+                                          float wg0, float wg1, float wg2, PL pl, SINK sink) {
+    const int sc = 4 * lane;
+    float uu[4][6];  // u at tile rows r0-1+k (mod 4), columns x-1 .. x+4
+    float gh[5][4];  // horizontal Gaussian at tile rows r0-2+k (mod 5), columns x .. x+3
+    float fyu[4];    // y-face flux above the current row
+
+    auto load_row = [&](int tr, float *v6, float *g4) {
+        const float *row = s + (tr + 2) * SW + sc;
+        const float4 L = *reinterpret_cast<const float4 *>(row);
+        const float4 C = *reinterpret_cast<const float4 *>(row + 4);
+        const float4 Rr = *reinterpret_cast<const float4 *>(row + 8);
+        const float v[8] = {L.z, L.w, C.x, C.y, C.z, C.w, Rr.x, Rr.y};  // x-2 .. x+5
+#pragma unroll
+        for (int j = 0; j < 4; ++j) g4[j] = gauss5(v[j], v[j + 1], v[j + 2], v[j + 3], v[j + 4], wg0, wg1, wg2);
+        if (v6) {
+#pragma unroll
+            for (int j = 0; j < 6; ++j) v6[j] = v[j + 1];
+        }
+    };
+
+    {
+        float dummy[6];
+        load_row(r0 - 2, dummy, gh[0]);
+        load_row(r0 - 1, uu[0], gh[1]);
+        load_row(r0, uu[1], gh[2]);
+        load_row(r0 + 1, uu[2], gh[3]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)  // y-face at r0 - 1/2, tangential difference on row r0-1
+            fyu[j] = face_flux<EDGE>(__fsub_rn(uu[1][j + 1], uu[0][j + 1]), half_diff(uu[0][j + 2], uu[0][j]), eps);
+    }
+
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int ty = r0 + i;
+        float *um = uu[(i + 0) & 3];
+        float *u0 = uu[(i + 1) & 3];
+        float *up = uu[(i + 2) & 3];
+        float *upp = uu[(i + 3) & 3];
+        load_row(ty + 2, upp, gh[(i + 4) % 5]);
+        const float *g_m2 = gh[(i + 0) % 5], *g_m1 = gh[(i + 1) % 5], *g_0 = gh[(i + 2) % 5];
+        const float *g_p1 = gh[(i + 3) % 5], *g_p2 = gh[(i + 4) % 5];
+        float ph[4], la[4];
+        pl(ty, ph, la);
+        // x-faces at x-1/2 .. x+3+1/2, tangential difference at the face's left cell
+        float fx[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+            fx[j] = face_flux<EDGE>(__fsub_rn(u0[j + 1], u0[j]), half_diff(up[j], um[j]), eps);
+        float nu[4], F[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float fyd = face_flux<EDGE>(__fsub_rn(up[j + 1], u0[j + 1]), half_diff(u0[j + 2], u0[j]), eps);
+            const float G = gauss5(g_m2[j], g_m1[j], g_0[j], g_p1[j], g_p2[j], wg0, wg1, wg2);
+            const float dv = __fadd_rn(__fsub_rn(fx[j + 1], fx[j]), __fsub_rn(fyd, fyu[j]));
+            F[j] = __fadd_rn(fmaf(-la[j], G, dv), ph[j]);
+            nu[j] = fmaf(tau, F[j], u0[j + 1]);
+            fyu[j] = fyd;
+        }
+        sink(ty, nu, F);
+    }
+}
+
+// Generic sweep (any W, any alignment): one CTA per (tile, channel), tile of
+// u^n gathered with the reflecting boundary by plain loads.
+template <int R, int NW, bool EDGE>
+__global__ void __launch_bounds__(NW * 32)
+k_sweep(const SolveDesc *__restrict__ d) {
+    constexpr int TH = R * NW;
+    constexpr int SW = kTW + 8;
+    constexpr int SH = TH + 4;
+    __shared__ __align__(16) float s[SH * SW];
+    __shared__ float2 red[NW];
+    __shared__ int s_last;
+
+    SolveState *st = d->st;
+    clear_condition(d);
+    if (__ldcg(&st->done)) return;
+    const int H = d->H, W = d->W;
+    const int c = blockIdx.z;
+    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * TH;
+    const int cur = __ldcg(&st->cur);
+    const size_t N = (size_t)H * W;
+    const float *__restrict__ u = d->u[cur] + c * N;
+    float *__restrict__ un = d->u[cur ^ 1] + c * N;
+    const float *__restrict__ phi = d->phi + c * N;
+    const float *__restrict__ lam = d->lam;
+
+    for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
+        const int r = e / SW, q = e - r * SW;
+        const int gy = reflect_idx(y0 - 2 + r, H), gx = reflect_idx(x0 - 4 + q, W);
+        s[e] = u[(size_t)gy * W + gx];
     }
     __syncthreads();
-    if (s_last) finish_iteration(d, st);
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = x0 + 4 * lane;
+    const bool vec = d->vec != 0;
+    float rs = 0.f, rc = 0.f;
+    auto pl = [&](int ty, float *ph, float *la) {
+        const int y = y0 + ty;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ph[j] = la[j] = 0.f;
+        if (y >= H) return;
+        const size_t ro = (size_t)y * W;
+        if (vec) {
+            if (x < W) {
+                const float4 p4 = __ldg(reinterpret_cast<const float4 *>(phi + ro + x));
+                const float4 l4 = __ldg(reinterpret_cast<const float4 *>(lam + ro + x));
+                ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
+                la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (x + j < W) { ph[j] = __ldg(phi + ro + x + j); la[j] = __ldg(lam + ro + x + j); }
+        }
+    };
+    auto sink = [&](int ty, const float *nu, const float *F) {
+        const int y = y0 + ty;
+        if (y >= H) return;
+        const size_t ro = (size_t)y * W;
+        float q = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (x + j < W) q = fmaf(F[j], F[j], q);
+        neumaier_add(rs, rc, q);
+        if (vec) {
+            if (x < W) *reinterpret_cast<float4 *>(un + ro + x) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (x + j < W) un[ro + x + j] = nu[j];
+        }
+    };
+    walk_rows<R, SW, EDGE>(s, w * R, lane, d->eps, d->tau, d->wg0, d->wg1, d->wg2, pl, sink);
+
+    const float2 tot = block_pair_sum<NW>(rs, rc, red);
+    if (threadIdx.x == 0)
+        d->part[(size_t)c * d->nblk + blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    arrive_and_finish(d, st, &s_last);
+}
+
+// Shared-memory plan of the TMA sweep: per stage the u^n tile with its halo,
+// the Phi tile and the lambda tile, each 1024-byte aligned.
+template <int TH, bool PL_SMEM>
+struct TmaPlan {
+    static constexpr int SW = kTW + 8;
+    static constexpr int SH = TH + 4;
+    static constexpr uint32_t U_BYTES = SH * SW * 4;
+    static constexpr uint32_t P_BYTES = PL_SMEM ? TH * kTW * 4 : 0;
+    static constexpr uint32_t U_OFF = 0;
+    static constexpr uint32_t PHI_OFF = (U_BYTES + 1023) / 1024 * 1024;
+    static constexpr uint32_t LAM_OFF = PHI_OFF + P_BYTES;
+    static constexpr uint32_t STAGE = (LAM_OFF + P_BYTES + 1023) / 1024 * 1024;
+    static constexpr uint32_t TX = U_BYTES + 2 * P_BYTES;
+};
+
+constexpr long long kWaitLimitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+// TMA sweep (W % 4 == 0, 16-byte aligned planes): persistent CTAs walk the
+// (tile, channel) items; one thread streams each item's u^n tile (with halo)
+// into shared memory by TMA, STAGES items ahead, together with the Phi and
+// lambda tiles when PL_SMEM (otherwise the walk reads those with vector
+// loads); the border halo is reflected in shared memory afterwards.
+template <int R, int NW, int STAGES, bool PL_SMEM, bool EDGE>
+__global__ void __launch_bounds__(NW * 32)
+k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
+            const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
+            const SolveDesc *__restrict__ d) {
+    constexpr int TH = R * NW;
+    using P = TmaPlan<TH, PL_SMEM>;
+    constexpr int SW = P::SW, SH = P::SH;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned base (the launch adds 1 KiB of slack)
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bar[STAGES];
+    __shared__ float2 red[NW];
+    __shared__ int s_last;
+
+    SolveState *st = d->st;
+    clear_condition(d);
+    if (__ldcg(&st->done)) return;
+    const int H = d->H, W = d->W;
+    const int cur = __ldcg(&st->cur);
+    const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
+    float *__restrict__ ubase = d->u[cur ^ 1];
+    const size_t N = (size_t)H * W;
+    const int ntx = (W + kTW - 1) / kTW, nty = (H + TH - 1) / TH;
+    const int ntiles = ntx * nty, nitems = 3 * ntiles;
+    const int G = gridDim.x;
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < STAGES; ++k) mbar_init(&bar[k], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int item, int stage) {
+        const int tile = item / 3, c = item - 3 * tile;
+        const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * TH;
+        unsigned char *sb = smem + stage * P::STAGE;
+        mbar_arrive_expect_tx(&bar[stage], P::TX);
+        tma_load_3d(sb + P::U_OFF, tm_u, &bar[stage], x0 - 4, y0 - 2, c);
+        if (PL_SMEM) {
+            tma_load_3d(sb + P::PHI_OFF, &tm_phi, &bar[stage], x0, y0, c);
+            tma_load_2d(sb + P::LAM_OFF, &tm_lam, &bar[stage], x0, y0);
+        }
+    };
+    if (threadIdx.x == 0)
+        for (int k = 0; k < STAGES; ++k)
+            if (blockIdx.x + k * G < nitems) issue(blockIdx.x + k * G, k);
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
+    int k = 0;
+    bool failed = false;
+    for (int item = blockIdx.x; item < nitems; item += G, ++k) {
+        const int stage = k % STAGES;
+        const uint32_t parity = (k / STAGES) & 1;
+        const int tile = item / 3, c = item - 3 * tile;
+        const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * TH;
+        unsigned char *sb = smem + stage * P::STAGE;
+        float *s = reinterpret_cast<float *>(sb + P::U_OFF);
+        const float *sphi = reinterpret_cast<const float *>(sb + P::PHI_OFF);
+        const float *slam = reinterpret_cast<const float *>(sb + P::LAM_OFF);
+
+        const bool ok = mbar_wait_bounded(&bar[stage], parity, kWaitLimitCycles);
+        if (__syncthreads_or(!ok)) {
+            failed = true;
+            break;
+        }
+        // reflect the halo cells that fall outside the image (TMA filled zeros)
+        if (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + TH + 2 > H) {
+            for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
+                const int r = e / SW, q = e - r * SW;
+                const int gy = y0 - 2 + r, gx = x0 - 4 + q;
+                const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
+                const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
+                const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
+                if ((fy && (inx || fx)) || (fx && iny)) {
+                    const int sy = reflect_idx(gy, H) - (y0 - 2), sx = reflect_idx(gx, W) - (x0 - 4);
+                    s[e] = s[sy * SW + sx];
+                }
+            }
+            fence_proxy_async_smem();  // these writes precede the stage's next TMA load
+        }
+        __syncthreads();
+
+        float *__restrict__ un = ubase + c * N;
+        const int x = x0 + 4 * lane;
+        float rs = 0.f, rc = 0.f;
+        const float *__restrict__ gphi = d->phi + c * N;
+        const float *__restrict__ glam = d->lam;
+        auto pl = [&](int ty, float *ph, float *la) {
+            float4 p4, l4;
+            if (PL_SMEM) {
+                p4 = *reinterpret_cast<const float4 *>(sphi + ty * kTW + 4 * lane);
+                l4 = *reinterpret_cast<const float4 *>(slam + ty * kTW + 4 * lane);
+            } else {
+                const int y = y0 + ty;
+                p4 = l4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (y < H && x < W) {
+                    p4 = __ldg(reinterpret_cast<const float4 *>(gphi + (size_t)y * W + x));
+                    l4 = __ldg(reinterpret_cast<const float4 *>(glam + (size_t)y * W + x));
+                }
+            }
+            ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
+            la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
+        };
+        auto sink = [&](int ty, const float *nu, const float *F) {
+            const int y = y0 + ty;
+            if (y >= H || x >= W) return;  // W % 4 == 0: x < W covers all 4 columns
+            float q = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q = fmaf(F[j], F[j], q);
+            neumaier_add(rs, rc, q);
+            *reinterpret_cast<float4 *>(un + (size_t)y * W + x) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+        };
+        walk_rows<R, SW, EDGE>(s, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
+
+        const float2 tot = block_pair_sum<NW>(rs, rc, red);  // ends with a barrier
+        if (threadIdx.x == 0) {
+            d->part[(size_t)c * d->nblk + tile] = tot;
+            const int nxt = item + STAGES * G;
+            if (nxt < nitems) {
+                fence_proxy_async_smem();
+                issue(nxt, stage);
+            }
+        }
+        __syncthreads();  // red[] reuse
+    }
+    if (failed) {
+        // let every load already issued land (bounded) before the CTA exits
+        for (int j = 0; j < STAGES; ++j) {
+            const int kk = k + j;
+            if (blockIdx.x + kk * G < nitems)
+                mbar_wait_bounded(&bar[kk % STAGES], (kk / STAGES) & 1, kWaitLimitCycles);
+        }
+        if (threadIdx.x == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
+    }
+    arrive_and_finish(d, st, &s_last);
 }
 
 // ------------------------------------------------------------ small kernels
@@ -264,6 +463,7 @@ __global__ void k_set_desc(SolveDesc *dst, SolveDesc v) {
     st->done = 0;
     st->status = 0;
     st->n_final = 0;
+    st->err = 0;
 }
 
 // J = clamp(u^n, 0, 1) and u^n copied to the caller's u when it sits in the
@@ -283,36 +483,113 @@ __global__ void k_output(const SolveDesc *__restrict__ d, float *J) {
 
 // ------------------------------------------------------------ configuration
 
+// Sweep variants.  tma = 0: generic kernel, one CTA per (tile, channel);
+// tma = 1: persistent TMA kernel with `stages` items in flight per CTA.
 struct SweepCfg {
-    int R, NW;
+    int R, NW, stages, tma;  // tma: 0 generic, 1 TMA (u, Phi, lambda), 2 TMA (u) + vector loads
     bool edge;
+    int th() const { return R * NW; }
 };
 
+constexpr int kMinTileH = 16;  // smallest tile height any variant uses
+
+int sweep_depth(const dh_params *) { return 1; }
+int sweep_tile_h(int) { return kMinTileH; }
+
 typedef void (*SweepFn)(const SolveDesc *);
+typedef void (*SweepTmaFn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const SolveDesc *);
 
 static SweepFn sweep_fn(int R, int NW, bool edge) {
-#define DH_SW(r, nw)                                              \
+#define DH_SW(r, nw) \
     if (R == r && NW == nw) return edge ? k_sweep<r, nw, true> : k_sweep<r, nw, false>;
-    DH_SW(16, 4)
     DH_SW(8, 4)
-    DH_SW(16, 2)
+    DH_SW(16, 4)
     DH_SW(8, 8)
 #undef DH_SW
     return nullptr;
 }
 
-int sweep_depth(const dh_params *) { return 1; }
-int sweep_tile_h(int) { return 16 * 4; }
+static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge) {
+#define DH_ST(r, nw, st, pls)                                                                   \
+    if (R == r && NW == nw && stages == st && tma == (pls ? 1 : 2))                              \
+        return edge ? (SweepTmaFn)k_sweep_tma<r, nw, st, pls, true>                             \
+                    : (SweepTmaFn)k_sweep_tma<r, nw, st, pls, false>;
+    DH_ST(8, 4, 2, true)
+    DH_ST(8, 4, 1, true)
+    DH_ST(4, 8, 2, true)
+    DH_ST(4, 8, 1, true)
+    DH_ST(8, 4, 1, false)
+    DH_ST(8, 4, 2, false)
+    DH_ST(4, 8, 1, false)
+    DH_ST(4, 8, 2, false)
+    DH_ST(16, 4, 1, false)
+    DH_ST(8, 8, 1, false)
+    DH_ST(16, 2, 2, false)
+#undef DH_ST
+    return nullptr;
+}
+
+static uint32_t tma_smem_bytes(int th, int stages, int tma) {
+    const uint32_t SW = kTW + 8, SH = th + 4;
+    const uint32_t ub = SH * SW * 4, pb = tma == 1 ? th * kTW * 4 : 0;
+    const uint32_t phi_off = (ub + 1023) / 1024 * 1024;
+    const uint32_t stage = (phi_off + 2 * pb + 1023) / 1024 * 1024;
+    return stages * stage + 1024;
+}
+
+// DH_SWEEP="R,NW,STAGES,TMA" overrides the default variant (for tuning).
+static SweepCfg pick_cfg(const dh_params *p, bool tma_ok) {
+    SweepCfg c{8, 4, 1, tma_ok ? 1 : 0, !(p->variant & DH_VAR_NO_EDGE)};
+    if (const char *e = std::getenv("DH_SWEEP")) {
+        int r, nw, st, t;
+        if (std::sscanf(e, "%d,%d,%d,%d", &r, &nw, &st, &t) == 4) {
+            c.R = r;
+            c.NW = nw;
+            c.stages = st;
+            c.tma = tma_ok ? t : 0;
+        }
+    }
+    if (!c.tma && !sweep_fn(c.R, c.NW, c.edge)) { c.R = 8; c.NW = 4; }
+    return c;
+}
+
+// ------------------------------------------------------------ tensor maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::mutex g_enc_mu;
+
+int encode_f32_map(CUtensorMap *m, const void *base, int rank, int W, int H, int C, int boxW, int boxH) {
+    {
+        std::lock_guard<std::mutex> lk(g_enc_mu);
+        if (!g_encode) {
+            void *fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                             cudaEnableDefault, &q);
+            if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cuda_fail(e);
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        }
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)C};
+    cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)W * H * 4};
+    cuuint32_t box[3] = {(cuuint32_t)boxW, (cuuint32_t)boxH, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void *>(base), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? DH_OK : DH_EINVAL;
+}
 
 // ------------------------------------------------------------ graph cache
 
 struct GraphKey {
     int dev;
     const void *ws;
-    int H, W, R, NW, edge;
+    const void *ptrs[4];
+    int H, W, R, NW, stages, tma, edge;
     bool operator==(const GraphKey &o) const {
-        return dev == o.dev && ws == o.ws && H == o.H && W == o.W && R == o.R && NW == o.NW &&
-               edge == o.edge;
+        return dev == o.dev && ws == o.ws && std::memcmp(ptrs, o.ptrs, sizeof(ptrs)) == 0 && H == o.H &&
+               W == o.W && R == o.R && NW == o.NW && stages == o.stages && tma == o.tma && edge == o.edge;
     }
 };
 
@@ -328,10 +605,16 @@ static std::vector<GraphEntry> g_cache;
 static unsigned long long g_clock = 0;
 constexpr size_t kGraphCacheMax = 16;
 
+struct LaunchSpec {
+    void *func;
+    dim3 grid, block;
+    unsigned smem;
+    void **args;
+};
+
 // A graph holding one while node whose body is the sweep kernel; the sweep's
-// last CTA sets the condition to 0 when the loop has to stop.
-static int get_loop_graph(const GraphKey &key, dim3 grid, dim3 block, const SolveDesc *desc_dev,
-                          SweepFn fn, GraphEntry *out) {
+// last CTA keeps the condition at 1 while the loop has to go on.
+static int get_loop_graph(const GraphKey &key, const LaunchSpec &ls, GraphEntry *out) {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto &e : g_cache)
         if (e.key == key) {
@@ -355,12 +638,11 @@ static int get_loop_graph(const GraphKey &key, dim3 grid, dim3 block, const Solv
     if (err == cudaSuccess) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         cudaKernelNodeParams kp = {};
-        void *args[] = {(void *)&desc_dev};
-        kp.func = (void *)fn;
-        kp.gridDim = grid;
-        kp.blockDim = block;
-        kp.sharedMemBytes = 0;
-        kp.kernelParams = args;
+        kp.func = ls.func;
+        kp.gridDim = ls.grid;
+        kp.blockDim = ls.block;
+        kp.sharedMemBytes = ls.smem;
+        kp.kernelParams = ls.args;
         cudaGraphNode_t kn;
         err = cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp);
     }
@@ -381,6 +663,24 @@ static int get_loop_graph(const GraphKey &key, dim3 grid, dim3 block, const Solv
     return DH_OK;
 }
 
+// Resident CTAs per SM x SMs for a persistent kernel (cached per device/kernel).
+static int persistent_grid(void *func, int block, unsigned smem) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<int, void *>, int>> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto &e : cache)
+        if (e.first.first == dev && e.first.second == func) return e.second;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, block, smem) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    const int g = per_sm * sms;
+    cache.push_back({{dev, func}, g});
+    return g;
+}
+
 // ------------------------------------------------------------ the solve loop
 
 // Queues the fixed-point loop for buffers u[0] (caller's, holds u^0) and
@@ -388,12 +688,6 @@ static int get_loop_graph(const GraphKey &key, dim3 grid, dim3 block, const Solv
 int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W, const dh_params *p,
               float *rho_hist, char *ws, const WsLayout &L, cudaStream_t s, float *J,
               cudaEvent_t loop_begin, cudaEvent_t loop_end, int *launches) {
-    const SweepCfg cfg{16, 4, !(p->variant & DH_VAR_NO_EDGE)};
-    SweepFn fn = sweep_fn(cfg.R, cfg.NW, cfg.edge);
-    if (!fn) return DH_EINVAL;
-    const int TH = cfg.R * cfg.NW;
-    dim3 grid((W + kTW - 1) / kTW, (H + TH - 1) / TH, 3);
-    dim3 block(cfg.NW * 32);
     SolveDesc *desc_dev = (SolveDesc *)(ws + L.desc);
     SolveDesc v = {};
     v.u[0] = u_caller;
@@ -407,29 +701,56 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
     v.W = W;
     v.max_iter = p->max_iter;
     v.depth = 1;
-    v.nblk = grid.x * grid.y;
-    if (v.nblk > L.nblk_sweep) return DH_EINVAL;  // workspace sized for another tiling
-    {
-        auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
-        v.vec = (W % 4 == 0) && a16(u_caller) && a16(v.u[1]) && a16(phi) && a16(lam);
-    }
     v.tol = p->tol;
     v.tau = p->tau;
     v.eps = p->eps;
+    auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+    v.vec = (W % 4 == 0) && a16(u_caller) && a16(v.u[1]) && a16(phi) && a16(lam);
     {  // App. A-B-2: normalised 5-tap Gaussian, sigma = p->sigma
-        double w[3], sum = 0.0;
+        double w[3];
         for (int k = 0; k <= 2; ++k) w[k] = exp(-(double)(k * k) / (2.0 * (double)p->sigma * p->sigma));
-        sum = w[0] + 2.0 * (w[1] + w[2]);
+        const double sum = w[0] + 2.0 * (w[1] + w[2]);
         v.wg0 = (float)(w[0] / sum);
         v.wg1 = (float)(w[1] / sum);
         v.wg2 = (float)(w[2] / sum);
     }
+    const SweepCfg cfg = pick_cfg(p, v.vec != 0);
+    const int TH = cfg.th();
+    if (TH < kMinTileH) return DH_EINVAL;
+    const int ntx = (W + kTW - 1) / kTW, nty = (H + TH - 1) / TH;
+    v.nblk = ntx * nty;
+    if (v.nblk > L.nblk_sweep) return DH_EINVAL;  // workspace sized for another tiling
+
+    CUtensorMap maps[4];
+    const SolveDesc *dptr = desc_dev;
+    void *args_tma[5] = {&maps[0], &maps[1], &maps[2], &maps[3], (void *)&dptr};
+    void *args_gen[1] = {(void *)&dptr};
+    LaunchSpec ls;
+    if (cfg.tma) {
+        int rc = encode_f32_map(&maps[0], v.u[0], 3, W, H, 3, kTW + 8, TH + 4);
+        if (!rc) rc = encode_f32_map(&maps[1], v.u[1], 3, W, H, 3, kTW + 8, TH + 4);
+        if (!rc) rc = encode_f32_map(&maps[2], phi, 3, W, H, 3, kTW, TH);
+        if (!rc) rc = encode_f32_map(&maps[3], lam, 2, W, H, 1, kTW, TH);
+        if (rc) return rc;
+        SweepTmaFn fn = sweep_tma_fn(cfg.R, cfg.NW, cfg.stages, cfg.tma, cfg.edge);
+        if (!fn) return DH_EINVAL;
+        const unsigned smem = tma_smem_bytes(TH, cfg.stages, cfg.tma);
+        const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
+        if (gmax <= 0) return DH_ECUDA;
+        const int items = 3 * v.nblk;
+        ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(cfg.NW * 32), smem, args_tma};
+    } else {
+        SweepFn fn = sweep_fn(cfg.R, cfg.NW, cfg.edge);
+        if (!fn) return DH_EINVAL;
+        ls = LaunchSpec{(void *)fn, dim3(ntx, nty, 3), dim3(cfg.NW * 32), 0, args_gen};
+    }
     if (p->use_graph) {
         int dev = 0;
         DH_CUDA_TRY(cudaGetDevice(&dev));
-        GraphKey key{dev, ws, H, W, cfg.R, cfg.NW, cfg.edge ? 1 : 0};
+        GraphKey key{dev, ws, {u_caller, v.u[1], phi, lam}, H, W, cfg.R, cfg.NW, cfg.stages, cfg.tma,
+                     cfg.edge ? 1 : 0};
         GraphEntry ge;
-        int rc = get_loop_graph(key, grid, block, desc_dev, fn, &ge);
+        int rc = get_loop_graph(key, ls, &ge);
         if (rc != DH_OK) return rc;
         v.cond = ge.cond;
         v.use_cond = 1;
@@ -442,8 +763,8 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
         v.use_cond = 0;
         k_set_desc<<<1, 1, 0, s>>>(desc_dev, v);
         if (loop_begin) DH_CUDA_TRY(cudaEventRecord(loop_begin, s));
-        for (int n = 0; n <= p->max_iter; ++n) fn<<<grid, block, 0, s>>>(desc_dev);
-        DH_CUDA_TRY(cudaGetLastError());
+        for (int n = 0; n <= p->max_iter; ++n)
+            DH_CUDA_TRY(cudaLaunchKernel(ls.func, ls.grid, ls.block, ls.args, ls.smem, s));
         if (loop_end) DH_CUDA_TRY(cudaEventRecord(loop_end, s));
         if (launches) *launches += p->max_iter + 1;  // queued; finished ones exit at once
     }

@@ -19,9 +19,13 @@ def main():
     ap.add_argument("--iters", type=int, default=8)
     ap.add_argument("--preset", default="stable")
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--host-loop", action="store_true",
+                    help="queue the sweeps from the host instead of the graph loop (profilers cannot "
+                         "see kernels inside a graph with conditional nodes)")
     a = ap.parse_args()
     I = torch.from_numpy(scenes.hazy_scene(a.seed, a.H, a.W)["I"]).cuda()
-    d = api.Dehazer(a.H, a.W, api.params(a.preset, tol=0.0, max_iter=a.iters))
+    d = api.Dehazer(a.H, a.W, api.params(a.preset, tol=0.0, max_iter=a.iters,
+                                                   use_graph=0 if a.host_loop else 1))
     for _ in range(a.repeat):
         rep = d(I)
     torch.cuda.synchronize()

@@ -225,6 +225,23 @@ def test_graph_and_host_loop_identical_and_resume_exact(N, api, orc):
     assert np.array_equal(host(u), outs[0])
 
 
+@pytest.mark.parametrize("H,W", [(64, 128), (100, 260), (33, 4), (300, 516)])
+def test_sweep_variants_bit_identical(N, api, orc, H, W, monkeypatch):
+    """The TMA kernel (every tiling) and the generic kernel compute each pixel
+    with the same float32 arithmetic, so their iterates agree bit for bit."""
+    _, _, Phi, lam = _problem(orc, 31 + H, H, W, "stable")
+    outs = {}
+    for cfg in ("8,4,2,0", "8,4,2,1", "8,4,1,1", "4,8,2,1", "8,4,1,2", "4,8,2,2", "16,4,1,2", "16,4,2,0"):
+        monkeypatch.setenv("DH_SWEEP", cfg)
+        u = dev(Phi.copy())
+        rep, _ = api.fixed_point(u, dev(Phi), dev(lam), api.params("stable", tol=0.0, max_iter=12))
+        assert rep.n_iter == 12
+        outs[cfg] = host(u)
+    ref = outs["8,4,2,0"]
+    for cfg, u in outs.items():
+        assert np.array_equal(u, ref), cfg
+
+
 def test_nonfinite_input_reported(N, api):
     I = scenes.hazy_scene(3, 64, 64)["I"].copy()
     I[1, 10, 10] = np.nan
