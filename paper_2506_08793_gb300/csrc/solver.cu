@@ -141,72 +141,134 @@ __device__ __forceinline__ float2 block_pair_sum(float rs, float rc, float2 *red
     return make_float2(a, b);
 }
 
+// Packed float32 pairs (Blackwell f32x2 ALU ops).  Each lane of a pair is an
+// IEEE round-to-nearest operation, the same as the scalar __f*_rn / fmaf.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " add.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mul.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 r;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+        " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}"
+        : "=f"(r.x), "=f"(r.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+
+// face_flux on two faces at once (same rounding as the scalar form)
+template <bool EDGE>
+__device__ __forceinline__ float2 face_flux2(float2 a, float2 b, float2 eps2) {
+    if (!EDGE) return a;
+    const float2 s = fma2(a, a, mul2(b, b));
+    const float2 q = add2(make_float2(sqrt_approx(s.x), sqrt_approx(s.y)), eps2);
+    return mul2(a, make_float2(rcp_approx(q.x), rcp_approx(q.y)));
+}
+
+// One row of u for a lane, as the pairs the stencil needs: odd pairs
+// o0 = (x-1, x), o1 = (x+1, x+2), o2 = (x+3, x+4) and even pairs
+// e1 = (x, x+1), e2 = (x+2, x+3).
+struct RowU {
+    float2 o0, e1, o1, e2, o2;
+};
+
 // One warp's walk over tile rows [r0, r0+R) for its lane's 4 columns.
 // `s` is the u^n tile in shared memory: row stride SW floats, tile row ty at
 // smem row ty+2, the lane's first column at smem column 4*lane+4.  Every x-
 // and y-face flux and every horizontally filtered row is computed once and
-// kept in rolling registers.  pl(ty, ph, la) supplies Phi and lambda for the
-// row; sink(ty, nu, F) consumes u^{n+1} and F.
+// kept in rolling registers; arithmetic runs on float32 pairs.
+// pl(ty, ph, la) supplies Phi and lambda for the row; sink(ty, nu, F)
+// consumes u^{n+1} and F.
 template <int R, int SW, bool EDGE, class PL, class SINK>
 __device__ __forceinline__ void walk_rows(const float *__restrict__ s, int r0, int lane, float eps, float tau,
                                           float wg0, float wg1, float wg2, PL pl, SINK sink) {
     const int sc = 4 * lane;
-    float uu[4][6];  // u at tile rows r0-1+k (mod 4), columns x-1 .. x+4
-    float gh[5][4];  // horizontal Gaussian at tile rows r0-2+k (mod 5), columns x .. x+3
-    float fyu[4];    // y-face flux above the current row
+    const float2 W0 = make_float2(wg0, wg0), W1 = make_float2(wg1, wg1), W2 = make_float2(wg2, wg2);
+    const float2 E2 = make_float2(eps, eps), HALF = make_float2(0.5f, 0.5f), TAU = make_float2(tau, tau);
+    const float2 MONE = make_float2(-1.f, -1.f);
+    RowU uu[4];       // u at tile rows r0-1+k (mod 4)
+    float2 gh[5][2];  // horizontal Gaussian at tile rows r0-2+k (mod 5), columns (x, x+1), (x+2, x+3)
+    float2 fyu[2];    // y-face fluxes above the current row
 
-    auto load_row = [&](int tr, float *v6, float *g4) {
+    auto gauss = [&](float2 m2, float2 m1, float2 c0, float2 p1, float2 p2) {
+        return fma2(W2, add2(m2, p2), fma2(W1, add2(m1, p1), mul2(W0, c0)));
+    };
+    auto load_row = [&](int tr, RowU &u, float2 *g) {
         const float *row = s + (tr + 2) * SW + sc;
         const float4 L = *reinterpret_cast<const float4 *>(row);
         const float4 C = *reinterpret_cast<const float4 *>(row + 4);
         const float4 Rr = *reinterpret_cast<const float4 *>(row + 8);
-        const float v[8] = {L.z, L.w, C.x, C.y, C.z, C.w, Rr.x, Rr.y};  // x-2 .. x+5
-#pragma unroll
-        for (int j = 0; j < 4; ++j) g4[j] = gauss5(v[j], v[j + 1], v[j + 2], v[j + 3], v[j + 4], wg0, wg1, wg2);
-        if (v6) {
-#pragma unroll
-            for (int j = 0; j < 6; ++j) v6[j] = v[j + 1];
-        }
+        const float2 e0 = make_float2(L.z, L.w), e3 = make_float2(Rr.x, Rr.y);
+        u.o0 = make_float2(L.w, C.x);
+        u.e1 = make_float2(C.x, C.y);
+        u.o1 = make_float2(C.y, C.z);
+        u.e2 = make_float2(C.z, C.w);
+        u.o2 = make_float2(C.w, Rr.x);
+        g[0] = gauss(e0, u.o0, u.e1, u.o1, u.e2);
+        g[1] = gauss(u.e1, u.o1, u.e2, u.o2, e3);
+    };
+    // y-face fluxes below row `a` (between a and b), tangential difference on row a
+    auto yfaces = [&](const RowU &a, const RowU &b, float2 *f) {
+        f[0] = face_flux2<EDGE>(sub2(b.e1, a.e1), mul2(HALF, sub2(a.o1, a.o0)), E2);
+        f[1] = face_flux2<EDGE>(sub2(b.e2, a.e2), mul2(HALF, sub2(a.o2, a.o1)), E2);
     };
 
     {
-        float dummy[6];
+        RowU dummy;
         load_row(r0 - 2, dummy, gh[0]);
         load_row(r0 - 1, uu[0], gh[1]);
         load_row(r0, uu[1], gh[2]);
         load_row(r0 + 1, uu[2], gh[3]);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)  // y-face at r0 - 1/2, tangential difference on row r0-1
-            fyu[j] = face_flux<EDGE>(__fsub_rn(uu[1][j + 1], uu[0][j + 1]), half_diff(uu[0][j + 2], uu[0][j]), eps);
+        yfaces(uu[0], uu[1], fyu);  // y-face at r0 - 1/2
     }
 
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const int ty = r0 + i;
-        float *um = uu[(i + 0) & 3];
-        float *u0 = uu[(i + 1) & 3];
-        float *up = uu[(i + 2) & 3];
-        float *upp = uu[(i + 3) & 3];
-        load_row(ty + 2, upp, gh[(i + 4) % 5]);
-        const float *g_m2 = gh[(i + 0) % 5], *g_m1 = gh[(i + 1) % 5], *g_0 = gh[(i + 2) % 5];
-        const float *g_p1 = gh[(i + 3) % 5], *g_p2 = gh[(i + 4) % 5];
+        const RowU &um = uu[(i + 0) & 3];
+        const RowU &u0 = uu[(i + 1) & 3];
+        const RowU &up = uu[(i + 2) & 3];
+        load_row(ty + 2, uu[(i + 3) & 3], gh[(i + 4) % 5]);
+        const float2 *g_m2 = gh[(i + 0) % 5], *g_m1 = gh[(i + 1) % 5], *g_0 = gh[(i + 2) % 5];
+        const float2 *g_p1 = gh[(i + 3) % 5], *g_p2 = gh[(i + 4) % 5];
         float ph[4], la[4];
         pl(ty, ph, la);
-        // x-faces at x-1/2 .. x+3+1/2, tangential difference at the face's left cell
-        float fx[5];
-#pragma unroll
-        for (int j = 0; j < 5; ++j)
-            fx[j] = face_flux<EDGE>(__fsub_rn(u0[j + 1], u0[j]), half_diff(up[j], um[j]), eps);
-        float nu[4], F[4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float fyd = face_flux<EDGE>(__fsub_rn(up[j + 1], u0[j + 1]), half_diff(u0[j + 2], u0[j]), eps);
-            const float G = gauss5(g_m2[j], g_m1[j], g_0[j], g_p1[j], g_p2[j], wg0, wg1, wg2);
-            const float dv = __fadd_rn(__fsub_rn(fx[j + 1], fx[j]), __fsub_rn(fyd, fyu[j]));
-            F[j] = __fadd_rn(fmaf(-la[j], G, dv), ph[j]);
-            nu[j] = fmaf(tau, F[j], u0[j + 1]);
-            fyu[j] = fyd;
-        }
+        // x-faces (x-1/2, x+1/2), (x+3/2, x+5/2) and x+7/2; tangential difference at the left cell
+        const float2 fxA = face_flux2<EDGE>(sub2(u0.e1, u0.o0), mul2(HALF, sub2(up.o0, um.o0)), E2);
+        const float2 fxB = face_flux2<EDGE>(sub2(u0.e2, u0.o1), mul2(HALF, sub2(up.o1, um.o1)), E2);
+        const float fx4 = face_flux<EDGE>(__fsub_rn(u0.o2.y, u0.o2.x), half_diff(up.o2.x, um.o2.x), eps);
+        float2 fyd[2];
+        yfaces(u0, up, fyd);
+        const float2 dxA = make_float2(__fsub_rn(fxA.y, fxA.x), __fsub_rn(fxB.x, fxA.y));
+        const float2 dxB = make_float2(__fsub_rn(fxB.y, fxB.x), __fsub_rn(fx4, fxB.y));
+        const float2 dvA = add2(dxA, sub2(fyd[0], fyu[0]));
+        const float2 dvB = add2(dxB, sub2(fyd[1], fyu[1]));
+        const float2 GA = gauss(g_m2[0], g_m1[0], g_0[0], g_p1[0], g_p2[0]);
+        const float2 GB = gauss(g_m2[1], g_m1[1], g_0[1], g_p1[1], g_p2[1]);
+        const float2 FA = add2(fma2(mul2(MONE, make_float2(la[0], la[1])), GA, dvA), make_float2(ph[0], ph[1]));
+        const float2 FB = add2(fma2(mul2(MONE, make_float2(la[2], la[3])), GB, dvB), make_float2(ph[2], ph[3]));
+        const float2 nA = fma2(TAU, FA, u0.e1);
+        const float2 nB = fma2(TAU, FB, u0.e2);
+        fyu[0] = fyd[0];
+        fyu[1] = fyd[1];
+        const float nu[4] = {nA.x, nA.y, nB.x, nB.y};
+        const float F[4] = {FA.x, FA.y, FB.x, FB.y};
         sink(ty, nu, F);
     }
 }
@@ -363,6 +425,10 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
+    const float *__restrict__ phi_all = d->phi;
+    const float *__restrict__ glam = d->lam;
+    float2 *__restrict__ part = d->part;
+    const int nblk = d->nblk;
     int k = 0;
     bool failed = false;
     for (int item = blockIdx.x; item < nitems; item += G, ++k) {
@@ -400,8 +466,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
         float *__restrict__ un = ubase + c * N;
         const int x = x0 + 4 * lane;
         float rs = 0.f, rc = 0.f;
-        const float *__restrict__ gphi = d->phi + c * N;
-        const float *__restrict__ glam = d->lam;
+        const float *__restrict__ gphi = phi_all + c * N;
         auto pl = [&](int ty, float *ph, float *la) {
             float4 p4, l4;
             if (PL_SMEM) {
@@ -431,7 +496,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
 
         const float2 tot = block_pair_sum<NW>(rs, rc, red);  // ends with a barrier
         if (threadIdx.x == 0) {
-            d->part[(size_t)c * d->nblk + tile] = tot;
+            part[(size_t)c * nblk + tile] = tot;
             const int nxt = item + STAGES * G;
             if (nxt < nitems) {
                 fence_proxy_async_smem();
