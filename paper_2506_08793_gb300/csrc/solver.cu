@@ -517,6 +517,223 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     arrive_and_finish(d, st, &s_last);
 }
 
+// Streaming sweep (W % 4 == 0, 16-byte aligned planes).  Each warp owns
+// segments of a 128-column strip of one channel (tasks) and walks their rows
+// top to bottom.  Lane 0 streams rows into a per-warp ring of NSLOT row slots
+// (u with a 4-column halo, Phi, lambda), one TMA load per array and row, one
+// mbarrier per slot, refilling a slot as soon as the walk has consumed it.
+// The vertical reflecting boundary is applied by loading the reflected row,
+// the horizontal one by substituting the reflected columns in registers.
+// Rows are unrolled in blocks of 20 (the period of the 4- and 5-row register
+// rings), so a segment is a multiple of 20 rows.
+constexpr int kStreamUnroll = 20;
+constexpr uint32_t kRowU = (kTW + 8) * 4;     // 544 bytes
+constexpr uint32_t kRowPhiOff = 640;          // 128-byte aligned offsets in a slot
+constexpr uint32_t kRowLamOff = 1152;
+constexpr uint32_t kRowBytes = 1664;
+
+template <int NW, int NSLOT, bool EDGE>
+__global__ void __launch_bounds__(NW * 32)
+k_sweep_stream(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
+               const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
+               const SolveDesc *__restrict__ d, int seg) {
+    static_assert(NSLOT >= 4 && (NSLOT & (NSLOT - 1)) == 0, "NSLOT: power of two >= 4");
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bars[NW][NSLOT];
+    __shared__ int s_last;
+
+    SolveState *st = d->st;
+    clear_condition(d);
+    if (__ldcg(&st->done)) return;
+    const int H = d->H, W = d->W;
+    const int cur = __ldcg(&st->cur);
+    const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
+    float *__restrict__ ubase = d->u[cur ^ 1];
+    const size_t N = (size_t)H * W;
+    const int ntx = (W + kTW - 1) / kTW;
+    const int nseg = (H + seg - 1) / seg;
+    const int ntasks = 3 * ntx * nseg;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int gw = blockIdx.x * NW + w, GW = gridDim.x * NW;
+    const int mytasks = gw < ntasks ? (ntasks - 1 - gw) / GW + 1 : 0;
+    const int P = seg + 4;  // stream positions per task: u rows y0-2 .. y0+seg+1
+    const int total = mytasks * P;
+    unsigned char *ring = smem + (size_t)w * NSLOT * kRowBytes;
+    uint64_t *bar = bars[w];
+    const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
+    float2 *__restrict__ part = d->part;
+    const int nblk = d->nblk;
+
+    if (lane == 0) {
+        for (int k = 0; k < NSLOT; ++k) mbar_init(&bar[k], 1);
+        fence_mbar_init();
+    }
+    __syncwarp();
+
+    // task k of this warp -> (channel, strip, segment)
+    auto task_of = [&](int k, int &c, int &x0, int &y0, int &tile) {
+        const int t = gw + k * GW;
+        c = t % 3;
+        const int r = t / 3;
+        tile = r;
+        x0 = (r % ntx) * kTW;
+        y0 = (r / ntx) * seg;
+    };
+    // Lane 0's issue cursor: positions are issued strictly in order, one per
+    // released slot, so the (task, row) of the next position is advanced
+    // incrementally.
+    int iss_pos = 0, iss_k = 0, iss_o = 0, iss_c = 0, iss_x0 = 0, iss_y0 = 0, iss_tile = 0;
+    if (mytasks > 0) task_of(0, iss_c, iss_x0, iss_y0, iss_tile);
+    auto issue_next = [&]() {  // lane 0 only
+        if (iss_pos >= total) return;
+        const int Y = reflect_idx(iss_y0 - 2 + iss_o, H);
+        const bool pl = iss_o >= 2 && iss_o < seg + 2;
+        const int slot = iss_pos & (NSLOT - 1);
+        unsigned char *sb = ring + slot * kRowBytes;
+        mbar_arrive_expect_tx(&bar[slot], kRowU + (pl ? 2 * kTW * 4 : 0));
+        tma_load_3d(sb, tm_u, &bar[slot], iss_x0 - 4, Y, iss_c);
+        if (pl) {
+            tma_load_3d(sb + kRowPhiOff, &tm_phi, &bar[slot], iss_x0, Y, iss_c);
+            tma_load_2d(sb + kRowLamOff, &tm_lam, &bar[slot], iss_x0, Y);
+        }
+        ++iss_pos;
+        if (++iss_o == P) {
+            iss_o = 0;
+            if (++iss_k < mytasks) task_of(iss_k, iss_c, iss_x0, iss_y0, iss_tile);
+        }
+    };
+    if (lane == 0)
+        for (int k = 0; k < NSLOT; ++k) issue_next();
+
+    bool failed = false;
+    int waited = 0;  // positions [0, waited) have been waited for
+    auto wait_pos = [&](int pos) -> const unsigned char * {
+        const int slot = pos & (NSLOT - 1);
+        const uint32_t parity = (uint32_t)((pos / NSLOT) & 1);
+        const bool ok = mbar_wait_bounded(&bar[slot], parity, kWaitLimitCycles);
+        if (__any_sync(0xffffffffu, !ok)) failed = true;
+        waited = pos + 1;
+        return ring + slot * kRowBytes;
+    };
+    // The walk is done with the oldest slot in use: refill it with the next position.
+    auto release = [&]() {
+        __syncwarp();
+        if (lane == 0) {
+            fence_proxy_async_smem();
+            issue_next();
+        }
+    };
+
+    const float2 W0 = make_float2(wg0, wg0), W1 = make_float2(wg1, wg1), W2 = make_float2(wg2, wg2);
+    const float2 E2 = make_float2(eps, eps), HALF = make_float2(0.5f, 0.5f), TAU = make_float2(tau, tau);
+    const float2 MONE = make_float2(-1.f, -1.f);
+    auto gauss = [&](float2 m2, float2 m1, float2 c0, float2 p1, float2 p2) {
+        return fma2(W2, add2(m2, p2), fma2(W1, add2(m1, p1), mul2(W0, c0)));
+    };
+
+    for (int k = 0; k < mytasks && !failed; ++k) {
+        int c, x0, y0, tile;
+        task_of(k, c, x0, y0, tile);
+        const int p0 = k * P;
+        const int x = x0 + 4 * lane;
+        const bool left = x == 0, right = x + 4 == W;
+        auto load_row = [&](const unsigned char *sb, RowU &u, float2 *g) {
+            const float *row = reinterpret_cast<const float *>(sb) + 4 * lane;
+            float4 L = *reinterpret_cast<const float4 *>(row);
+            const float4 C = *reinterpret_cast<const float4 *>(row + 4);
+            float4 Rr = *reinterpret_cast<const float4 *>(row + 8);
+            if (left) { L.z = C.y; L.w = C.x; }     // u(-2) = u(1), u(-1) = u(0)
+            if (right) { Rr.x = C.w; Rr.y = C.z; }  // u(W) = u(W-1), u(W+1) = u(W-2)
+            const float2 e0 = make_float2(L.z, L.w), e3 = make_float2(Rr.x, Rr.y);
+            u.o0 = make_float2(L.w, C.x);
+            u.e1 = make_float2(C.x, C.y);
+            u.o1 = make_float2(C.y, C.z);
+            u.e2 = make_float2(C.z, C.w);
+            u.o2 = make_float2(C.w, Rr.x);
+            g[0] = gauss(e0, u.o0, u.e1, u.o1, u.e2);
+            g[1] = gauss(u.e1, u.o1, u.e2, u.o2, e3);
+        };
+        auto yfaces = [&](const RowU &a, const RowU &b, float2 *f) {
+            f[0] = face_flux2<EDGE>(sub2(b.e1, a.e1), mul2(HALF, sub2(a.o1, a.o0)), E2);
+            f[1] = face_flux2<EDGE>(sub2(b.e2, a.e2), mul2(HALF, sub2(a.o2, a.o1)), E2);
+        };
+        RowU uu[4];
+        float2 gh[5][2];
+        float2 fyu[2];
+        {
+            RowU dummy;
+            load_row(wait_pos(p0 + 0), dummy, gh[0]);
+            load_row(wait_pos(p0 + 1), uu[0], gh[1]);
+            load_row(wait_pos(p0 + 2), uu[1], gh[2]);
+            load_row(wait_pos(p0 + 3), uu[2], gh[3]);
+            yfaces(uu[0], uu[1], fyu);
+            release();  // rows y0-2, y0-1 carry no Phi/lambda: done with them
+            release();
+        }
+        if (failed) break;
+        float rs = 0.f, rc = 0.f;
+        float *__restrict__ un = ubase + c * N;
+        for (int m = 0; m < seg; m += kStreamUnroll) {
+#pragma unroll
+            for (int j = 0; j < kStreamUnroll; ++j) {
+                const int i = m + j;
+                const RowU &um = uu[(j + 0) & 3];
+                const RowU &u0 = uu[(j + 1) & 3];
+                const RowU &up = uu[(j + 2) & 3];
+                load_row(wait_pos(p0 + 4 + i), uu[(j + 3) & 3], gh[(j + 4) % 5]);
+                const unsigned char *sbo = ring + ((p0 + 2 + i) & (NSLOT - 1)) * kRowBytes;
+                const float4 p4 = *reinterpret_cast<const float4 *>(sbo + kRowPhiOff + 16 * lane);
+                const float4 l4 = *reinterpret_cast<const float4 *>(sbo + kRowLamOff + 16 * lane);
+                const float2 *g_m2 = gh[(j + 0) % 5], *g_m1 = gh[(j + 1) % 5], *g_0 = gh[(j + 2) % 5];
+                const float2 *g_p1 = gh[(j + 3) % 5], *g_p2 = gh[(j + 4) % 5];
+                const float2 fxA = face_flux2<EDGE>(sub2(u0.e1, u0.o0), mul2(HALF, sub2(up.o0, um.o0)), E2);
+                const float2 fxB = face_flux2<EDGE>(sub2(u0.e2, u0.o1), mul2(HALF, sub2(up.o1, um.o1)), E2);
+                const float fx4 = face_flux<EDGE>(__fsub_rn(u0.o2.y, u0.o2.x), half_diff(up.o2.x, um.o2.x), eps);
+                float2 fyd[2];
+                yfaces(u0, up, fyd);
+                const float2 dxA = make_float2(__fsub_rn(fxA.y, fxA.x), __fsub_rn(fxB.x, fxA.y));
+                const float2 dxB = make_float2(__fsub_rn(fxB.y, fxB.x), __fsub_rn(fx4, fxB.y));
+                const float2 dvA = add2(dxA, sub2(fyd[0], fyu[0]));
+                const float2 dvB = add2(dxB, sub2(fyd[1], fyu[1]));
+                const float2 GA = gauss(g_m2[0], g_m1[0], g_0[0], g_p1[0], g_p2[0]);
+                const float2 GB = gauss(g_m2[1], g_m1[1], g_0[1], g_p1[1], g_p2[1]);
+                const float2 FA = add2(fma2(mul2(MONE, make_float2(l4.x, l4.y)), GA, dvA), make_float2(p4.x, p4.y));
+                const float2 FB = add2(fma2(mul2(MONE, make_float2(l4.z, l4.w)), GB, dvB), make_float2(p4.z, p4.w));
+                const float2 nA = fma2(TAU, FA, u0.e1);
+                const float2 nB = fma2(TAU, FB, u0.e2);
+                fyu[0] = fyd[0];
+                fyu[1] = fyd[1];
+                const int y = y0 + i;
+                if (y < H && x < W) {
+                    const float2 q2 = fma2(FB, FB, mul2(FA, FA));
+                    neumaier_add(rs, rc, __fadd_rn(q2.x, q2.y));
+                    *reinterpret_cast<float4 *>(un + (size_t)y * W + x) = make_float4(nA.x, nA.y, nB.x, nB.y);
+                }
+                release();
+            }
+            if (failed) break;
+        }
+        if (failed) break;
+        release();  // look-ahead rows of the segment's end
+        release();
+        for (int off = 16; off; off >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, rs, off);
+            const float c2 = __shfl_down_sync(0xffffffffu, rc, off);
+            neumaier_merge(rs, rc, s2, c2);
+        }
+        if (lane == 0) part[(size_t)c * nblk + tile] = make_float2(rs, rc);
+    }
+    if (failed) {
+        // let the loads this warp still has in flight land (bounded), then report
+        const int issued = __shfl_sync(0xffffffffu, iss_pos, 0);
+        for (int pos = waited; pos < issued; ++pos)
+            mbar_wait_bounded(&bar[pos & (NSLOT - 1)], (uint32_t)((pos / NSLOT) & 1), kWaitLimitCycles);
+        if (lane == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
+    }
+    arrive_and_finish(d, st, &s_last);
+}
+
 // ------------------------------------------------------------ small kernels
 
 __global__ void k_set_desc(SolveDesc *dst, SolveDesc v) {
@@ -594,6 +811,39 @@ static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge) {
     return nullptr;
 }
 
+typedef void (*SweepStreamFn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const SolveDesc *, int);
+
+static SweepStreamFn sweep_stream_fn(int NW, int NSLOT, bool edge) {
+#define DH_SS(nw, ns) \
+    if (NW == nw && NSLOT == ns) return edge ? k_sweep_stream<nw, ns, true> : k_sweep_stream<nw, ns, false>;
+    DH_SS(4, 8)
+    DH_SS(8, 8)
+    DH_SS(4, 16)
+    DH_SS(2, 8)
+    DH_SS(8, 4)
+#undef DH_SS
+    return nullptr;
+}
+
+// Segment height (a multiple of the 20-row unroll) that minimises the waves of
+// (channel, strip, segment) tasks over `warps` resident warps.
+static int stream_segment(int H, int ntx, int warps) {
+    int best_seg = kStreamUnroll, best_cost = 0x7fffffff;
+    const int max_n = (H + kStreamUnroll - 1) / kStreamUnroll;
+    for (int n = 1; n <= max_n; ++n) {
+        const int seg = kStreamUnroll * ((H + kStreamUnroll * n - 1) / (kStreamUnroll * n));
+        const int nseg = (H + seg - 1) / seg;
+        const long long tasks = 3LL * ntx * nseg;
+        const long long waves = (tasks + warps - 1) / warps;
+        const long long cost = waves * (seg + 4);
+        if (cost < best_cost || (cost == best_cost && seg > best_seg)) {
+            best_cost = (int)cost;
+            best_seg = seg;
+        }
+    }
+    return best_seg;
+}
+
 static uint32_t tma_smem_bytes(int th, int stages, int tma) {
     const uint32_t SW = kTW + 8, SH = th + 4;
     const uint32_t ub = SH * SW * 4, pb = tma == 1 ? th * kTW * 4 : 0;
@@ -602,7 +852,8 @@ static uint32_t tma_smem_bytes(int th, int stages, int tma) {
     return stages * stage + 1024;
 }
 
-// DH_SWEEP="R,NW,STAGES,TMA" overrides the default variant (for tuning).
+// DH_SWEEP="R,NW,STAGES,TMA" overrides the default variant (for tuning);
+// TMA = 3 selects the streaming kernel with R = ring slots per warp.
 static SweepCfg pick_cfg(const dh_params *p, bool tma_ok) {
     SweepCfg c{8, 4, 1, tma_ok ? 1 : 0, !(p->variant & DH_VAR_NO_EDGE)};
     if (const char *e = std::getenv("DH_SWEEP")) {
@@ -615,6 +866,7 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok) {
         }
     }
     if (!c.tma && !sweep_fn(c.R, c.NW, c.edge)) { c.R = 8; c.NW = 4; }
+    if (!c.tma) c.stages = 1;
     return c;
 }
 
@@ -780,18 +1032,38 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
         v.wg2 = (float)(w[2] / sum);
     }
     const SweepCfg cfg = pick_cfg(p, v.vec != 0);
-    const int TH = cfg.th();
-    if (TH < kMinTileH) return DH_EINVAL;
-    const int ntx = (W + kTW - 1) / kTW, nty = (H + TH - 1) / TH;
-    v.nblk = ntx * nty;
-    if (v.nblk > L.nblk_sweep) return DH_EINVAL;  // workspace sized for another tiling
-
+    const int ntx = (W + kTW - 1) / kTW;
     CUtensorMap maps[4];
     const SolveDesc *dptr = desc_dev;
+    int seg = 0;
     void *args_tma[5] = {&maps[0], &maps[1], &maps[2], &maps[3], (void *)&dptr};
+    void *args_stream[6] = {&maps[0], &maps[1], &maps[2], &maps[3], (void *)&dptr, (void *)&seg};
     void *args_gen[1] = {(void *)&dptr};
     LaunchSpec ls;
-    if (cfg.tma) {
+    if (cfg.tma == 3) {
+        // per-warp row streams over (channel, 128-column strip, segment) tasks
+        int rc = encode_f32_map(&maps[0], v.u[0], 3, W, H, 3, kTW + 8, 1);
+        if (!rc) rc = encode_f32_map(&maps[1], v.u[1], 3, W, H, 3, kTW + 8, 1);
+        if (!rc) rc = encode_f32_map(&maps[2], phi, 3, W, H, 3, kTW, 1);
+        if (!rc) rc = encode_f32_map(&maps[3], lam, 2, W, H, 1, kTW, 1);
+        if (rc) return rc;
+        SweepStreamFn fn = sweep_stream_fn(cfg.NW, cfg.R, cfg.edge);
+        if (!fn) return DH_EINVAL;
+        const unsigned smem = cfg.NW * cfg.R * kRowBytes + 1024;
+        const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
+        if (gmax <= 0) return DH_ECUDA;
+        seg = stream_segment(H, ntx, gmax * cfg.NW);
+        const int nseg = (H + seg - 1) / seg;
+        v.nblk = ntx * nseg;
+        if (v.nblk > L.nblk_sweep) return DH_EINVAL;
+        const int tasks = 3 * v.nblk;
+        const int g = (tasks + cfg.NW - 1) / cfg.NW;
+        ls = LaunchSpec{(void *)fn, dim3(g < gmax ? g : gmax), dim3(cfg.NW * 32), smem, args_stream};
+    } else if (cfg.tma) {
+        const int TH = cfg.th();
+        if (TH < kMinTileH) return DH_EINVAL;
+        v.nblk = ntx * ((H + TH - 1) / TH);
+        if (v.nblk > L.nblk_sweep) return DH_EINVAL;  // workspace sized for another tiling
         int rc = encode_f32_map(&maps[0], v.u[0], 3, W, H, 3, kTW + 8, TH + 4);
         if (!rc) rc = encode_f32_map(&maps[1], v.u[1], 3, W, H, 3, kTW + 8, TH + 4);
         if (!rc) rc = encode_f32_map(&maps[2], phi, 3, W, H, 3, kTW, TH);
@@ -805,6 +1077,11 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
         const int items = 3 * v.nblk;
         ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(cfg.NW * 32), smem, args_tma};
     } else {
+        const int TH = cfg.th();
+        if (TH < kMinTileH) return DH_EINVAL;
+        const int nty = (H + TH - 1) / TH;
+        v.nblk = ntx * nty;
+        if (v.nblk > L.nblk_sweep) return DH_EINVAL;
         SweepFn fn = sweep_fn(cfg.R, cfg.NW, cfg.edge);
         if (!fn) return DH_EINVAL;
         ls = LaunchSpec{(void *)fn, dim3(ntx, nty, 3), dim3(cfg.NW * 32), 0, args_gen};

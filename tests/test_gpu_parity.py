@@ -225,7 +225,7 @@ def test_graph_and_host_loop_identical_and_resume_exact(N, api, orc):
     assert np.array_equal(host(u), outs[0])
 
 
-@pytest.mark.parametrize("H,W", [(64, 128), (100, 260), (33, 4), (300, 516)])
+@pytest.mark.parametrize("H,W", [(64, 128), (100, 260), (33, 4), (300, 516), (1, 200), (2, 8), (45, 132)])
 def test_sweep_variants_bit_identical(N, api, orc, H, W, monkeypatch):
     """The TMA kernel (every tiling) and the generic kernel run the same
     float32 arithmetic per pixel.  Faces on a warp's first/last row are
@@ -234,7 +234,8 @@ def test_sweep_variants_bit_identical(N, api, orc, H, W, monkeypatch):
     (and each variant is deterministic run to run)."""
     _, _, Phi, lam = _problem(orc, 31 + H, H, W, "stable")
     outs = {}
-    for cfg in ("8,4,2,0", "8,4,2,1", "8,4,1,1", "4,8,2,1", "8,4,1,2", "4,8,2,2", "16,4,1,2", "16,4,2,0"):
+    for cfg in ("8,4,2,0", "8,4,2,1", "8,4,1,1", "4,8,2,1", "8,4,1,2", "4,8,2,2", "16,4,1,2", "16,4,2,0",
+                "8,4,1,3", "8,8,1,3", "16,4,1,3", "8,2,1,3", "4,8,1,3"):
         monkeypatch.setenv("DH_SWEEP", cfg)
         u = dev(Phi.copy())
         rep, _ = api.fixed_point(u, dev(Phi), dev(lam), api.params("stable", tol=0.0, max_iter=12))
