@@ -56,10 +56,16 @@ extern "C" {
 #define DH_PRESET_PAPER 0  /* the paper's constants (Sec. IV-B), eps = 1e-3 */
 #define DH_PRESET_STABLE 1 /* the same with eps = 1.0, which satisfies App. A-A's step bound */
 
-/* iterate storage (u and its halos); arithmetic is always float32 */
+/* iterate storage (u and its halos); Phi, lambda and all arithmetic stay
+ * float32.  The 16-bit forms stall at a residual set by their quantum (u is
+ * O(10) at the fixed point); the switched forms run 16-bit storage until the
+ * residual stops falling (less than 2 % over 16 iterations), then convert the
+ * iterate and finish in float32. */
 #define DH_STORE_F32 0
 #define DH_STORE_BF16 1
 #define DH_STORE_F16 2
+#define DH_STORE_BF16_F32 3
+#define DH_STORE_F16_F32 4
 
 /* ablation switches (Sec. IV-E, Table II), OR-ed into dh_params.variant */
 #define DH_VAR_NO_ADAPTIVE 1 /* lambda(t) == lambda0 */

@@ -22,7 +22,7 @@ DH_ECUDA = -4
 DH_ETIMEOUT = -5
 DH_PRESET_PAPER = 0
 DH_PRESET_STABLE = 1
-DH_STORE_F32, DH_STORE_BF16, DH_STORE_F16 = 0, 1, 2
+DH_STORE_F32, DH_STORE_BF16, DH_STORE_F16, DH_STORE_BF16_F32, DH_STORE_F16_F32 = 0, 1, 2, 3, 4
 DH_VAR_NO_ADAPTIVE, DH_VAR_NO_EDGE, DH_VAR_NO_NONLOCAL = 1, 2, 4
 
 # Every symbol include/dehaze.h declares.

@@ -20,6 +20,8 @@ constexpr int kTW = 128;
 
 // ---------------------------------------------------------------- device state
 // Iteration state of one image, in the workspace.
+constexpr int kStallWindow = 16;  // residual-stall test of a 16-bit phase: iterations compared
+
 struct SolveState {
     unsigned arrive;   // CTAs of the current sweep launch that have finished
     int n;             // index of the current iterate u^n
@@ -30,13 +32,18 @@ struct SolveState {
     float rho[3];      // residual of u^n_final
     float phin2[3];    // ||Phi^c||^2
     int err;           // error raised inside a sweep (DH_ETIMEOUT), 0 if none
-    int pad[3];
+    int phase_start;   // first n of the current precision phase
+    int pad[2];
+    float rmax[kStallWindow];  // max_c rho_n of the last iterations (ring)
 };
+
+// status a 16-bit phase ends with when its residual stalls (internal)
+constexpr int kStatusSwitch = 100;
 
 // Everything the loop kernels need; written to the workspace by one tiny
 // kernel per call so that a cached CUDA graph can be relaunched unchanged.
 struct SolveDesc {
-    float *u[2];
+    void *u[2];          // iterate buffers, float or 16-bit (storage)
     const float *phi;
     const float *lam;
     float *rho_hist;     // [3*(max_iter+1)] or nullptr
@@ -45,6 +52,8 @@ struct SolveDesc {
     unsigned long long cond;  // cudaGraphConditionalHandle of the while node
     int use_cond;
     int vec;             // W % 4 == 0 and every plane 16-byte aligned
+    int storage;         // element type of u[]: 0 float, 1 bf16, 2 f16
+    int phase_stop;      // 1: stop this phase when the residual stalls
     int H, W;
     int max_iter;
     int depth;           // iterations fused per sweep launch
@@ -89,7 +98,7 @@ static inline WsLayout ws_layout(int H, int W, int depth, int tile_h) {
     L.nblk_sel = kSelBlocks;
     size_t o = 0;
     L.state = o; o = align_up(o + sizeof(SolveState));
-    L.desc = o; o = align_up(o + sizeof(SolveDesc));
+    L.desc = o; o = align_up(o + 2 * sizeof(SolveDesc));  // one per precision phase
     L.sel = o; o = align_up(o + sizeof(SelectState));
     L.hist = o; o = align_up(o + 256 * sizeof(unsigned));
     L.blk = o; o = align_up(o + (size_t)kSelBlocks * 16);
@@ -98,7 +107,7 @@ static inline WsLayout ws_layout(int H, int W, int depth, int tile_h) {
     L.dc = o; o = align_up(o + N * sizeof(float));
     L.lam = o; o = align_up(o + N * sizeof(float));
     L.phi = o; o = align_up(o + 3 * N * sizeof(float));
-    L.ub = o; o = align_up(o + 3 * N * sizeof(float));
+    L.ub = o; o = align_up(o + 3 * N * sizeof(float) + kAlign);  // f32 buffer, or two 16-bit ones
     L.total = o;
     return L;
 }

@@ -11,6 +11,9 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "tma.cuh"
 
@@ -85,11 +88,21 @@ __device__ void finish_iteration(const SolveDesc *d, SolveState *st) {
     }
     const int err = __ldcg(&st->err);
     const bool conv = finite && worst <= d->tol;
+    // a 16-bit phase ends once its residual falls by less than 2 % over
+    // kStallWindow iterations (the storage quantum has been reached)
+    bool stall = false;
+    if (d->phase_stop && finite) {
+        const int slot = n % kStallWindow;
+        if (n - st->phase_start >= kStallWindow && worst > 0.98f * st->rmax[slot]) stall = true;
+        st->rmax[slot] = worst;
+    }
     unsigned cont = 1;
-    if (err || conv || !finite || n >= d->max_iter) {
+    if (err || conv || !finite || n >= d->max_iter || stall) {
         st->done = 1;
         st->n_final = n;
-        st->status = err ? err : (!finite ? DH_ENONFINITE : (conv ? DH_OK : DH_WNOCONV));
+        st->status = err ? err
+                         : (!finite ? DH_ENONFINITE
+                                    : (conv ? DH_OK : (n >= d->max_iter ? DH_WNOCONV : kStatusSwitch)));
         for (int c = 0; c < 3; ++c) st->rho[c] = rho[c];
         cont = 0;
     } else {
@@ -181,6 +194,80 @@ __device__ __forceinline__ float2 face_flux2(float2 a, float2 b, float2 eps2) {
     return mul2(a, make_float2(rcp_approx(q.x), rcp_approx(q.y)));
 }
 
+// Iterate storage: float, or bf16 / f16 converted to float on load and
+// rounded to nearest-even on store.  HALO = columns of tile halo on each side
+// as loaded by TMA (a 16-bit TMA row must start on a multiple of 8 columns).
+template <class T>
+struct Store;
+template <>
+struct Store<float> {
+    static constexpr int HALO = 4;
+    static constexpr int TMA_TYPE = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    __device__ static void read12(const float *p, float *v) {  // 16-byte aligned
+        const float4 a = *reinterpret_cast<const float4 *>(p);
+        const float4 b = *reinterpret_cast<const float4 *>(p + 4);
+        const float4 c = *reinterpret_cast<const float4 *>(p + 8);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y;
+        v[6] = b.z; v[7] = b.w; v[8] = c.x; v[9] = c.y; v[10] = c.z; v[11] = c.w;
+    }
+    __device__ static void write4(float *p, float a, float b, float c, float d) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    }
+    __device__ static float get(const float *p) { return *p; }
+    __device__ static void put(float *p, float v) { *p = v; }
+};
+template <>
+struct Store<__nv_bfloat16> {
+    static constexpr int HALO = 8;
+    static constexpr int TMA_TYPE = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    __device__ static void w2(unsigned w, float &lo, float &hi) {
+        lo = __uint_as_float(w << 16);
+        hi = __uint_as_float(w & 0xffff0000u);
+    }
+    __device__ static void read12(const __nv_bfloat16 *p, float *v) {  // 8-byte aligned
+        const uint2 a = *reinterpret_cast<const uint2 *>(p);
+        const uint2 b = *reinterpret_cast<const uint2 *>(p + 4);
+        const uint2 c = *reinterpret_cast<const uint2 *>(p + 8);
+        w2(a.x, v[0], v[1]); w2(a.y, v[2], v[3]); w2(b.x, v[4], v[5]);
+        w2(b.y, v[6], v[7]); w2(c.x, v[8], v[9]); w2(c.y, v[10], v[11]);
+    }
+    __device__ static void write4(__nv_bfloat16 *p, float a, float b, float c, float d) {
+        const __nv_bfloat162 x = __floats2bfloat162_rn(a, b), y = __floats2bfloat162_rn(c, d);
+        uint2 q;
+        q.x = *reinterpret_cast<const unsigned *>(&x);
+        q.y = *reinterpret_cast<const unsigned *>(&y);
+        *reinterpret_cast<uint2 *>(p) = q;
+    }
+    __device__ static float get(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+    __device__ static void put(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+template <>
+struct Store<__half> {
+    static constexpr int HALO = 8;
+    static constexpr int TMA_TYPE = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    __device__ static void w2(unsigned w, float &lo, float &hi) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w));
+        lo = f.x;
+        hi = f.y;
+    }
+    __device__ static void read12(const __half *p, float *v) {
+        const uint2 a = *reinterpret_cast<const uint2 *>(p);
+        const uint2 b = *reinterpret_cast<const uint2 *>(p + 4);
+        const uint2 c = *reinterpret_cast<const uint2 *>(p + 8);
+        w2(a.x, v[0], v[1]); w2(a.y, v[2], v[3]); w2(b.x, v[4], v[5]);
+        w2(b.y, v[6], v[7]); w2(c.x, v[8], v[9]); w2(c.y, v[10], v[11]);
+    }
+    __device__ static void write4(__half *p, float a, float b, float c, float d) {
+        const __half2 x = __floats2half2_rn(a, b), y = __floats2half2_rn(c, d);
+        uint2 q;
+        q.x = *reinterpret_cast<const unsigned *>(&x);
+        q.y = *reinterpret_cast<const unsigned *>(&y);
+        *reinterpret_cast<uint2 *>(p) = q;
+    }
+    __device__ static float get(const __half *p) { return __half2float(*p); }
+    __device__ static void put(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
 // One row of u for a lane, as the pairs the stencil needs: odd pairs
 // o0 = (x-1, x), o1 = (x+1, x+2), o2 = (x+3, x+4) and even pairs
 // e1 = (x, x+1), e2 = (x+2, x+3).
@@ -195,10 +282,10 @@ struct RowU {
 // kept in rolling registers; arithmetic runs on float32 pairs.
 // pl(ty, ph, la) supplies Phi and lambda for the row; sink(ty, nu, F)
 // consumes u^{n+1} and F.
-template <int R, int SW, bool EDGE, class PL, class SINK>
-__device__ __forceinline__ void walk_rows(const float *__restrict__ s, int r0, int lane, float eps, float tau,
+template <int R, int SW, class T, bool EDGE, class PL, class SINK>
+__device__ __forceinline__ void walk_rows(const T *__restrict__ s, int r0, int lane, float eps, float tau,
                                           float wg0, float wg1, float wg2, PL pl, SINK sink) {
-    const int sc = 4 * lane;
+    const int sc = 4 * lane + (Store<T>::HALO - 4);  // smem column of x-4
     const float2 W0 = make_float2(wg0, wg0), W1 = make_float2(wg1, wg1), W2 = make_float2(wg2, wg2);
     const float2 E2 = make_float2(eps, eps), HALF = make_float2(0.5f, 0.5f), TAU = make_float2(tau, tau);
     const float2 MONE = make_float2(-1.f, -1.f);
@@ -210,16 +297,14 @@ __device__ __forceinline__ void walk_rows(const float *__restrict__ s, int r0, i
         return fma2(W2, add2(m2, p2), fma2(W1, add2(m1, p1), mul2(W0, c0)));
     };
     auto load_row = [&](int tr, RowU &u, float2 *g) {
-        const float *row = s + (tr + 2) * SW + sc;
-        const float4 L = *reinterpret_cast<const float4 *>(row);
-        const float4 C = *reinterpret_cast<const float4 *>(row + 4);
-        const float4 Rr = *reinterpret_cast<const float4 *>(row + 8);
-        const float2 e0 = make_float2(L.z, L.w), e3 = make_float2(Rr.x, Rr.y);
-        u.o0 = make_float2(L.w, C.x);
-        u.e1 = make_float2(C.x, C.y);
-        u.o1 = make_float2(C.y, C.z);
-        u.e2 = make_float2(C.z, C.w);
-        u.o2 = make_float2(C.w, Rr.x);
+        float v[12];  // columns x-4 .. x+7
+        Store<T>::read12(s + (tr + 2) * SW + sc, v);
+        const float2 e0 = make_float2(v[2], v[3]), e3 = make_float2(v[8], v[9]);
+        u.o0 = make_float2(v[3], v[4]);
+        u.e1 = make_float2(v[4], v[5]);
+        u.o1 = make_float2(v[5], v[6]);
+        u.e2 = make_float2(v[6], v[7]);
+        u.o2 = make_float2(v[7], v[8]);
         g[0] = gauss(e0, u.o0, u.e1, u.o1, u.e2);
         g[1] = gauss(u.e1, u.o1, u.e2, u.o2, e3);
     };
@@ -275,7 +360,7 @@ __device__ __forceinline__ void walk_rows(const float *__restrict__ s, int r0, i
 
 // Generic sweep (any W, any alignment): one CTA per (tile, channel), tile of
 // u^n gathered with the reflecting boundary by plain loads.
-template <int R, int NW, bool EDGE>
+template <int R, int NW, class T, bool EDGE>
 __global__ void __launch_bounds__(NW * 32)
 k_sweep(const SolveDesc *__restrict__ d) {
     constexpr int TH = R * NW;
@@ -293,15 +378,15 @@ k_sweep(const SolveDesc *__restrict__ d) {
     const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * TH;
     const int cur = __ldcg(&st->cur);
     const size_t N = (size_t)H * W;
-    const float *__restrict__ u = d->u[cur] + c * N;
-    float *__restrict__ un = d->u[cur ^ 1] + c * N;
+    const T *__restrict__ u = static_cast<const T *>(d->u[cur]) + c * N;
+    T *__restrict__ un = static_cast<T *>(d->u[cur ^ 1]) + c * N;
     const float *__restrict__ phi = d->phi + c * N;
     const float *__restrict__ lam = d->lam;
 
     for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
         const int r = e / SW, q = e - r * SW;
         const int gy = reflect_idx(y0 - 2 + r, H), gx = reflect_idx(x0 - 4 + q, W);
-        s[e] = u[(size_t)gy * W + gx];
+        s[e] = Store<T>::get(u + (size_t)gy * W + gx);
     }
     __syncthreads();
 
@@ -338,14 +423,14 @@ k_sweep(const SolveDesc *__restrict__ d) {
             if (x + j < W) q = fmaf(F[j], F[j], q);
         neumaier_add(rs, rc, q);
         if (vec) {
-            if (x < W) *reinterpret_cast<float4 *>(un + ro + x) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+            if (x < W) Store<T>::write4(un + ro + x, nu[0], nu[1], nu[2], nu[3]);
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j)
-                if (x + j < W) un[ro + x + j] = nu[j];
+                if (x + j < W) Store<T>::put(un + ro + x + j, nu[j]);
         }
     };
-    walk_rows<R, SW, EDGE>(s, w * R, lane, d->eps, d->tau, d->wg0, d->wg1, d->wg2, pl, sink);
+    walk_rows<R, SW, float, EDGE>(s, w * R, lane, d->eps, d->tau, d->wg0, d->wg1, d->wg2, pl, sink);
 
     const float2 tot = block_pair_sum<NW>(rs, rc, red);
     if (threadIdx.x == 0)
@@ -355,11 +440,11 @@ k_sweep(const SolveDesc *__restrict__ d) {
 
 // Shared-memory plan of the TMA sweep: per stage the u^n tile with its halo,
 // the Phi tile and the lambda tile, each 1024-byte aligned.
-template <int TH, bool PL_SMEM>
+template <int TH, bool PL_SMEM, class T>
 struct TmaPlan {
-    static constexpr int SW = kTW + 8;
+    static constexpr int SW = kTW + 2 * Store<T>::HALO;
     static constexpr int SH = TH + 4;
-    static constexpr uint32_t U_BYTES = SH * SW * 4;
+    static constexpr uint32_t U_BYTES = SH * SW * sizeof(T);
     static constexpr uint32_t P_BYTES = PL_SMEM ? TH * kTW * 4 : 0;
     static constexpr uint32_t U_OFF = 0;
     static constexpr uint32_t PHI_OFF = (U_BYTES + 1023) / 1024 * 1024;
@@ -375,13 +460,14 @@ constexpr long long kWaitLimitCycles = 4000000000LL;  // about 2 s at 2 GHz
 // into shared memory by TMA, STAGES items ahead, together with the Phi and
 // lambda tiles when PL_SMEM (otherwise the walk reads those with vector
 // loads); the border halo is reflected in shared memory afterwards.
-template <int R, int NW, int STAGES, bool PL_SMEM, bool EDGE>
+template <int R, int NW, int STAGES, bool PL_SMEM, class T, bool EDGE>
 __global__ void __launch_bounds__(NW * 32)
 k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
             const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
             const SolveDesc *__restrict__ d) {
     constexpr int TH = R * NW;
-    using P = TmaPlan<TH, PL_SMEM>;
+    constexpr int HALO = Store<T>::HALO;
+    using P = TmaPlan<TH, PL_SMEM, T>;
     constexpr int SW = P::SW, SH = P::SH;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base (the launch adds 1 KiB of slack)
@@ -396,7 +482,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     const int H = d->H, W = d->W;
     const int cur = __ldcg(&st->cur);
     const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
-    float *__restrict__ ubase = d->u[cur ^ 1];
+    T *__restrict__ ubase = static_cast<T *>(d->u[cur ^ 1]);
     const size_t N = (size_t)H * W;
     const int ntx = (W + kTW - 1) / kTW, nty = (H + TH - 1) / TH;
     const int ntiles = ntx * nty, nitems = 3 * ntiles;
@@ -413,7 +499,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
         const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * TH;
         unsigned char *sb = smem + stage * P::STAGE;
         mbar_arrive_expect_tx(&bar[stage], P::TX);
-        tma_load_3d(sb + P::U_OFF, tm_u, &bar[stage], x0 - 4, y0 - 2, c);
+        tma_load_3d(sb + P::U_OFF, tm_u, &bar[stage], x0 - HALO, y0 - 2, c);
         if (PL_SMEM) {
             tma_load_3d(sb + P::PHI_OFF, &tm_phi, &bar[stage], x0, y0, c);
             tma_load_2d(sb + P::LAM_OFF, &tm_lam, &bar[stage], x0, y0);
@@ -437,7 +523,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
         const int tile = item / 3, c = item - 3 * tile;
         const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * TH;
         unsigned char *sb = smem + stage * P::STAGE;
-        float *s = reinterpret_cast<float *>(sb + P::U_OFF);
+        T *s = reinterpret_cast<T *>(sb + P::U_OFF);
         const float *sphi = reinterpret_cast<const float *>(sb + P::PHI_OFF);
         const float *slam = reinterpret_cast<const float *>(sb + P::LAM_OFF);
 
@@ -450,12 +536,12 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
         if (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + TH + 2 > H) {
             for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
                 const int r = e / SW, q = e - r * SW;
-                const int gy = y0 - 2 + r, gx = x0 - 4 + q;
+                const int gy = y0 - 2 + r, gx = x0 - HALO + q;
                 const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
                 const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
                 const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
                 if ((fy && (inx || fx)) || (fx && iny)) {
-                    const int sy = reflect_idx(gy, H) - (y0 - 2), sx = reflect_idx(gx, W) - (x0 - 4);
+                    const int sy = reflect_idx(gy, H) - (y0 - 2), sx = reflect_idx(gx, W) - (x0 - HALO);
                     s[e] = s[sy * SW + sx];
                 }
             }
@@ -463,7 +549,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
         }
         __syncthreads();
 
-        float *__restrict__ un = ubase + c * N;
+        T *__restrict__ un = ubase + c * N;
         const int x = x0 + 4 * lane;
         float rs = 0.f, rc = 0.f;
         const float *__restrict__ gphi = phi_all + c * N;
@@ -490,9 +576,9 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
 #pragma unroll
             for (int j = 0; j < 4; ++j) q = fmaf(F[j], F[j], q);
             neumaier_add(rs, rc, q);
-            *reinterpret_cast<float4 *>(un + (size_t)y * W + x) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+            Store<T>::write4(un + (size_t)y * W + x, nu[0], nu[1], nu[2], nu[3]);
         };
-        walk_rows<R, SW, EDGE>(s, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
+        walk_rows<R, SW, T, EDGE>(s, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
 
         const float2 tot = block_pair_sum<NW>(rs, rc, red);  // ends with a barrier
         if (threadIdx.x == 0) {
@@ -549,7 +635,7 @@ k_sweep_stream(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant_
     const int H = d->H, W = d->W;
     const int cur = __ldcg(&st->cur);
     const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
-    float *__restrict__ ubase = d->u[cur ^ 1];
+    float *__restrict__ ubase = static_cast<float *>(d->u[cur ^ 1]);
     const size_t N = (size_t)H * W;
     const int ntx = (W + kTW - 1) / kTW;
     const int nseg = (H + seg - 1) / seg;
@@ -736,8 +822,11 @@ k_sweep_stream(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant_
 
 // ------------------------------------------------------------ small kernels
 
-__global__ void k_set_desc(SolveDesc *dst, SolveDesc v) {
+// Writes the loop descriptor; `reset` starts a new solve, otherwise the
+// iteration state (n, history) carries over into the next precision phase.
+__global__ void k_set_desc(SolveDesc *dst, SolveDesc v, int reset) {
     *dst = v;
+    if (!reset) return;
     SolveState *st = v.st;
     st->arrive = 0;
     st->n = 0;
@@ -746,20 +835,49 @@ __global__ void k_set_desc(SolveDesc *dst, SolveDesc v) {
     st->status = 0;
     st->n_final = 0;
     st->err = 0;
+    st->phase_start = 0;
 }
 
-// J = clamp(u^n, 0, 1) and u^n copied to the caller's u when it sits in the
-// workspace buffer.
-__global__ void k_output(const SolveDesc *__restrict__ d, float *J) {
-    const int cur = ld_state_int(&d->st->cur);
+// J = clamp(u^n, 0, 1) and u^n as float32 into u_out (skipped when u^n is
+// already there: float storage, buffer 0).
+template <class T>
+__global__ void k_output(const SolveDesc *__restrict__ d, float *J, float *u_out) {
+    const int cur = __ldcg(&d->st->cur);
     const size_t n3 = (size_t)3 * d->H * d->W;
-    const float *src = d->u[cur];
-    float *u0 = d->u[0];
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const float v = src[i];
-        if (cur) u0[i] = v;
+    const T *src = static_cast<const T *>(d->u[cur]);
+    const bool copy = u_out && (sizeof(T) != sizeof(float) || cur != 0);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = Store<T>::get(src + i);
+        if (copy) u_out[i] = v;
         if (J) J[i] = fminf(fmaxf(v, 0.f), 1.f);
+    }
+}
+
+template <class Tin, class Tout>
+__global__ void k_convert(const Tin *__restrict__ src, Tout *__restrict__ dst, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        Store<Tout>::put(dst + i, Store<Tin>::get(src + i));
+}
+
+// End of a 16-bit phase: its iterate u^n (in d->u[cur]) becomes float32 in `dst`.
+template <class T>
+__global__ void k_phase_convert(const SolveDesc *__restrict__ d, float *dst) {
+    const int cur = __ldcg(&d->st->cur);
+    const size_t n3 = (size_t)3 * d->H * d->W;
+    const T *src = static_cast<const T *>(d->u[cur]);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = Store<T>::get(src + i);
+}
+
+// Hands the state to the float32 phase: the iterate now sits in buffer 0; a
+// stalled phase continues from the same n, any other outcome stays final.
+__global__ void k_phase_state(SolveState *st) {
+    st->cur = 0;
+    st->arrive = 0;
+    if (st->status == kStatusSwitch) {
+        st->done = 0;
+        st->status = 0;
+        st->phase_start = st->n;
     }
 }
 
@@ -781,32 +899,38 @@ int sweep_tile_h(int) { return kMinTileH; }
 typedef void (*SweepFn)(const SolveDesc *);
 typedef void (*SweepTmaFn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const SolveDesc *);
 
+template <class T>
 static SweepFn sweep_fn(int R, int NW, bool edge) {
 #define DH_SW(r, nw) \
-    if (R == r && NW == nw) return edge ? k_sweep<r, nw, true> : k_sweep<r, nw, false>;
+    if (R == r && NW == nw) return edge ? k_sweep<r, nw, T, true> : k_sweep<r, nw, T, false>;
     DH_SW(8, 4)
-    DH_SW(16, 4)
-    DH_SW(8, 8)
+    if (sizeof(T) == 4) {
+        DH_SW(16, 4)
+        DH_SW(8, 8)
+    }
 #undef DH_SW
     return nullptr;
 }
 
+template <class T>
 static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge) {
 #define DH_ST(r, nw, st, pls)                                                                   \
     if (R == r && NW == nw && stages == st && tma == (pls ? 1 : 2))                              \
-        return edge ? (SweepTmaFn)k_sweep_tma<r, nw, st, pls, true>                             \
-                    : (SweepTmaFn)k_sweep_tma<r, nw, st, pls, false>;
-    DH_ST(8, 4, 2, true)
+        return edge ? (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, true>                          \
+                    : (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, false>;
     DH_ST(8, 4, 1, true)
-    DH_ST(4, 8, 2, true)
-    DH_ST(4, 8, 1, true)
-    DH_ST(8, 4, 1, false)
-    DH_ST(8, 4, 2, false)
-    DH_ST(4, 8, 1, false)
-    DH_ST(4, 8, 2, false)
-    DH_ST(16, 4, 1, false)
-    DH_ST(8, 8, 1, false)
-    DH_ST(16, 2, 2, false)
+    if (sizeof(T) == 4) {
+        DH_ST(8, 4, 2, true)
+        DH_ST(4, 8, 2, true)
+        DH_ST(4, 8, 1, true)
+        DH_ST(8, 4, 1, false)
+        DH_ST(8, 4, 2, false)
+        DH_ST(4, 8, 1, false)
+        DH_ST(4, 8, 2, false)
+        DH_ST(16, 4, 1, false)
+        DH_ST(8, 8, 1, false)
+        DH_ST(16, 2, 2, false)
+    }
 #undef DH_ST
     return nullptr;
 }
@@ -844,9 +968,9 @@ static int stream_segment(int H, int ntx, int warps) {
     return best_seg;
 }
 
-static uint32_t tma_smem_bytes(int th, int stages, int tma) {
-    const uint32_t SW = kTW + 8, SH = th + 4;
-    const uint32_t ub = SH * SW * 4, pb = tma == 1 ? th * kTW * 4 : 0;
+static uint32_t tma_smem_bytes(int th, int stages, int tma, int esize) {
+    const uint32_t SW = kTW + (esize == 4 ? 8 : 16), SH = th + 4;
+    const uint32_t ub = SH * SW * esize, pb = tma == 1 ? th * kTW * 4 : 0;
     const uint32_t phi_off = (ub + 1023) / 1024 * 1024;
     const uint32_t stage = (phi_off + 2 * pb + 1023) / 1024 * 1024;
     return stages * stage + 1024;
@@ -854,8 +978,9 @@ static uint32_t tma_smem_bytes(int th, int stages, int tma) {
 
 // DH_SWEEP="R,NW,STAGES,TMA" overrides the default variant (for tuning);
 // TMA = 3 selects the streaming kernel with R = ring slots per warp.
-static SweepCfg pick_cfg(const dh_params *p, bool tma_ok) {
+static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16) {
     SweepCfg c{8, 4, 1, tma_ok ? 1 : 0, !(p->variant & DH_VAR_NO_EDGE)};
+    if (is16) return c;  // 16-bit storage: the default tiling only
     if (const char *e = std::getenv("DH_SWEEP")) {
         int r, nw, st, t;
         if (std::sscanf(e, "%d,%d,%d,%d", &r, &nw, &st, &t) == 4) {
@@ -865,7 +990,7 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok) {
             c.tma = tma_ok ? t : 0;
         }
     }
-    if (!c.tma && !sweep_fn(c.R, c.NW, c.edge)) { c.R = 8; c.NW = 4; }
+    if (!c.tma && !sweep_fn<float>(c.R, c.NW, c.edge)) { c.R = 8; c.NW = 4; }
     if (!c.tma) c.stages = 1;
     return c;
 }
@@ -875,7 +1000,15 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok) {
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 static std::mutex g_enc_mu;
 
+static int encode_map(CUtensorMap *m, CUtensorMapDataType dt, int esize, const void *base, int rank, int W, int H,
+                      int C, int boxW, int boxH);
+
 int encode_f32_map(CUtensorMap *m, const void *base, int rank, int W, int H, int C, int boxW, int boxH) {
+    return encode_map(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, rank, W, H, C, boxW, boxH);
+}
+
+static int encode_map(CUtensorMap *m, CUtensorMapDataType dt, int esize, const void *base, int rank, int W, int H,
+                      int C, int boxW, int boxH) {
     {
         std::lock_guard<std::mutex> lk(g_enc_mu);
         if (!g_encode) {
@@ -888,10 +1021,10 @@ int encode_f32_map(CUtensorMap *m, const void *base, int rank, int W, int H, int
         }
     }
     cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)C};
-    cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)W * H * 4};
+    cuuint64_t strides[2] = {(cuuint64_t)W * esize, (cuuint64_t)W * H * esize};
     cuuint32_t box[3] = {(cuuint32_t)boxW, (cuuint32_t)boxH, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, const_cast<void *>(base), dims, strides, box,
+    CUresult r = g_encode(m, dt, rank, const_cast<void *>(base), dims, strides, box,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? DH_OK : DH_EINVAL;
@@ -901,12 +1034,13 @@ int encode_f32_map(CUtensorMap *m, const void *base, int rank, int W, int H, int
 
 struct GraphKey {
     int dev;
-    const void *ws;
+    const void *desc;
     const void *ptrs[4];
-    int H, W, R, NW, stages, tma, edge;
+    int H, W, R, NW, stages, tma, edge, storage;
     bool operator==(const GraphKey &o) const {
-        return dev == o.dev && ws == o.ws && std::memcmp(ptrs, o.ptrs, sizeof(ptrs)) == 0 && H == o.H &&
-               W == o.W && R == o.R && NW == o.NW && stages == o.stages && tma == o.tma && edge == o.edge;
+        return dev == o.dev && desc == o.desc && std::memcmp(ptrs, o.ptrs, sizeof(ptrs)) == 0 && H == o.H &&
+               W == o.W && R == o.R && NW == o.NW && stages == o.stages && tma == o.tma && edge == o.edge &&
+               storage == o.storage;
     }
 };
 
@@ -1000,15 +1134,112 @@ static int persistent_grid(void *func, int block, unsigned smem) {
 
 // ------------------------------------------------------------ the solve loop
 
-// Queues the fixed-point loop for buffers u[0] (caller's, holds u^0) and
-// u[1] (workspace).  st->phin2 must already be set on the stream.
+// Queues one precision phase of the fixed-point loop: descriptor `v` (its
+// u[0]/u[1] hold element type T) written to desc_dev, then the sweep kernel
+// repeated in a graph while loop (or from the host).
+template <class T>
+static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_params *p, const WsLayout &L,
+                      cudaStream_t s, int *launches) {
+    const int H = v.H, W = v.W;
+    constexpr int esize = (int)sizeof(T);
+    auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+    const bool aligned = a16(v.u[0]) && a16(v.u[1]) && a16(v.phi) && a16(v.lam);
+    // float4 Phi/lambda loads need W % 4; TMA rows of T need W * esize % 16
+    v.vec = (W % 4 == 0) && aligned;
+    const bool tma_ok = v.vec && (W * esize) % 16 == 0;
+    v.storage = esize == 4 ? 0 : (Store<T>::TMA_TYPE == CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 ? 1 : 2);
+    const SweepCfg cfg = pick_cfg(p, tma_ok, esize != 4);
+    const int ntx = (W + kTW - 1) / kTW;
+    CUtensorMap maps[4];
+    const SolveDesc *dptr = desc_dev;
+    int seg = 0;
+    void *args_tma[5] = {&maps[0], &maps[1], &maps[2], &maps[3], (void *)&dptr};
+    void *args_stream[6] = {&maps[0], &maps[1], &maps[2], &maps[3], (void *)&dptr, (void *)&seg};
+    void *args_gen[1] = {(void *)&dptr};
+    LaunchSpec ls;
+    if (cfg.tma == 3 && esize == 4) {
+        // per-warp row streams over (channel, 128-column strip, segment) tasks
+        int rc = encode_f32_map(&maps[0], v.u[0], 3, W, H, 3, kTW + 8, 1);
+        if (!rc) rc = encode_f32_map(&maps[1], v.u[1], 3, W, H, 3, kTW + 8, 1);
+        if (!rc) rc = encode_f32_map(&maps[2], v.phi, 3, W, H, 3, kTW, 1);
+        if (!rc) rc = encode_f32_map(&maps[3], v.lam, 2, W, H, 1, kTW, 1);
+        if (rc) return rc;
+        SweepStreamFn fn = sweep_stream_fn(cfg.NW, cfg.R, cfg.edge);
+        if (!fn) return DH_EINVAL;
+        const unsigned smem = cfg.NW * cfg.R * kRowBytes + 1024;
+        const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
+        if (gmax <= 0) return DH_ECUDA;
+        seg = stream_segment(H, ntx, gmax * cfg.NW);
+        v.nblk = ntx * ((H + seg - 1) / seg);
+        if (v.nblk > L.nblk_sweep) return DH_EINVAL;
+        const int g = (3 * v.nblk + cfg.NW - 1) / cfg.NW;
+        ls = LaunchSpec{(void *)fn, dim3(g < gmax ? g : gmax), dim3(cfg.NW * 32), smem, args_stream};
+    } else if (cfg.tma == 1 || cfg.tma == 2) {
+        const int TH = cfg.th();
+        if (TH < kMinTileH) return DH_EINVAL;
+        v.nblk = ntx * ((H + TH - 1) / TH);
+        if (v.nblk > L.nblk_sweep) return DH_EINVAL;  // workspace sized for another tiling
+        const int halo = Store<T>::HALO;
+        const CUtensorMapDataType dt = (CUtensorMapDataType)Store<T>::TMA_TYPE;
+        int rc = encode_map(&maps[0], dt, esize, v.u[0], 3, W, H, 3, kTW + 2 * halo, TH + 4);
+        if (!rc) rc = encode_map(&maps[1], dt, esize, v.u[1], 3, W, H, 3, kTW + 2 * halo, TH + 4);
+        if (!rc) rc = encode_f32_map(&maps[2], v.phi, 3, W, H, 3, kTW, TH);
+        if (!rc) rc = encode_f32_map(&maps[3], v.lam, 2, W, H, 1, kTW, TH);
+        if (rc) return rc;
+        SweepTmaFn fn = sweep_tma_fn<T>(cfg.R, cfg.NW, cfg.stages, cfg.tma, cfg.edge);
+        if (!fn) return DH_EINVAL;
+        const unsigned smem = tma_smem_bytes(TH, cfg.stages, cfg.tma, esize);
+        const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
+        if (gmax <= 0) return DH_ECUDA;
+        const int items = 3 * v.nblk;
+        ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(cfg.NW * 32), smem, args_tma};
+    } else {
+        const int TH = cfg.th();
+        if (TH < kMinTileH) return DH_EINVAL;
+        const int nty = (H + TH - 1) / TH;
+        v.nblk = ntx * nty;
+        if (v.nblk > L.nblk_sweep) return DH_EINVAL;
+        SweepFn fn = sweep_fn<T>(cfg.R, cfg.NW, cfg.edge);
+        if (!fn) return DH_EINVAL;
+        ls = LaunchSpec{(void *)fn, dim3(ntx, nty, 3), dim3(cfg.NW * 32), 0, args_gen};
+    }
+    if (p->use_graph) {
+        int dev = 0;
+        DH_CUDA_TRY(cudaGetDevice(&dev));
+        GraphKey key{dev, desc_dev, {v.u[0], v.u[1], v.phi, v.lam}, H, W, cfg.R, cfg.NW, cfg.stages, cfg.tma,
+                     cfg.edge ? 1 : 0, v.storage};
+        GraphEntry ge;
+        int rc = get_loop_graph(key, ls, &ge);
+        if (rc != DH_OK) return rc;
+        v.cond = ge.cond;
+        v.use_cond = 1;
+        k_set_desc<<<1, 1, 0, s>>>(desc_dev, v, reset ? 1 : 0);
+        DH_CUDA_TRY(cudaGetLastError());
+        DH_CUDA_TRY(cudaGraphLaunch(ge.exec, s));
+    } else {
+        v.use_cond = 0;
+        k_set_desc<<<1, 1, 0, s>>>(desc_dev, v, reset ? 1 : 0);
+        for (int n = 0; n <= p->max_iter; ++n)
+            DH_CUDA_TRY(cudaLaunchKernel(ls.func, ls.grid, ls.block, ls.args, ls.smem, s));
+        if (launches) *launches += p->max_iter + 1;  // queued; finished ones exit at once
+    }
+    if (launches) *launches += 1;  // k_set_desc
+    return DH_OK;
+}
+
+static int grid_for(size_t n) { return (int)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16); }
+
+// The fixed-point loop from the caller's u (holding u^0, float32) to u^n
+// (float32 in the caller's u) and optionally J.  st->phin2 must be set.
+// Storage: float32 iterates ping-pong between the caller's u and the
+// workspace buffer; 16-bit iterates between two halves of that buffer, and
+// the switched forms finish with a float32 phase from the converted iterate.
 int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W, const dh_params *p,
               float *rho_hist, char *ws, const WsLayout &L, cudaStream_t s, float *J,
               cudaEvent_t loop_begin, cudaEvent_t loop_end, int *launches) {
-    SolveDesc *desc_dev = (SolveDesc *)(ws + L.desc);
+    SolveDesc *desc1 = (SolveDesc *)(ws + L.desc);
+    SolveDesc *desc2 = desc1 + 1;
     SolveDesc v = {};
-    v.u[0] = u_caller;
-    v.u[1] = (float *)(ws + L.ub);
     v.phi = phi;
     v.lam = lam;
     v.rho_hist = rho_hist;
@@ -1021,8 +1252,6 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
     v.tol = p->tol;
     v.tau = p->tau;
     v.eps = p->eps;
-    auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
-    v.vec = (W % 4 == 0) && a16(u_caller) && a16(v.u[1]) && a16(phi) && a16(lam);
     {  // App. A-B-2: normalised 5-tap Gaussian, sigma = p->sigma
         double w[3];
         for (int k = 0; k <= 2; ++k) w[k] = exp(-(double)(k * k) / (2.0 * (double)p->sigma * p->sigma));
@@ -1031,89 +1260,62 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
         v.wg1 = (float)(w[1] / sum);
         v.wg2 = (float)(w[2] / sum);
     }
-    const SweepCfg cfg = pick_cfg(p, v.vec != 0);
-    const int ntx = (W + kTW - 1) / kTW;
-    CUtensorMap maps[4];
-    const SolveDesc *dptr = desc_dev;
-    int seg = 0;
-    void *args_tma[5] = {&maps[0], &maps[1], &maps[2], &maps[3], (void *)&dptr};
-    void *args_stream[6] = {&maps[0], &maps[1], &maps[2], &maps[3], (void *)&dptr, (void *)&seg};
-    void *args_gen[1] = {(void *)&dptr};
-    LaunchSpec ls;
-    if (cfg.tma == 3) {
-        // per-warp row streams over (channel, 128-column strip, segment) tasks
-        int rc = encode_f32_map(&maps[0], v.u[0], 3, W, H, 3, kTW + 8, 1);
-        if (!rc) rc = encode_f32_map(&maps[1], v.u[1], 3, W, H, 3, kTW + 8, 1);
-        if (!rc) rc = encode_f32_map(&maps[2], phi, 3, W, H, 3, kTW, 1);
-        if (!rc) rc = encode_f32_map(&maps[3], lam, 2, W, H, 1, kTW, 1);
-        if (rc) return rc;
-        SweepStreamFn fn = sweep_stream_fn(cfg.NW, cfg.R, cfg.edge);
-        if (!fn) return DH_EINVAL;
-        const unsigned smem = cfg.NW * cfg.R * kRowBytes + 1024;
-        const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
-        if (gmax <= 0) return DH_ECUDA;
-        seg = stream_segment(H, ntx, gmax * cfg.NW);
-        const int nseg = (H + seg - 1) / seg;
-        v.nblk = ntx * nseg;
-        if (v.nblk > L.nblk_sweep) return DH_EINVAL;
-        const int tasks = 3 * v.nblk;
-        const int g = (tasks + cfg.NW - 1) / cfg.NW;
-        ls = LaunchSpec{(void *)fn, dim3(g < gmax ? g : gmax), dim3(cfg.NW * 32), smem, args_stream};
-    } else if (cfg.tma) {
-        const int TH = cfg.th();
-        if (TH < kMinTileH) return DH_EINVAL;
-        v.nblk = ntx * ((H + TH - 1) / TH);
-        if (v.nblk > L.nblk_sweep) return DH_EINVAL;  // workspace sized for another tiling
-        int rc = encode_f32_map(&maps[0], v.u[0], 3, W, H, 3, kTW + 8, TH + 4);
-        if (!rc) rc = encode_f32_map(&maps[1], v.u[1], 3, W, H, 3, kTW + 8, TH + 4);
-        if (!rc) rc = encode_f32_map(&maps[2], phi, 3, W, H, 3, kTW, TH);
-        if (!rc) rc = encode_f32_map(&maps[3], lam, 2, W, H, 1, kTW, TH);
-        if (rc) return rc;
-        SweepTmaFn fn = sweep_tma_fn(cfg.R, cfg.NW, cfg.stages, cfg.tma, cfg.edge);
-        if (!fn) return DH_EINVAL;
-        const unsigned smem = tma_smem_bytes(TH, cfg.stages, cfg.tma);
-        const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
-        if (gmax <= 0) return DH_ECUDA;
-        const int items = 3 * v.nblk;
-        ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(cfg.NW * 32), smem, args_tma};
-    } else {
-        const int TH = cfg.th();
-        if (TH < kMinTileH) return DH_EINVAL;
-        const int nty = (H + TH - 1) / TH;
-        v.nblk = ntx * nty;
-        if (v.nblk > L.nblk_sweep) return DH_EINVAL;
-        SweepFn fn = sweep_fn(cfg.R, cfg.NW, cfg.edge);
-        if (!fn) return DH_EINVAL;
-        ls = LaunchSpec{(void *)fn, dim3(ntx, nty, 3), dim3(cfg.NW * 32), 0, args_gen};
-    }
-    if (p->use_graph) {
-        int dev = 0;
-        DH_CUDA_TRY(cudaGetDevice(&dev));
-        GraphKey key{dev, ws, {u_caller, v.u[1], phi, lam}, H, W, cfg.R, cfg.NW, cfg.stages, cfg.tma,
-                     cfg.edge ? 1 : 0};
-        GraphEntry ge;
-        int rc = get_loop_graph(key, ls, &ge);
-        if (rc != DH_OK) return rc;
-        v.cond = ge.cond;
-        v.use_cond = 1;
-        k_set_desc<<<1, 1, 0, s>>>(desc_dev, v);
-        DH_CUDA_TRY(cudaGetLastError());
-        if (loop_begin) DH_CUDA_TRY(cudaEventRecord(loop_begin, s));
-        DH_CUDA_TRY(cudaGraphLaunch(ge.exec, s));
-        if (loop_end) DH_CUDA_TRY(cudaEventRecord(loop_end, s));
-    } else {
-        v.use_cond = 0;
-        k_set_desc<<<1, 1, 0, s>>>(desc_dev, v);
-        if (loop_begin) DH_CUDA_TRY(cudaEventRecord(loop_begin, s));
-        for (int n = 0; n <= p->max_iter; ++n)
-            DH_CUDA_TRY(cudaLaunchKernel(ls.func, ls.grid, ls.block, ls.args, ls.smem, s));
-        if (loop_end) DH_CUDA_TRY(cudaEventRecord(loop_end, s));
-        if (launches) *launches += p->max_iter + 1;  // queued; finished ones exit at once
-    }
-    if (launches) *launches += 2;  // k_set_desc, k_output
     const size_t n3 = (size_t)3 * H * W;
-    const int ob = (int)((n3 + 255) / 256 < 152 * 16 ? (n3 + 255) / 256 : 152 * 16);
-    k_output<<<ob, 256, 0, s>>>(desc_dev, J);
+    char *ub = ws + L.ub;
+    float *ub32 = (float *)ub;
+    const int storage = p->storage;
+    const bool is16 = storage != DH_STORE_F32;
+    const bool bf = storage == DH_STORE_BF16 || storage == DH_STORE_BF16_F32;
+    const bool switched = storage == DH_STORE_BF16_F32 || storage == DH_STORE_F16_F32;
+    int rc = DH_OK;
+    if (loop_begin) DH_CUDA_TRY(cudaEventRecord(loop_begin, s));
+    if (!is16) {
+        v.u[0] = u_caller;
+        v.u[1] = ub32;
+        v.phase_stop = 0;
+        rc = queue_loop<float>(v, desc1, true, p, L, s, launches);
+        if (rc) return rc;
+        if (loop_end) DH_CUDA_TRY(cudaEventRecord(loop_end, s));
+        k_output<float><<<grid_for(n3), 256, 0, s>>>(desc1, J, u_caller);
+    } else {
+        void *b0 = ub;
+        void *b1 = ub + align_up(n3 * 2);
+        v.u[0] = b0;
+        v.u[1] = b1;
+        v.phase_stop = switched ? 1 : 0;
+        if (bf) {
+            k_convert<float, __nv_bfloat16><<<grid_for(n3), 256, 0, s>>>(u_caller, (__nv_bfloat16 *)b0, n3);
+            rc = queue_loop<__nv_bfloat16>(v, desc1, true, p, L, s, launches);
+        } else {
+            k_convert<float, __half><<<grid_for(n3), 256, 0, s>>>(u_caller, (__half *)b0, n3);
+            rc = queue_loop<__half>(v, desc1, true, p, L, s, launches);
+        }
+        if (rc) return rc;
+        if (launches) *launches += 1;
+        if (switched) {
+            if (bf)
+                k_phase_convert<__nv_bfloat16><<<grid_for(n3), 256, 0, s>>>(desc1, u_caller);
+            else
+                k_phase_convert<__half><<<grid_for(n3), 256, 0, s>>>(desc1, u_caller);
+            k_phase_state<<<1, 1, 0, s>>>(v.st);
+            SolveDesc v2 = v;
+            v2.u[0] = u_caller;
+            v2.u[1] = ub32;
+            v2.phase_stop = 0;
+            rc = queue_loop<float>(v2, desc2, false, p, L, s, launches);
+            if (rc) return rc;
+            if (loop_end) DH_CUDA_TRY(cudaEventRecord(loop_end, s));
+            k_output<float><<<grid_for(n3), 256, 0, s>>>(desc2, J, u_caller);
+            if (launches) *launches += 2;
+        } else {
+            if (loop_end) DH_CUDA_TRY(cudaEventRecord(loop_end, s));
+            if (bf)
+                k_output<__nv_bfloat16><<<grid_for(n3), 256, 0, s>>>(desc1, J, u_caller);
+            else
+                k_output<__half><<<grid_for(n3), 256, 0, s>>>(desc1, J, u_caller);
+        }
+    }
+    if (launches) *launches += 1;  // k_output
     DH_CUDA_TRY(cudaGetLastError());
     return DH_OK;
 }

@@ -19,18 +19,20 @@ def main():
     ap.add_argument("--iters", type=int, default=8)
     ap.add_argument("--preset", default="stable")
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--storage", type=int, default=0, help="0 f32, 1 bf16, 2 f16, 3 bf16->f32, 4 f16->f32")
+    ap.add_argument("--tol", type=float, default=0.0)
     ap.add_argument("--host-loop", action="store_true",
                     help="queue the sweeps from the host instead of the graph loop (profilers cannot "
                          "see kernels inside a graph with conditional nodes)")
     a = ap.parse_args()
     I = torch.from_numpy(scenes.hazy_scene(a.seed, a.H, a.W)["I"]).cuda()
-    d = api.Dehazer(a.H, a.W, api.params(a.preset, tol=0.0, max_iter=a.iters,
+    d = api.Dehazer(a.H, a.W, api.params(a.preset, tol=a.tol, max_iter=a.iters, storage=a.storage,
                                                    use_graph=0 if a.host_loop else 1))
     for _ in range(a.repeat):
         rep = d(I)
     torch.cuda.synchronize()
     print(f"{a.H}x{a.W}: {rep.n_iter} iterations, {rep.ms:.3f} ms, loop {rep.ms_loop:.3f} ms, "
-          f"{rep.launches} launches")
+          f"{rep.launches} launches, status {rep.status}, rho {max(rep.rho):.3e}")
 
 
 if __name__ == "__main__":
