@@ -166,6 +166,29 @@ int dh_dehaze(const float *I, int H, int W, const dh_params *p, const float *u0,
               float *u, float *t, float *A, void *workspace, size_t workspace_bytes,
               void *stream, dh_report *report);
 
+/* One image of a batch: inputs I (3xHxW) and optional u0, outputs J, u
+ * (3xHxW), t (HxW) and A (float[3]); all device pointers, caller-owned. */
+typedef struct dh_image {
+    const float *I;
+    int H, W;
+    const float *u0;
+    float *J, *u, *t, *A;
+} dh_image;
+
+/* Workspace bytes dh_dehaze_batch needs for these images (0 if invalid). */
+size_t dh_batch_workspace_bytes(int n, const dh_image *imgs, const dh_params *p);
+
+/* The whole method on n <= 256 images of any sizes (float32 storage).  The
+ * front end (Sec. II-D, II-A) runs per image; the fixed-point loops (App. A-A)
+ * of all images run in one CUDA graph while loop whose body is ONE persistent
+ * sweep launch over the (128x32 tile, channel) items of every image still
+ * iterating; each image stops on its own residual or max_iter, exactly as in
+ * dh_dehaze, and leaves the batch's work list.  reports: host array of n or
+ * NULL; with reports the call waits and reports[i].ms is the batch's time.
+ * Returns the first error, else the first warning, else DH_OK. */
+int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *workspace,
+                    size_t workspace_bytes, void *stream, dh_report *reports);
+
 /* dh_atmospheric_light without a workspace and without any allocation.
  * The paper has no counterpart: this exists for callers that cannot call
  * cudaMalloc, such as a plug-in whose host application owns all device memory,

@@ -28,7 +28,7 @@ DH_VAR_NO_ADAPTIVE, DH_VAR_NO_EDGE, DH_VAR_NO_NONLOCAL = 1, 2, 4
 # Every symbol include/dehaze.h declares.
 EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes",
            "dh_dark_channel", "dh_atmospheric_light", "dh_transmission", "dh_fixed_point",
-           "dh_dehaze", "dh_atmospheric_light_noalloc")
+           "dh_dehaze", "dh_batch_workspace_bytes", "dh_dehaze_batch", "dh_atmospheric_light_noalloc")
 
 
 class DhParams(ctypes.Structure):
@@ -75,6 +75,19 @@ class DhReport(ctypes.Structure):
     ]
 
 
+class DhImage(ctypes.Structure):
+    _fields_ = [
+        ("I", ctypes.c_void_p),
+        ("H", ctypes.c_int),
+        ("W", ctypes.c_int),
+        ("u0", ctypes.c_void_p),
+        ("J", ctypes.c_void_p),
+        ("u", ctypes.c_void_p),
+        ("t", ctypes.c_void_p),
+        ("A", ctypes.c_void_p),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -107,6 +120,8 @@ def lib(build_if_missing: bool = True):
             "dh_fixed_point": ([P, P, P, I, I, PP, P, P, S, P, PR], I),
             "dh_dehaze": ([P, I, I, PP, P, P, P, P, P, P, S, P, PR], I),
             "dh_atmospheric_light_noalloc": ([P, P, I, I, I, P, P, P], I),
+            "dh_batch_workspace_bytes": ([I, ctypes.POINTER(DhImage), PP], S),
+            "dh_dehaze_batch": ([I, ctypes.POINTER(DhImage), PP, P, S, P, PR], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -189,3 +204,18 @@ def dh_atmospheric_light_noalloc(I, dc, H, W, topk_permille, A_out, index_out, s
     place of a caller workspace (for callers that may not allocate)."""
     return lib().dh_atmospheric_light_noalloc(_p(I), _p(dc), H, W, topk_permille, _p(A_out), _p(index_out),
                                               _stream(stream))
+
+
+def dh_image(I, H, W, u0, J, u, t, A) -> DhImage:
+    return DhImage(_p(I), H, W, _p(u0), _p(J), _p(u), _p(t), _p(A))
+
+
+def dh_batch_workspace_bytes(n, imgs, p: DhParams) -> int:
+    arr = (DhImage * n)(*imgs)
+    return lib().dh_batch_workspace_bytes(n, arr, ctypes.byref(p))
+
+
+def dh_dehaze_batch(n, imgs, p: DhParams, workspace, workspace_bytes, stream=None, reports=None) -> int:
+    """imgs: sequence of DhImage; reports: ctypes array of n DhReport or None."""
+    arr = (DhImage * n)(*imgs)
+    return lib().dh_dehaze_batch(n, arr, ctypes.byref(p), _p(workspace), workspace_bytes, _stream(stream), reports)

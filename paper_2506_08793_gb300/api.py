@@ -124,3 +124,52 @@ def dehaze(I: torch.Tensor, p: DhParams | None = None, u0: torch.Tensor | None =
     d = Dehazer(H, W, p, I.device)
     rep = d(I, u0)
     return dict(J=d.J, u=d.u, t=d.t, A=d.A, report=rep)
+
+
+class BatchDehazer:
+    """The whole method on a fixed list of image shapes, solved together: one
+    persistent sweep launch per iteration over every image still iterating.
+    Outputs and workspace stay resident between calls."""
+
+    def __init__(self, shapes, p: DhParams | None = None, device="cuda"):
+        import ctypes
+
+        self.shapes = [tuple(map(int, s)) for s in shapes]
+        self.p = p or params()
+        self.device = torch.device(device)
+        self.out = []
+        for H, W in self.shapes:
+            self.out.append(dict(J=torch.empty((3, H, W), dtype=torch.float32, device=self.device),
+                                 u=torch.empty((3, H, W), dtype=torch.float32, device=self.device),
+                                 t=torch.empty((H, W), dtype=torch.float32, device=self.device),
+                                 A=torch.empty(3, dtype=torch.float32, device=self.device)))
+        self._reports = (DhReport * len(self.shapes))()
+        probe = [N.dh_image(None, H, W, None, o["J"], o["u"], o["t"], o["A"])
+                 for (H, W), o in zip(self.shapes, self.out)]
+        nb = N.dh_batch_workspace_bytes(len(probe), probe, self.p)
+        if nb == 0:
+            raise ValueError("invalid batch")
+        self.ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self._ctypes = ctypes
+
+    def __call__(self, images, u0s=None, report: bool = True, stream=None):
+        if len(images) != len(self.shapes):
+            raise ValueError("wrong number of images")
+        imgs = []
+        for k, (I, (H, W), o) in enumerate(zip(images, self.shapes, self.out)):
+            if _img(I) != (H, W):
+                raise ValueError(f"image {k} has the wrong shape")
+            u0 = None if u0s is None else u0s[k]
+            imgs.append(N.dh_image(I, H, W, u0, o["J"], o["u"], o["t"], o["A"]))
+        rc = N.dh_dehaze_batch(len(imgs), imgs, self.p, self.ws, self.ws.numel(), _stream(stream),
+                               self._reports if report else None)
+        _check(rc, "dh_dehaze_batch")
+        return [DhReport.from_buffer_copy(r) for r in self._reports] if report else None
+
+
+def dehaze_batch(images, p: DhParams | None = None):
+    """Several images of any sizes in one batched solve; returns one dict per
+    image (J, u, t, A, report)."""
+    b = BatchDehazer([tuple(I.shape[1:]) for I in images], p, images[0].device)
+    reps = b(images)
+    return [dict(o, report=r) for o, r in zip(b.out, reps)]

@@ -1,0 +1,529 @@
+// Batched dehazing of images of uneven sizes.  The front end runs per image;
+// the fixed-point loops of all images share one CUDA graph while loop whose
+// body is a single persistent sweep launch over the (tile, channel) items of
+// every image that is still iterating.  Each image stops on its own residual
+// (App. A-A, stop rule as in the single-image path); the launch's last CTA
+// compacts the list of active images and ends the loop when it is empty.
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "sweep.cuh"
+
+namespace dh {
+
+int launch_dark_channel(const float *I, int H, int W, int patch, const float *A, float *out, cudaStream_t s);
+int launch_transmission(const float *I, int H, int W, const dh_params *p, const float *A, float *td, float *t,
+                        float *lam, float *phi, float *u0, float2 *phin_part, cudaStream_t s);
+int launch_phin_final(const float2 *part, int H, int W, SolveState *st, cudaStream_t s);
+int launch_select_A(const float *I, const float *dc, int H, int W, int permille, float *A,
+                    long long *index_out, char *ws, const WsLayout &L, cudaStream_t s);
+int launch_output_f32(const SolveDesc *desc_dev, float *J, float *u, size_t n3, cudaStream_t s);
+int encode_f32_map(CUtensorMap *m, const void *base, int rank, int W, int H, int C, int boxW, int boxH);
+int sweep_tile_h(int depth);
+
+constexpr int kMaxBatch = 256;
+constexpr int kBR = 8, kBNW = 4, kBTH = kBR * kBNW;  // 128 x 32 tiles, 4 warps
+
+// Per-image loop data in device memory.
+struct __align__(128) BImg {
+    CUtensorMap tm[4];  // u buffer 0, u buffer 1, Phi, lambda (when tma)
+    SolveDesc d;        // per-image descriptor (use_cond = 0: the batch owns the loop)
+    int ntx, items, tma, pad;
+};
+
+struct BatchHdr {
+    BImg *imgs;
+    int nimg;
+    int nactive;
+    unsigned arrive;
+    int use_cond;
+    unsigned long long cond;
+    int active[kMaxBatch];
+    int prefix[kMaxBatch + 1];  // items before each active image
+};
+
+struct BatchLayout {
+    size_t hdr, imgs, img0, total;
+    std::vector<size_t> off;  // per-image workspace offsets
+};
+
+static WsLayout img_layout(int H, int W) { return ws_layout(H, W, 1, sweep_tile_h(1)); }
+
+static BatchLayout batch_layout(int n, const dh_image *im) {
+    BatchLayout B;
+    size_t o = 0;
+    B.hdr = o; o = align_up(o + sizeof(BatchHdr));
+    B.imgs = o; o = align_up(o + (size_t)n * sizeof(BImg));
+    B.img0 = o;
+    for (int i = 0; i < n; ++i) {
+        B.off.push_back(o);
+        o = align_up(o + img_layout(im[i].H, im[i].W).total);
+    }
+    B.total = o;
+    return B;
+}
+
+// Host -> device copy of a few BImg records through kernel parameters (no
+// staging allocation), plus the reset of each image's iteration state.
+constexpr int kPutChunk = 4;
+struct PutChunk {
+    BImg rec[kPutChunk];
+};
+
+__global__ void k_batch_put(BImg *dst, const __grid_constant__ PutChunk ch, int count) {
+    const int words = (int)(sizeof(BImg) / 4);
+    for (int r = 0; r < count; ++r) {
+        const unsigned *src = reinterpret_cast<const unsigned *>(&ch.rec[r]);
+        unsigned *d = reinterpret_cast<unsigned *>(dst + r);
+        for (int k = threadIdx.x; k < words; k += blockDim.x) d[k] = src[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < count) {
+        SolveState *st = ch.rec[threadIdx.x].d.st;
+        st->arrive = 0;
+        st->n = 0;
+        st->cur = 0;
+        st->done = 0;
+        st->status = 0;
+        st->n_final = 0;
+        st->err = 0;
+        st->phase_start = 0;
+    }
+    __threadfence();
+    tensormap_release();
+}
+
+__global__ void k_batch_init(BatchHdr *h, BImg *imgs, int n, int use_cond, unsigned long long cond) {
+    if (threadIdx.x != 0) return;
+    h->imgs = imgs;
+    h->nimg = n;
+    h->nactive = n;
+    h->arrive = 0;
+    h->use_cond = use_cond;
+    h->cond = cond;
+    int acc = 0;
+    for (int i = 0; i < n; ++i) {
+        h->active[i] = i;
+        h->prefix[i] = acc;
+        acc += imgs[i].items;
+    }
+    h->prefix[n] = acc;
+}
+
+template <bool EDGE>
+__global__ void __launch_bounds__(kBNW * 32)
+k_sweep_batch(BatchHdr *__restrict__ hb) {
+    using P = TmaPlan<kBTH, true, float>;
+    constexpr int SW = P::SW, SH = P::SH;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sb = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float2 red[kBNW];
+    __shared__ int s_last, s_img_last;
+    __shared__ int s_active[kMaxBatch];
+    __shared__ int s_prefix[kMaxBatch + 1];
+
+    if (hb->use_cond && (blockIdx.x | threadIdx.x) == 0) {
+        cudaGraphSetConditional(hb->cond, 0);  // the last CTA sets it back while images remain
+        __threadfence();
+    }
+    const int nact = __ldcg(&hb->nactive);
+    for (int k = threadIdx.x; k < nact; k += blockDim.x) s_active[k] = __ldcg(&hb->active[k]);
+    for (int k = threadIdx.x; k <= nact; k += blockDim.x) s_prefix[k] = __ldcg(&hb->prefix[k]);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int total = s_prefix[nact];
+    BImg *imgs = hb->imgs;
+    const int G = gridDim.x;
+    float *s = reinterpret_cast<float *>(sb + P::U_OFF);
+    float *sphi = reinterpret_cast<float *>(sb + P::PHI_OFF);
+    float *slam = reinterpret_cast<float *>(sb + P::LAM_OFF);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+
+    // item -> (image, tile, channel)
+    auto locate = [&](int item, int &img, int &tile, int &c) {
+        int lo = 0, hi = nact - 1;  // last k with prefix[k] <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_prefix[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        img = s_active[lo];
+        const int j = item - s_prefix[lo];
+        tile = j / 3;
+        c = j - 3 * tile;
+    };
+    auto issue = [&](int item) {  // thread 0, TMA images only
+        int img, tile, c;
+        locate(item, img, tile, c);
+        BImg *im = imgs + img;
+        if (!im->tma) return;
+        const SolveDesc &d = im->d;
+        const int x0 = (tile % im->ntx) * kTW, y0 = (tile / im->ntx) * kBTH;
+        const int cur = __ldcg(&d.st->cur);
+        const CUtensorMap *tu = &im->tm[cur];
+        tensormap_acquire(tu);
+        tensormap_acquire(&im->tm[2]);
+        tensormap_acquire(&im->tm[3]);
+        mbar_arrive_expect_tx(&bar, P::TX);
+        tma_load_3d(sb + P::U_OFF, tu, &bar, x0 - 4, y0 - 2, c);
+        tma_load_3d(sb + P::PHI_OFF, &im->tm[2], &bar, x0, y0, c);
+        tma_load_2d(sb + P::LAM_OFF, &im->tm[3], &bar, x0, y0);
+    };
+    if (threadIdx.x == 0 && (int)blockIdx.x < total) issue(blockIdx.x);
+
+    int kt = 0;  // TMA items waited for so far (barrier phase)
+    bool failed = false;
+    for (int item = blockIdx.x; item < total; item += G) {
+        int img, tile, c;
+        locate(item, img, tile, c);
+        BImg *im = imgs + img;
+        const SolveDesc *d = &im->d;
+        SolveState *st = d->st;
+        const int H = d->H, W = d->W;
+        const size_t N = (size_t)H * W;
+        const int ntx = im->ntx;
+        const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * kBTH;
+        const int cur = __ldcg(&st->cur);
+        if (im->tma) {
+            const bool ok = mbar_wait_bounded(&bar, kt & 1, kWaitLimitCycles);
+            ++kt;
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            if (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + kBTH + 2 > H) {
+                for (int e = threadIdx.x; e < SH * SW; e += kBNW * 32) {
+                    const int r = e / SW, q = e - r * SW;
+                    const int gy = y0 - 2 + r, gx = x0 - 4 + q;
+                    const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
+                    const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
+                    const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
+                    if ((fy && (inx || fx)) || (fx && iny)) {
+                        const int sy = reflect_idx(gy, H) - (y0 - 2), sx = reflect_idx(gx, W) - (x0 - 4);
+                        s[e] = s[sy * SW + sx];
+                    }
+                }
+                fence_proxy_async_smem();
+            }
+        } else {
+            // gather the tile with the reflecting boundary (W % 4 != 0 or unaligned image)
+            const float *u = static_cast<const float *>(d->u[cur]) + c * N;
+            for (int e = threadIdx.x; e < SH * SW; e += kBNW * 32) {
+                const int r = e / SW, q = e - r * SW;
+                s[e] = u[(size_t)reflect_idx(y0 - 2 + r, H) * W + reflect_idx(x0 - 4 + q, W)];
+            }
+            for (int e = threadIdx.x; e < kBTH * kTW; e += kBNW * 32) {
+                const int r = e / kTW, q = e - r * kTW;
+                const int y = y0 + r, x = x0 + q;
+                const bool in = y < H && x < W;
+                sphi[e] = in ? d->phi[c * N + (size_t)y * W + x] : 0.f;
+                slam[e] = in ? d->lam[(size_t)y * W + x] : 0.f;
+            }
+            fence_proxy_async_smem();
+        }
+        __syncthreads();
+
+        float *__restrict__ un = static_cast<float *>(d->u[cur ^ 1]) + c * N;
+        const int x = x0 + 4 * lane;
+        const bool vec = im->tma != 0;  // aligned planes, W % 4 == 0
+        float rs = 0.f, rc = 0.f;
+        auto pl = [&](int ty, float *ph, float *la) {
+            const float4 p4 = *reinterpret_cast<const float4 *>(sphi + ty * kTW + 4 * lane);
+            const float4 l4 = *reinterpret_cast<const float4 *>(slam + ty * kTW + 4 * lane);
+            ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
+            la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
+        };
+        auto sink = [&](int ty, const float *nu, const float *F) {
+            const int y = y0 + ty;
+            if (y >= H || x >= W) return;
+            const size_t ro = (size_t)y * W;
+            float q = 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (x + j < W) q = fmaf(F[j], F[j], q);
+            neumaier_add(rs, rc, q);
+            if (vec) {
+                *reinterpret_cast<float4 *>(un + ro + x) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (x + j < W) un[ro + x + j] = nu[j];
+            }
+        };
+        walk_rows<kBR, SW, float, EDGE>(s, w * kBR, lane, d->eps, d->tau, d->wg0, d->wg1, d->wg2, pl, sink);
+
+        const float2 tot = block_pair_sum<kBNW>(rs, rc, red);  // ends with a barrier
+        if (threadIdx.x == 0) {
+            d->part[(size_t)c * d->nblk + tile] = tot;
+            __threadfence();
+            const unsigned prev = atomicAdd(&st->arrive, 1u);
+            s_img_last = prev == (unsigned)im->items - 1u;
+        }
+        __syncthreads();
+        if (s_img_last) finish_iteration(d, st);  // this image's iteration is complete
+        if (threadIdx.x == 0 && item + G < total) {
+            fence_proxy_async_smem();
+            issue(item + G);
+        }
+        __syncthreads();
+    }
+    if (failed) {
+        if (threadIdx.x == 0) {
+            mbar_wait_bounded(&bar, kt & 1, kWaitLimitCycles);  // the load already issued
+            for (int k = 0; k < nact; ++k) atomicCAS(&imgs[s_active[k]].d.st->err, 0, DH_ETIMEOUT);
+        }
+    }
+    // last CTA: compact the active list, keep the loop going while it is not empty
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&hb->arrive, 1u);
+        s_last = prev == gridDim.x - 1u;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        int k = 0, acc = 0;
+        for (int i = 0; i < hb->nimg; ++i) {
+            SolveState *st = imgs[i].d.st;
+            if (__ldcg(&st->done)) continue;
+            const int err = __ldcg(&st->err);
+            if (err) {  // a bounded wait gave up: this image stops with the error
+                st->done = 1;
+                st->status = err;
+                st->n_final = st->n;
+                continue;
+            }
+            hb->active[k] = i;
+            hb->prefix[k] = acc;
+            acc += imgs[i].items;
+            ++k;
+        }
+        hb->prefix[k] = acc;
+        hb->nactive = k;
+        hb->arrive = 0;
+        __threadfence();
+        if (hb->use_cond && k > 0) cudaGraphSetConditional(hb->cond, 1);
+    }
+}
+
+// ------------------------------------------------------------ host
+
+struct BatchGraph {
+    int dev;
+    const void *hdr;
+    int grid;
+    int edge;
+    cudaGraphExec_t exec;
+    cudaGraphConditionalHandle cond;
+};
+static std::mutex g_bmu;
+static std::vector<BatchGraph> g_bcache;
+
+static int batch_graph(int dev, BatchHdr *hdr, int grid, bool edge, unsigned smem, BatchGraph *out) {
+    std::lock_guard<std::mutex> lk(g_bmu);
+    for (auto &e : g_bcache)
+        if (e.dev == dev && e.hdr == hdr && e.grid == grid && e.edge == (edge ? 1 : 0)) {
+            *out = e;
+            return DH_OK;
+        }
+    cudaGraph_t g = nullptr;
+    DH_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t err = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t wn;
+    if (err == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        err = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &cp);
+    }
+    if (err == cudaSuccess) {
+        cudaKernelNodeParams kp = {};
+        void *args[] = {(void *)&hdr};
+        kp.func = edge ? (void *)k_sweep_batch<true> : (void *)k_sweep_batch<false>;
+        kp.gridDim = dim3(grid);
+        kp.blockDim = dim3(kBNW * 32);
+        kp.sharedMemBytes = smem;
+        kp.kernelParams = args;
+        cudaGraphNode_t kn;
+        err = cudaGraphAddKernelNode(&kn, cp.conditional.phGraph_out[0], nullptr, 0, &kp);
+    }
+    cudaGraphExec_t exec = nullptr;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (err != cudaSuccess) return cuda_fail(err);
+    if (g_bcache.size() >= 8) {
+        cudaGraphExecDestroy(g_bcache.front().exec);
+        g_bcache.erase(g_bcache.begin());
+    }
+    BatchGraph e{dev, hdr, grid, edge ? 1 : 0, exec, h};
+    g_bcache.push_back(e);
+    *out = e;
+    return DH_OK;
+}
+
+static bool image_ok(const dh_image &m) {
+    return m.I && m.J && m.u && m.t && m.A && shape_ok(m.H, m.W);
+}
+
+}  // namespace dh
+
+using namespace dh;
+
+extern "C" {
+
+size_t dh_batch_workspace_bytes(int n, const dh_image *imgs, const dh_params *p) {
+    if (n < 1 || n > kMaxBatch || !imgs || !p) return 0;
+    for (int i = 0; i < n; ++i)
+        if (!shape_ok(imgs[i].H, imgs[i].W)) return 0;
+    if (dh_workspace_bytes(1, 1, p) == 0) return 0;
+    return batch_layout(n, imgs).total;
+}
+
+int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *workspace, size_t workspace_bytes,
+                    void *stream, dh_report *reports) {
+    if (n < 1 || n > kMaxBatch || !imgs || !p) return DH_EINVAL;
+    if (dh_workspace_bytes(1, 1, p) == 0 || p->storage != DH_STORE_F32) return DH_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!image_ok(imgs[i])) return DH_EINVAL;
+    const BatchLayout B = batch_layout(n, imgs);
+    if (!workspace || ((uintptr_t)workspace % kAlign) || workspace_bytes < B.total) return DH_EWORKSPACE;
+    char *ws = (char *)workspace;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (reports) {
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        cudaEventRecord(e0, s);
+    }
+    // front end per image (Sec. II-D, II-A)
+    std::vector<BImg> recs(n);
+    int total_items = 0;
+    for (int i = 0; i < n; ++i) {
+        const dh_image &m = imgs[i];
+        char *iw = ws + B.off[i];
+        const WsLayout L = img_layout(m.H, m.W);
+        float *dc = (float *)(iw + L.dc), *lam = (float *)(iw + L.lam), *phi = (float *)(iw + L.phi);
+        int rc = launch_dark_channel(m.I, m.H, m.W, p->patch, nullptr, dc, s);
+        if (!rc) rc = launch_select_A(m.I, dc, m.H, m.W, p->topk_permille, m.A, nullptr, iw, L, s);
+        if (!rc) rc = launch_transmission(m.I, m.H, m.W, p, m.A, nullptr, m.t, lam, phi, m.u0 ? nullptr : m.u,
+                                          (float2 *)(iw + L.phin_part), s);
+        if (rc) return rc;
+        if (m.u0)
+            DH_CUDA_TRY(cudaMemcpyAsync(m.u, m.u0, (size_t)3 * m.H * m.W * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        rc = launch_phin_final((const float2 *)(iw + L.phin_part), m.H, m.W, (SolveState *)(iw + L.state), s);
+        if (rc) return rc;
+        BImg &r = recs[i];
+        std::memset(&r, 0, sizeof(r));
+        SolveDesc &d = r.d;
+        d.u[0] = m.u;
+        d.u[1] = iw + L.ub;
+        d.phi = phi;
+        d.lam = lam;
+        d.part = (float2 *)(iw + L.part);
+        d.st = (SolveState *)(iw + L.state);
+        d.H = m.H;
+        d.W = m.W;
+        d.max_iter = p->max_iter;
+        d.depth = 1;
+        d.tol = p->tol;
+        d.tau = p->tau;
+        d.eps = p->eps;
+        double wgt[3];
+        for (int k = 0; k <= 2; ++k) wgt[k] = exp(-(double)(k * k) / (2.0 * (double)p->sigma * p->sigma));
+        const double sum = wgt[0] + 2.0 * (wgt[1] + wgt[2]);
+        d.wg0 = (float)(wgt[0] / sum);
+        d.wg1 = (float)(wgt[1] / sum);
+        d.wg2 = (float)(wgt[2] / sum);
+        r.ntx = (m.W + kTW - 1) / kTW;
+        d.nblk = r.ntx * ((m.H + kBTH - 1) / kBTH);
+        r.items = 3 * d.nblk;
+        total_items += r.items;
+        auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+        r.tma = (m.W % 4 == 0) && a16(d.u[0]) && a16(d.u[1]) && a16(phi) && a16(lam);
+        if (r.tma) {
+            int e = encode_f32_map(&r.tm[0], d.u[0], 3, m.W, m.H, 3, kTW + 8, kBTH + 4);
+            if (!e) e = encode_f32_map(&r.tm[1], d.u[1], 3, m.W, m.H, 3, kTW + 8, kBTH + 4);
+            if (!e) e = encode_f32_map(&r.tm[2], phi, 3, m.W, m.H, 3, kTW, kBTH);
+            if (!e) e = encode_f32_map(&r.tm[3], lam, 2, m.W, m.H, 1, kTW, kBTH);
+            if (e) return e;
+        }
+    }
+    BImg *dimgs = (BImg *)(ws + B.imgs);
+    for (int i = 0; i < n; i += kPutChunk) {
+        PutChunk ch;
+        const int cnt = n - i < kPutChunk ? n - i : kPutChunk;
+        for (int k = 0; k < cnt; ++k) ch.rec[k] = recs[i + k];
+        k_batch_put<<<1, 128, 0, s>>>(dimgs + i, ch, cnt);
+    }
+    DH_CUDA_TRY(cudaGetLastError());
+    // the batched loop
+    const bool edge = !(p->variant & DH_VAR_NO_EDGE);
+    const unsigned smem = TmaPlan<kBTH, true, float>::STAGE + 1024;
+    void *fn = edge ? (void *)k_sweep_batch<true> : (void *)k_sweep_batch<false>;
+    int dev = 0, per_sm = 0, sms = 0;
+    DH_CUDA_TRY(cudaGetDevice(&dev));
+    DH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBNW * 32, smem));
+    DH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = total_items < per_sm * sms ? total_items : per_sm * sms;
+    BatchHdr *hdr = (BatchHdr *)(ws + B.hdr);
+    int launches = 0;
+    if (p->use_graph) {
+        BatchGraph bg;
+        int rc = batch_graph(dev, hdr, grid, edge, smem, &bg);
+        if (rc) return rc;
+        k_batch_init<<<1, 32, 0, s>>>(hdr, dimgs, n, 1, bg.cond);
+        DH_CUDA_TRY(cudaGraphLaunch(bg.exec, s));
+    } else {
+        k_batch_init<<<1, 32, 0, s>>>(hdr, dimgs, n, 0, 0);
+        void *args[] = {(void *)&hdr};
+        for (int it = 0; it <= p->max_iter; ++it) DH_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kBNW * 32), args, smem, s));
+        launches += p->max_iter + 1;
+    }
+    for (int i = 0; i < n; ++i) {
+        int rc = launch_output_f32(&dimgs[i].d, imgs[i].J, imgs[i].u, (size_t)3 * imgs[i].H * imgs[i].W, s);
+        if (rc) return rc;
+    }
+    DH_CUDA_TRY(cudaGetLastError());
+    if (!reports) return DH_OK;
+    float ms = 0.f;
+    cudaEventRecord(e1, s);
+    DH_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaGetLastError();
+    int worst = DH_OK, max_n = 0;
+    for (int i = 0; i < n; ++i) {
+        SolveState st;
+        SelectState sel;
+        const WsLayout L = img_layout(imgs[i].H, imgs[i].W);
+        DH_CUDA_TRY(cudaMemcpy(&st, ws + B.off[i] + L.state, sizeof(st), cudaMemcpyDeviceToHost));
+        DH_CUDA_TRY(cudaMemcpy(&sel, ws + B.off[i] + L.sel, sizeof(sel), cudaMemcpyDeviceToHost));
+        dh_report &r = reports[i];
+        std::memset(&r, 0, sizeof(r));
+        r.status = st.status;
+        if (r.status == DH_OK && sel.clamped) r.status = DH_WDEGENERATE;
+        r.n_iter = st.n_final;
+        for (int c = 0; c < 3; ++c) r.rho[c] = st.rho[c];
+        DH_CUDA_TRY(cudaMemcpy(r.A, imgs[i].A, 3 * sizeof(float), cudaMemcpyDeviceToHost));
+        r.a_index = sel.best;
+        r.ms = ms;  // the whole batch
+        r.launches = 18 + 1;  // front end + output of this image
+        if (st.n_final > max_n) max_n = st.n_final;
+        if (r.status < 0 && worst >= 0) worst = r.status;
+        else if (worst == DH_OK && r.status > 0) worst = r.status;
+    }
+    reports[0].launches += (p->use_graph ? max_n + 1 : launches) + 1 + (n + kPutChunk - 1) / kPutChunk;
+    return worst;
+}
+
+}  // extern "C"

@@ -67,6 +67,15 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// A tensor map written to global memory by generic stores must be released to
+// the tensor-map proxy by the writer and acquired by the thread that uses it.
+__device__ __forceinline__ void tensormap_release() {
+    asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+}
+__device__ __forceinline__ void tensormap_acquire(const void *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
+
 // Host: encodes a float32 tensor map of rank 2 or 3 over a planar image stack
 // (dims W, H[, C]); out-of-bounds box elements read as zero.
 int encode_f32_map(CUtensorMap *m, const void *base, int rank, int W, int H, int C, int boxW, int boxH);

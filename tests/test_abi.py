@@ -86,3 +86,9 @@ def test_invalid_arguments_rejected_on_host():
     assert N.dh_dehaze(fake, 8, 8, p, None, fake, fake, fake, fake, fake, 16) == N.DH_EWORKSPACE
     assert N.dh_dehaze(fake, 8, 8, p.replace(storage=9), None, fake, fake, fake, fake, fake, 1 << 30) == N.DH_EINVAL
     assert N.dh_atmospheric_light(fake, fake, 8, 8, 0, fake, None, fake, 1 << 30) == N.DH_EINVAL
+    img = N.dh_image(fake, 8, 8, None, fake, fake, fake, fake)
+    assert N.dh_batch_workspace_bytes(1, [img], p) > 0
+    assert N.dh_batch_workspace_bytes(1, [N.dh_image(fake, 0, 8, None, fake, fake, fake, fake)], p) == 0
+    assert N.dh_dehaze_batch(1, [img], p, None, 0) == N.DH_EWORKSPACE
+    assert N.dh_dehaze_batch(1, [N.dh_image(None, 8, 8, None, fake, fake, fake, fake)], p, fake, 1 << 30) == N.DH_EINVAL
+    assert N.dh_dehaze_batch(1, [img], p.replace(storage=1), fake, 1 << 30) == N.DH_EINVAL

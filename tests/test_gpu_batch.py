@@ -1,0 +1,83 @@
+"""Batched solve of images of uneven sizes (one persistent sweep launch per
+iteration over every still-active image, in one graph while loop) against
+the single-image path and the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from paper_2506_08793_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_08793_gb300 import _native, api as a
+
+    _native.lib()
+    return a
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+SHAPES = [(64, 128), (61, 83), (130, 264), (1, 1), (33, 4), (96, 40), (200, 130)]
+
+
+def test_batch_matches_single_image_path(api):
+    imgs = [torch.from_numpy(scenes.hazy_scene(300 + k, H, W)["I"]).cuda() for k, (H, W) in enumerate(SHAPES)]
+    p = api.params("stable")
+    outs = api.dehaze_batch(imgs, p)
+    for k, (I, o) in enumerate(zip(imgs, outs)):
+        one = api.dehaze(I, p)
+        ro, rb = one["report"], o["report"]
+        assert rb.status == 0 and max(rb.rho) <= 1e-4, k
+        assert torch.equal(one["A"], o["A"]) and torch.equal(one["t"], o["t"]), k
+        assert rb.a_index == ro.a_index
+        assert abs(rb.n_iter - ro.n_iter) <= 1, (k, rb.n_iter, ro.n_iter)
+        if rb.n_iter == ro.n_iter:
+            d = np.abs(host(o["u"]) - host(one["u"]))
+            assert np.max(d / np.maximum(1.0, np.abs(host(one["u"])))) <= 1e-6, k
+            assert torch.equal(torch.clamp(o["u"], 0, 1), o["J"])
+
+
+def test_batch_against_oracle(api, orc):
+    shapes = [(64, 128), (61, 83), (48, 52)]
+    Is = [scenes.hazy_scene(400 + k, H, W)["I"] for k, (H, W) in enumerate(shapes)]
+    outs = api.dehaze_batch([torch.from_numpy(I).cuda() for I in Is], api.params("stable"))
+    op = orc.params(**orc.STABLE)
+    for I, o in zip(Is, outs):
+        r = orc.dehaze(I, op, 5000, 1e-4)
+        n = o["report"].n_iter
+        assert abs(n - r["n"]) <= 1
+        assert o["report"].a_index == r["a_index"]
+        ou, _, _ = orc.solve(r["Phi"], r["Phi"], r["lam"], op, n, 0.0)
+        assert np.max(np.abs(host(o["u"]) - ou)) <= 1e-4
+        assert np.max(np.abs(host(o["J"]) - np.clip(ou, 0, 1))) <= 1e-4
+
+
+def test_batch_graph_equals_host_loop_and_max_iter(api):
+    imgs = [torch.from_numpy(scenes.hazy_scene(500 + k, H, W)["I"]).cuda() for k, (H, W) in enumerate(SHAPES[:4])]
+    a = api.dehaze_batch(imgs, api.params("stable", max_iter=60))
+    b = api.dehaze_batch(imgs, api.params("stable", max_iter=60, use_graph=0))
+    for x, y in zip(a, b):
+        assert x["report"].n_iter == y["report"].n_iter
+        assert torch.equal(x["u"], y["u"])
+        assert x["report"].status in (0, 2)
+
+
+def test_batch_uneven_full_sizes(api):
+    """Sizes drawn from the four photo sizes (480x640 .. 1200x1600)."""
+    sizes = scenes.batch_sizes(3000, 6)
+    imgs = [torch.from_numpy(scenes.hazy_scene(3000 + k, H, W)["I"]).cuda() for k, (H, W) in enumerate(sizes)]
+    outs = api.dehaze_batch(imgs, api.params("stable"))
+    for k, (I, o) in enumerate(zip(imgs, outs)):
+        assert o["report"].status == 0 and max(o["report"].rho) <= 1e-4
+        one = api.dehaze(I, api.params("stable"))
+        assert abs(one["report"].n_iter - o["report"].n_iter) <= 1
+        if one["report"].n_iter == o["report"].n_iter:
+            assert torch.allclose(one["u"], o["u"], rtol=1e-6, atol=1e-6)
