@@ -90,6 +90,8 @@ typedef struct dh_params {
     int variant;        /* DH_VAR_* bits, 0 = the full method */
     int use_graph;      /* 1: iteration loop in a CUDA graph with a device-side
                            while condition (default); 0: host-queued launches */
+    int sweep_variant;  /* sweep kernel variant (1..dh_sweep_variants()-1); 0 = the
+                           tuned choice for this shape if dh_tune ran, else default */
 } dh_params;
 
 typedef struct dh_report {
@@ -165,6 +167,31 @@ int dh_fixed_point(float *u, const float *Phi, const float *lam, int H, int W,
 int dh_dehaze(const float *I, int H, int W, const dh_params *p, const float *u0, float *J,
               float *u, float *t, float *A, void *workspace, size_t workspace_bytes,
               void *stream, dh_report *report);
+
+/* Timings of one dh_tune run. */
+typedef struct dh_tune_result {
+    int best;               /* fastest usable variant */
+    int count;              /* entries below */
+    int variant[32];        /* variant ids timed */
+    float us_per_iter[32];  /* device time per iteration (graph loop) */
+} dh_tune_result;
+
+/* Number of sweep variants (valid ids are 1 .. count-1). */
+int dh_sweep_variants(void);
+
+/* Autotuner (not in the paper): times every sweep variant usable for an HxW
+ * image under *p (float32 storage) on the caller's Phi, lambda (as for
+ * dh_fixed_point) for `iters` fixed-point iterations each, in the graph loop,
+ * with CUDA events on `stream`; u_scratch (3xHxW) is overwritten.  The fastest
+ * is recorded for (current device, H, W) and used by later calls with
+ * sweep_variant = 0.  Waits for the stream.  out may be NULL. */
+int dh_tune(const float *Phi, const float *lam, float *u_scratch, int H, int W, const dh_params *p,
+            int iters, void *workspace, size_t workspace_bytes, void *stream, dh_tune_result *out);
+
+/* Records / reads the tuned variant for (current device, H, W, storage), e.g.
+ * from a saved tuning table.  dh_tune_get returns 0 when none is recorded. */
+int dh_tune_set(int H, int W, int storage, int variant);
+int dh_tune_get(int H, int W, int storage);
 
 /* One image of a batch: inputs I (3xHxW) and optional u0, outputs J, u
  * (3xHxW), t (HxW) and A (float[3]); all device pointers, caller-owned. */

@@ -28,7 +28,8 @@ DH_VAR_NO_ADAPTIVE, DH_VAR_NO_EDGE, DH_VAR_NO_NONLOCAL = 1, 2, 4
 # Every symbol include/dehaze.h declares.
 EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes",
            "dh_dark_channel", "dh_atmospheric_light", "dh_transmission", "dh_fixed_point",
-           "dh_dehaze", "dh_batch_workspace_bytes", "dh_dehaze_batch", "dh_atmospheric_light_noalloc")
+           "dh_dehaze", "dh_batch_workspace_bytes", "dh_dehaze_batch", "dh_sweep_variants", "dh_tune",
+           "dh_tune_set", "dh_tune_get", "dh_atmospheric_light_noalloc")
 
 
 class DhParams(ctypes.Structure):
@@ -49,6 +50,7 @@ class DhParams(ctypes.Structure):
         ("storage", ctypes.c_int),
         ("variant", ctypes.c_int),
         ("use_graph", ctypes.c_int),
+        ("sweep_variant", ctypes.c_int),
     ]
 
     def replace(self, **kw) -> "DhParams":
@@ -72,6 +74,15 @@ class DhReport(ctypes.Structure):
         ("ms", ctypes.c_float),
         ("ms_loop", ctypes.c_float),
         ("launches", ctypes.c_int),
+    ]
+
+
+class DhTuneResult(ctypes.Structure):
+    _fields_ = [
+        ("best", ctypes.c_int),
+        ("count", ctypes.c_int),
+        ("variant", ctypes.c_int * 32),
+        ("us_per_iter", ctypes.c_float * 32),
     ]
 
 
@@ -122,6 +133,10 @@ def lib(build_if_missing: bool = True):
             "dh_atmospheric_light_noalloc": ([P, P, I, I, I, P, P, P], I),
             "dh_batch_workspace_bytes": ([I, ctypes.POINTER(DhImage), PP], S),
             "dh_dehaze_batch": ([I, ctypes.POINTER(DhImage), PP, P, S, P, PR], I),
+            "dh_sweep_variants": ([], I),
+            "dh_tune": ([P, P, P, I, I, PP, I, P, S, P, ctypes.POINTER(DhTuneResult)], I),
+            "dh_tune_set": ([I, I, I, I], I),
+            "dh_tune_get": ([I, I, I], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -219,3 +234,21 @@ def dh_dehaze_batch(n, imgs, p: DhParams, workspace, workspace_bytes, stream=Non
     """imgs: sequence of DhImage; reports: ctypes array of n DhReport or None."""
     arr = (DhImage * n)(*imgs)
     return lib().dh_dehaze_batch(n, arr, ctypes.byref(p), _p(workspace), workspace_bytes, _stream(stream), reports)
+
+
+def dh_sweep_variants() -> int:
+    return lib().dh_sweep_variants()
+
+
+def dh_tune(Phi, lam, u_scratch, H, W, p: DhParams, iters, workspace, workspace_bytes, stream=None,
+            out: DhTuneResult | None = None) -> int:
+    return lib().dh_tune(_p(Phi), _p(lam), _p(u_scratch), H, W, ctypes.byref(p), iters, _p(workspace),
+                         workspace_bytes, _stream(stream), _ref(out))
+
+
+def dh_tune_set(H, W, storage, variant) -> int:
+    return lib().dh_tune_set(H, W, storage, variant)
+
+
+def dh_tune_get(H, W, storage) -> int:
+    return lib().dh_tune_get(H, W, storage)

@@ -173,3 +173,45 @@ def dehaze_batch(images, p: DhParams | None = None):
     b = BatchDehazer([tuple(I.shape[1:]) for I in images], p, images[0].device)
     reps = b(images)
     return [dict(o, report=r) for o, r in zip(b.out, reps)]
+
+
+def tune(I: torch.Tensor, p: DhParams | None = None, iters: int = 40) -> dict:
+    """Times every sweep variant on this image's own Phi and lambda and records
+    the fastest for its shape (used by later calls on this device).  Returns
+    {"best": id, "us_per_iter": {id: us}}."""
+    H, W = _img(I)
+    p = p or params()
+    dc = dark_channel(I, p.patch)
+    A, _, _ = atmospheric_light(I, dc, p.topk_permille)
+    _, _, lam, Phi = transmission(I, A, p)
+    ws = workspace(H, W, p, I.device)
+    u = torch.empty_like(Phi)
+    res = N.DhTuneResult()
+    _check(N.dh_tune(Phi, lam, u, H, W, p, iters, ws, ws.numel(), _stream(None), res), "dh_tune")
+    return {"best": res.best, "us_per_iter": {res.variant[k]: res.us_per_iter[k] for k in range(res.count)}}
+
+
+def save_tuning(path: str, shapes) -> None:
+    """Writes the tuned variants of these (H, W) shapes (float32 storage) as JSON."""
+    import json
+
+    table = {f"{H}x{W}": N.dh_tune_get(H, W, N.DH_STORE_F32) for H, W in shapes}
+    with open(path, "w") as f:
+        json.dump({"device": torch.cuda.get_device_name(), "variants": table}, f, indent=1)
+
+
+def load_tuning(path: str) -> int:
+    """Loads a JSON tuning table written by save_tuning into the library;
+    returns the number of entries applied (0 when it was made on another GPU)."""
+    import json
+
+    with open(path) as f:
+        t = json.load(f)
+    if t.get("device") != torch.cuda.get_device_name():
+        return 0
+    n = 0
+    for key, v in t["variants"].items():
+        H, W = map(int, key.split("x"))
+        if v and N.dh_tune_set(H, W, N.DH_STORE_F32, int(v)) == N.DH_OK:
+            n += 1
+    return n

@@ -21,6 +21,10 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
               float *rho_hist, char *ws, const WsLayout &L, cudaStream_t s, float *J,
               cudaEvent_t loop_begin, cudaEvent_t loop_end, int *launches);
 int read_solve_state(const char *ws, const WsLayout &L, SolveState *out);
+int sweep_variant_count();
+bool sweep_variant_usable(int v, int W, bool aligned);
+void tune_set(int dev, int H, int W, int storage, int variant);
+int tune_get(int dev, int H, int W, int storage);
 
 int cuda_fail(cudaError_t) {
     cudaGetLastError();  // clear a non-sticky error so the next call starts clean
@@ -44,6 +48,7 @@ static bool params_ok(const dh_params *p) {
     if (p->tb_depth < 0 || p->tb_depth > 8) return false;
     if (p->storage < DH_STORE_F32 || p->storage > DH_STORE_F16_F32) return false;
     if (p->variant & ~(DH_VAR_NO_ADAPTIVE | DH_VAR_NO_EDGE | DH_VAR_NO_NONLOCAL)) return false;
+    if (p->sweep_variant < 0 || p->sweep_variant >= sweep_variant_count()) return false;
     return true;
 }
 
@@ -118,6 +123,7 @@ int dh_params_default(dh_params *p, int preset) {
     p->storage = DH_STORE_F32;
     p->variant = 0;
     p->use_graph = 1;
+    p->sweep_variant = 0;
     return DH_OK;
 }
 
@@ -260,6 +266,83 @@ int dh_dehaze(const float *I, int H, int W, const dh_params *p, const float *u0,
     report->a_index = sel.best;
     if (report->status == DH_OK && sel.clamped) report->status = DH_WDEGENERATE;
     return report->status;
+}
+
+int dh_sweep_variants(void) { return sweep_variant_count(); }
+
+int dh_tune_set(int H, int W, int storage, int variant) {
+    if (!shape_ok(H, W) || variant < 0 || variant >= sweep_variant_count() || storage < 0 || storage > DH_STORE_F16_F32)
+        return DH_EINVAL;
+    int dev = 0;
+    DH_CUDA_TRY(cudaGetDevice(&dev));
+    tune_set(dev, H, W, storage, variant);
+    return DH_OK;
+}
+
+int dh_tune_get(int H, int W, int storage) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return tune_get(dev, H, W, storage);
+}
+
+int dh_tune(const float *Phi, const float *lam, float *u_scratch, int H, int W, const dh_params *p, int iters,
+            void *workspace, size_t workspace_bytes, void *stream, dh_tune_result *out) {
+    if (!Phi || !lam || !u_scratch || !shape_ok(H, W) || !params_ok(p) || iters < 1 || iters > 100000 ||
+        p->storage != DH_STORE_F32)
+        return DH_EINVAL;
+    const WsLayout L = layout_for(H, W, p);
+    int rc = ws_ok(workspace, workspace_bytes, L);
+    if (rc) return rc;
+    char *ws = (char *)workspace;
+    cudaStream_t s = (cudaStream_t)stream;
+    auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+    const bool aligned = a16(Phi) && a16(lam) && a16(u_scratch) && a16(ws + L.ub);
+    dh_tune_result res;
+    std::memset(&res, 0, sizeof(res));
+    res.best = 0;
+    float best = 3.4e38f;
+    cudaEvent_t a, b;
+    DH_CUDA_TRY(cudaEventCreate(&a));
+    DH_CUDA_TRY(cudaEventCreate(&b));
+    const size_t bytes = (size_t)3 * H * W * sizeof(float);
+    rc = launch_phin(Phi, H, W, (float2 *)(ws + L.phin_part), (SolveState *)(ws + L.state), s);
+    for (int v = 1; !rc && v < sweep_variant_count() && res.count < 32; ++v) {
+        if (!sweep_variant_usable(v, W, aligned)) continue;
+        dh_params q = *p;
+        q.sweep_variant = v;
+        q.tol = 0.f;
+        q.max_iter = iters;
+        q.use_graph = 1;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && !rc; ++rep) {  // the first run builds and warms the graph
+            if (cudaMemcpyAsync(u_scratch, Phi, bytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess) { rc = DH_ECUDA; break; }
+            rc = run_solve(u_scratch, Phi, lam, H, W, &q, nullptr, ws, L, s, nullptr, a, b, nullptr);
+            if (!rc && rep == 1) {
+                if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess)
+                    rc = DH_ECUDA;
+            }
+        }
+        if (rc) break;
+        const float us = 1e3f * ms / (iters + 1);
+        res.variant[res.count] = v;
+        res.us_per_iter[res.count] = us;
+        ++res.count;
+        if (us < best) {
+            best = us;
+            res.best = v;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc == DH_ECUDA ? cuda_fail(cudaGetLastError()) : rc;
+    int dev = 0;
+    DH_CUDA_TRY(cudaGetDevice(&dev));
+    if (res.best > 0) tune_set(dev, H, W, DH_STORE_F32, res.best);
+    if (out) *out = res;
+    return DH_OK;
 }
 
 }  // extern "C"

@@ -616,11 +616,68 @@ static uint32_t tma_smem_bytes(int th, int stages, int tma, int esize) {
     return stages * stage + 1024;
 }
 
-// DH_SWEEP="R,NW,STAGES,TMA" overrides the default variant (for tuning);
-// TMA = 3 selects the streaming kernel with R = ring slots per warp.
-static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16) {
-    SweepCfg c{8, 4, 1, tma_ok ? 1 : 0, !(p->variant & DH_VAR_NO_EDGE)};
+// Sweep variants the tuner chooses from (index = dh_params.sweep_variant).
+// tma: 0 generic gather, 1 TMA tiles with Phi/lambda staged, 2 TMA u tile with
+// Phi/lambda vector loads, 3 per-warp row streams (R = ring slots).
+static const SweepCfg kVariants[] = {
+    {8, 4, 1, 1, true},  // 0: library default (also the auto choice)
+    {8, 4, 1, 1, true},  {8, 4, 2, 1, true},  {4, 8, 2, 1, true},  {4, 8, 1, 1, true},
+    {8, 4, 1, 2, true},  {8, 4, 2, 2, true},  {4, 8, 1, 2, true},  {16, 4, 1, 2, true},
+    {8, 8, 1, 2, true},  {16, 2, 2, 2, true}, {8, 4, 1, 3, true},  {8, 8, 1, 3, true},
+    {16, 4, 1, 3, true}, {8, 2, 1, 3, true},  {8, 4, 1, 0, true},  {16, 4, 1, 0, true},
+    {8, 8, 1, 0, true},
+};
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+
+int sweep_variant_count() { return kNumVariants; }
+bool sweep_variant_usable(int v, int W, bool aligned) {
+    if (v < 1 || v >= kNumVariants) return false;
+    return kVariants[v].tma == 0 || (aligned && W % 4 == 0);
+}
+
+// Per-device table of tuned variants by image shape and storage (dh_tune).
+struct TuneEntry {
+    int dev, H, W, storage, variant;
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tuned;
+
+void tune_set(int dev, int H, int W, int storage, int variant) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &e : g_tuned)
+        if (e.dev == dev && e.H == H && e.W == W && e.storage == storage) {
+            e.variant = variant;
+            return;
+        }
+    g_tuned.push_back({dev, H, W, storage, variant});
+}
+
+int tune_get(int dev, int H, int W, int storage) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &e : g_tuned)
+        if (e.dev == dev && e.H == H && e.W == W && e.storage == storage) return e.variant;
+    return 0;
+}
+
+// Variant for this call: an explicit dh_params.sweep_variant, else the tuned
+// entry for (device, shape, storage), else DH_SWEEP="R,NW,STAGES,TMA" from the
+// environment (for experiments), else the default.
+static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int W) {
+    const bool edge = !(p->variant & DH_VAR_NO_EDGE);
+    SweepCfg c = kVariants[0];
+    c.edge = edge;
+    if (!tma_ok) c.tma = 0;
     if (is16) return c;  // 16-bit storage: the default tiling only
+    int v = p->sweep_variant;
+    if (v <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) v = tune_get(dev, H, W, p->storage);
+    }
+    if (v > 0 && v < kNumVariants && (kVariants[v].tma == 0 || tma_ok)) {
+        c = kVariants[v];
+        c.edge = edge;
+        return c;
+    }
     if (const char *e = std::getenv("DH_SWEEP")) {
         int r, nw, st, t;
         if (std::sscanf(e, "%d,%d,%d,%d", &r, &nw, &st, &t) == 4) {
@@ -788,7 +845,7 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
     v.vec = (W % 4 == 0) && aligned;
     const bool tma_ok = v.vec && (W * esize) % 16 == 0;
     v.storage = esize == 4 ? 0 : (Store<T>::TMA_TYPE == CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 ? 1 : 2);
-    const SweepCfg cfg = pick_cfg(p, tma_ok, esize != 4);
+    const SweepCfg cfg = pick_cfg(p, tma_ok, esize != 4, H, W);
     const int ntx = (W + kTW - 1) / kTW;
     CUtensorMap maps[4];
     const SolveDesc *dptr = desc_dev;

@@ -36,8 +36,8 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_struct_sizes_match_header():
-    # dh_params: 16 4-byte fields; dh_report: 2 ints, 6 floats, long long, 2 floats, int (+pad)
-    assert ctypes.sizeof(N.DhParams) == 64
+    # dh_params: 17 4-byte fields; dh_report: 2 ints, 6 floats, long long, 2 floats, int (+pad)
+    assert ctypes.sizeof(N.DhParams) == 68
     assert ctypes.sizeof(N.DhReport) == 56
 
 
@@ -92,3 +92,7 @@ def test_invalid_arguments_rejected_on_host():
     assert N.dh_dehaze_batch(1, [img], p, None, 0) == N.DH_EWORKSPACE
     assert N.dh_dehaze_batch(1, [N.dh_image(None, 8, 8, None, fake, fake, fake, fake)], p, fake, 1 << 30) == N.DH_EINVAL
     assert N.dh_dehaze_batch(1, [img], p.replace(storage=1), fake, 1 << 30) == N.DH_EINVAL
+    assert N.dh_sweep_variants() >= 2
+    assert N.dh_workspace_bytes(4, 4, p.replace(sweep_variant=N.dh_sweep_variants())) == 0
+    assert N.dh_tune(fake, fake, fake, 8, 8, p, 0, fake, 1 << 30) == N.DH_EINVAL
+    assert N.dh_tune_set(8, 8, 0, 999) == N.DH_EINVAL
