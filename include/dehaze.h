@@ -216,6 +216,50 @@ size_t dh_batch_workspace_bytes(int n, const dh_image *imgs, const dh_params *p)
 int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *workspace,
                     size_t workspace_bytes, void *stream, dh_report *reports);
 
+/* ---- Learned warm start (not in the paper, which only points at hybrids of
+ * the PDE with learned models, Sec. I and V): a 4-level U-Net over (I, t, A)
+ * predicts y = lambda * u*, and u0 = y / lambda starts the fixed-point loop.
+ * Architecture: 14 3x3 convolutions (zero padding, bias, ReLU) with `base`
+ * (16 or 32) channels at full resolution doubling per level, 2x2 average
+ * pooling, nearest 2x upsampling, skip concatenation (upsampled channels
+ * first), a 1x1 head to 3 channels.  Parameters are one float32 vector:
+ * per convolution k weights [cout][3][3][cin] then bias [cout]; then the head
+ * weights [3][base] and bias [3].  The input has 16 channels (I^R, I^G, I^B, t,
+ * A^R, A^G, A^B, zeros).  Activations are bf16 NHWC in the workspace;
+ * convolutions run on the tensor cores (bf16 in, fp32 accumulate).  Images
+ * are N x H x W with H, W multiples of 8 and N*H*W <= 2^26.  I: N x 3 x H x W,
+ * t: N x H x W, A: N x 3, y / target: N x 3 x H x W, all float32 device. */
+size_t dh_unet_param_count(int base);
+size_t dh_unet_workspace_bytes(int base, int N, int H, int W, int train);
+/* He-normal weights from a counter-based generator, zero biases. */
+int dh_unet_init(float *params, int base, unsigned long long seed, void *stream);
+int dh_unet_forward(const float *params, int base, const float *I, const float *t, const float *A, int N,
+                    int H, int W, float *y, void *workspace, size_t workspace_bytes, void *stream);
+/* Forward, MSE loss mean((y - target)^2) into loss (device float[1]), and the
+ * gradient of every parameter into grads (same layout as params). */
+int dh_unet_backward(const float *params, int base, const float *I, const float *t, const float *A,
+                     const float *target, int N, int H, int W, float *grads, float *loss, void *workspace,
+                     size_t workspace_bytes, void *stream);
+/* One Adam step (bias-corrected; step counts from 1) over n parameters. */
+int dh_unet_adam(float *params, const float *grads, float *m, float *v, size_t n, float lr, float beta1,
+                 float beta2, float eps, int step, void *stream);
+/* u0^c = y^c / lambda (3xHxW planar, lambda HxW). */
+int dh_warm_start(const float *y, const float *lam, int H, int W, float *u0, void *stream);
+/* One 3x3 convolution layer on bf16 NHWC data with channel pitch ldx / ldy
+ * (C % 16 == 0, Cout % 8 == 0): y = [ReLU](conv(x, w) + bias), w bf16
+ * [Cout][3][3][C]; and its weight / bias gradients (fp32) from dy, with
+ * `scratch` (fp32) for per-split partial sums. */
+int dh_conv3x3_forward(const void *x, int ldx, int C, int N, int H, int W, const void *w, const float *bias,
+                       int Cout, int relu, void *y, int ldy, void *stream);
+int dh_conv3x3_backward_weights(const void *x, int ldx, int C, const void *dy, int lddy, int Cout, int N, int H,
+                                int W, float *dw, float *db, float *scratch, size_t scratch_bytes, void *stream);
+/* The whole method with the network's warm start: dark channel, A, t, lambda,
+ * Phi, then y = net(I, t, A), u0 = y / lambda, then the fixed-point loop from
+ * u0 and J = clamp(u).  net_workspace: dh_unet_workspace_bytes(base, 1, H, W, 0). */
+int dh_dehaze_warm(const float *params, int base, const float *I, int H, int W, const dh_params *p, float *J,
+                   float *u, float *t, float *A, void *workspace, size_t workspace_bytes, void *net_workspace,
+                   size_t net_workspace_bytes, void *stream, dh_report *report);
+
 /* dh_atmospheric_light without a workspace and without any allocation.
  * The paper has no counterpart: this exists for callers that cannot call
  * cudaMalloc, such as a plug-in whose host application owns all device memory,

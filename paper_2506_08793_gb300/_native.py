@@ -29,7 +29,9 @@ DH_VAR_NO_ADAPTIVE, DH_VAR_NO_EDGE, DH_VAR_NO_NONLOCAL = 1, 2, 4
 EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes",
            "dh_dark_channel", "dh_atmospheric_light", "dh_transmission", "dh_fixed_point",
            "dh_dehaze", "dh_batch_workspace_bytes", "dh_dehaze_batch", "dh_sweep_variants", "dh_tune",
-           "dh_tune_set", "dh_tune_get", "dh_atmospheric_light_noalloc")
+           "dh_tune_set", "dh_tune_get", "dh_unet_param_count", "dh_unet_workspace_bytes", "dh_unet_init",
+           "dh_unet_forward", "dh_unet_backward", "dh_unet_adam", "dh_warm_start", "dh_conv3x3_forward",
+           "dh_conv3x3_backward_weights", "dh_dehaze_warm", "dh_atmospheric_light_noalloc")
 
 
 class DhParams(ctypes.Structure):
@@ -137,6 +139,16 @@ def lib(build_if_missing: bool = True):
             "dh_tune": ([P, P, P, I, I, PP, I, P, S, P, ctypes.POINTER(DhTuneResult)], I),
             "dh_tune_set": ([I, I, I, I], I),
             "dh_tune_get": ([I, I, I], I),
+            "dh_unet_param_count": ([I], S),
+            "dh_unet_workspace_bytes": ([I, I, I, I, I], S),
+            "dh_unet_init": ([P, I, ctypes.c_ulonglong, P], I),
+            "dh_unet_forward": ([P, I, P, P, P, I, I, I, P, P, S, P], I),
+            "dh_unet_backward": ([P, I, P, P, P, P, I, I, I, P, P, P, S, P], I),
+            "dh_unet_adam": ([P, P, P, P, S, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, I, P], I),
+            "dh_warm_start": ([P, P, I, I, P, P], I),
+            "dh_conv3x3_forward": ([P, I, I, I, I, I, P, P, I, I, P, I, P], I),
+            "dh_conv3x3_backward_weights": ([P, I, I, P, I, I, I, I, I, P, P, P, S, P], I),
+            "dh_dehaze_warm": ([P, I, P, I, I, PP, P, P, P, P, P, S, P, S, P, PR], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -252,3 +264,51 @@ def dh_tune_set(H, W, storage, variant) -> int:
 
 def dh_tune_get(H, W, storage) -> int:
     return lib().dh_tune_get(H, W, storage)
+
+
+def dh_unet_param_count(base) -> int:
+    return lib().dh_unet_param_count(base)
+
+
+def dh_unet_workspace_bytes(base, N, H, W, train) -> int:
+    return lib().dh_unet_workspace_bytes(base, N, H, W, train)
+
+
+def dh_unet_init(params, base, seed, stream=None) -> int:
+    return lib().dh_unet_init(_p(params), base, seed, _stream(stream))
+
+
+def dh_unet_forward(params, base, I, t, A, N, H, W, y, workspace, workspace_bytes, stream=None) -> int:
+    return lib().dh_unet_forward(_p(params), base, _p(I), _p(t), _p(A), N, H, W, _p(y), _p(workspace),
+                                 workspace_bytes, _stream(stream))
+
+
+def dh_unet_backward(params, base, I, t, A, target, N, H, W, grads, loss, workspace, workspace_bytes,
+                     stream=None) -> int:
+    return lib().dh_unet_backward(_p(params), base, _p(I), _p(t), _p(A), _p(target), N, H, W, _p(grads), _p(loss),
+                                  _p(workspace), workspace_bytes, _stream(stream))
+
+
+def dh_unet_adam(params, grads, m, v, n, lr, beta1, beta2, eps, step, stream=None) -> int:
+    return lib().dh_unet_adam(_p(params), _p(grads), _p(m), _p(v), n, lr, beta1, beta2, eps, step, _stream(stream))
+
+
+def dh_warm_start(y, lam, H, W, u0, stream=None) -> int:
+    return lib().dh_warm_start(_p(y), _p(lam), H, W, _p(u0), _stream(stream))
+
+
+def dh_conv3x3_forward(x, ldx, C, N, H, W, w, bias, Cout, relu, y, ldy, stream=None) -> int:
+    return lib().dh_conv3x3_forward(_p(x), ldx, C, N, H, W, _p(w), _p(bias), Cout, relu, _p(y), ldy, _stream(stream))
+
+
+def dh_conv3x3_backward_weights(x, ldx, C, dy, lddy, Cout, N, H, W, dw, db, scratch, scratch_bytes,
+                                stream=None) -> int:
+    return lib().dh_conv3x3_backward_weights(_p(x), ldx, C, _p(dy), lddy, Cout, N, H, W, _p(dw), _p(db),
+                                             _p(scratch), scratch_bytes, _stream(stream))
+
+
+def dh_dehaze_warm(params, base, I, H, W, p: DhParams, J, u, t, A, workspace, workspace_bytes, net_workspace,
+                   net_workspace_bytes, stream=None, report: DhReport | None = None) -> int:
+    return lib().dh_dehaze_warm(_p(params), base, _p(I), H, W, ctypes.byref(p), _p(J), _p(u), _p(t), _p(A),
+                                _p(workspace), workspace_bytes, _p(net_workspace), net_workspace_bytes,
+                                _stream(stream), _ref(report))

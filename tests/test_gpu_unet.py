@@ -1,0 +1,135 @@
+"""Warm-start network kernels (bf16 tensor-core convolutions, whole-network
+forward / backward, Adam) against the FP64 oracle in oracle/unet.py, through
+the C ABI."""
+import numpy as np
+import pytest
+
+from paper_2506_08793_gb300 import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def N():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2506_08793_gb300 import _native
+
+    _native.lib()
+    return _native
+
+
+def rnd(seed, *shape, lo=-1.0, hi=1.0):
+    return scenes.uniform(seed, 93, int(np.prod(shape)), lo, hi).reshape(shape)
+
+
+def bf(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(torch.bfloat16)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.float().cpu().numpy()
+
+
+@pytest.mark.parametrize("n,H,W,C,ldx,Cout,relu", [(2, 7, 13, 16, 16, 32, 1), (1, 9, 20, 32, 48, 64, 0),
+                                                   (1, 12, 8, 96, 96, 96, 1), (3, 5, 5, 64, 64, 128, 0)])
+def test_conv_forward(N, n, H, W, C, ldx, Cout, relu):
+    from oracle import unet as U
+
+    x = rnd(1 + C, n, H, W, ldx)
+    w = rnd(2 + C, Cout, 3, 3, C, lo=-0.3, hi=0.3)
+    b = rnd(3 + C, Cout)
+    xb, wb = bf(x), bf(w)
+    want = U.conv3x3(xb.float().numpy()[..., :C].astype(np.float64), wb.float().numpy().astype(np.float64), b)
+    if relu:
+        want = np.maximum(want, 0)
+    y = torch.zeros((n, H, W, Cout + 8), dtype=torch.bfloat16, device="cuda")
+    rc = N.dh_conv3x3_forward(xb.cuda(), ldx, C, n, H, W, wb.cuda(), torch.from_numpy(b.astype(np.float32)).cuda(),
+                              Cout, relu, y, Cout + 8)
+    assert rc == 0
+    got = host(y)[..., :Cout]
+    assert np.all(np.abs(got - want) <= 2.0 ** -8 * np.abs(want) + 1e-3 * np.abs(want).max())
+    assert np.all(host(y)[..., Cout:] == 0)
+
+
+@pytest.mark.parametrize("n,H,W,C,Cout", [(2, 7, 13, 16, 32), (1, 30, 41, 64, 32), (2, 16, 16, 96, 64)])
+def test_conv_weight_gradient(N, n, H, W, C, Cout):
+    from oracle import unet as U
+
+    x = bf(rnd(5 + C, n, H, W, C))
+    dy = bf(rnd(6 + C, n, H, W, Cout))
+    _, gw, gb = U.conv3x3_backward(x.float().numpy().astype(np.float64), np.zeros((Cout, 3, 3, C)),
+                                   dy.float().numpy().astype(np.float64))
+    dw = torch.zeros(Cout * 9 * C, device="cuda")
+    db = torch.zeros(Cout, device="cuda")
+    scratch = torch.empty(16 << 20, dtype=torch.uint8, device="cuda")
+    rc = N.dh_conv3x3_backward_weights(x.cuda(), C, C, dy.cuda(), Cout, Cout, n, H, W, dw, db, scratch,
+                                       scratch.numel())
+    assert rc == 0
+    assert np.max(np.abs(host(dw).reshape(gw.shape) - gw)) <= 1e-4 * np.abs(gw).max()
+    assert np.max(np.abs(host(db) - gb)) <= 1e-3 * max(1.0, np.abs(gb).max())
+
+
+def _net_inputs(n, H, W, seed):
+    I = np.stack([scenes.hazy_scene(seed + k, H, W)["I"] for k in range(n)])
+    t = rnd(seed, n, H, W, lo=0.1, hi=1.0)
+    A = rnd(seed + 1, n, 3, lo=0.8, hi=1.0)
+    tgt = rnd(seed + 2, n, 3, H, W, lo=0.0, hi=1.0)
+    return I.astype(np.float32), t.astype(np.float32), A.astype(np.float32), tgt.astype(np.float32)
+
+
+def test_network_forward_backward_against_oracle(N):
+    from oracle import unet as U
+
+    base, n, H, W = 16, 2, 16, 24
+    I, t, A, tgt = _net_inputs(n, H, W, 40)
+    npar = N.dh_unet_param_count(base)
+    assert npar == U.param_count(base)
+    params = torch.empty(npar, device="cuda")
+    assert N.dh_unet_init(params, base, 7) == 0
+    ws = torch.empty(N.dh_unet_workspace_bytes(base, n, H, W, 1), dtype=torch.uint8, device="cuda")
+    d = {k: torch.from_numpy(v).cuda() for k, v in dict(I=I, t=t, A=A, tgt=tgt).items()}
+    y = torch.empty((n, 3, H, W), device="cuda")
+    assert N.dh_unet_forward(params, base, d["I"], d["t"], d["A"], n, H, W, y, ws, ws.numel()) == 0
+    P = host(params).astype(np.float64)
+    yo, _ = U.forward(P, base, I, t, A)
+    assert np.linalg.norm(host(y) - yo) <= 3e-2 * np.linalg.norm(yo)
+    grads = torch.empty(npar, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    assert N.dh_unet_backward(params, base, d["I"], d["t"], d["A"], d["tgt"], n, H, W, grads, loss, ws,
+                              ws.numel()) == 0
+    lo, go = U.loss_and_grads(P, base, I, t, A, tgt)
+    assert abs(host(loss)[0] - lo) <= 3e-2 * lo
+    g = host(grads).astype(np.float64)
+    o = 0
+    for k, (cin, cout) in enumerate(U.convs(base)):
+        for size in (cout * 9 * cin, cout):
+            a, b = g[o:o + size], go[o:o + size]
+            o += size
+            if np.linalg.norm(b) < 1e-8:
+                continue
+            cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
+            assert cos >= 0.99 and np.linalg.norm(a - b) <= 0.1 * np.linalg.norm(b), (k, size, cos)
+    a, b = g[o:], go[o:]
+    assert np.linalg.norm(a - b) <= 0.05 * np.linalg.norm(b)
+
+
+def test_adam_training_reduces_loss(N):
+    base, n, H, W = 16, 2, 32, 32
+    I, t, A, tgt = _net_inputs(n, H, W, 60)
+    d = {k: torch.from_numpy(v).cuda() for k, v in dict(I=I, t=t, A=A, tgt=tgt).items()}
+    npar = N.dh_unet_param_count(base)
+    params = torch.empty(npar, device="cuda")
+    N.dh_unet_init(params, base, 3)
+    grads, m, v = torch.empty(npar, device="cuda"), torch.zeros(npar, device="cuda"), torch.zeros(npar, device="cuda")
+    loss = torch.empty(1, device="cuda")
+    ws = torch.empty(N.dh_unet_workspace_bytes(base, n, H, W, 1), dtype=torch.uint8, device="cuda")
+    losses = []
+    for step in range(1, 61):
+        assert N.dh_unet_backward(params, base, d["I"], d["t"], d["A"], d["tgt"], n, H, W, grads, loss, ws,
+                                  ws.numel()) == 0
+        losses.append(float(host(loss)[0]))
+        assert N.dh_unet_adam(params, grads, m, v, npar, 2e-3, 0.9, 0.999, 1e-8, step) == 0
+    assert np.isfinite(losses).all() and losses[-1] < 0.5 * losses[0], losses[::10]

@@ -1,0 +1,66 @@
+"""Pins of the network oracle (oracle/unet.py): the convolution against a
+brute-force loop, the hand-written backward against central differences."""
+import numpy as np
+
+from oracle import unet as U
+from paper_2506_08793_gb300 import scenes
+
+
+def rnd(seed, *shape, lo=-1.0, hi=1.0):
+    return scenes.uniform(seed, 91, int(np.prod(shape)), lo, hi).reshape(shape)
+
+
+def test_conv3x3_brute_force():
+    x = rnd(1, 2, 5, 6, 3)
+    w = rnd(2, 4, 3, 3, 3)
+    b = rnd(3, 4)
+    y = U.conv3x3(x, w, b)
+    for n in range(2):
+        for i in range(5):
+            for j in range(6):
+                for co in range(4):
+                    s = b[co]
+                    for dy in range(3):
+                        for dx in range(3):
+                            ii, jj = i + dy - 1, j + dx - 1
+                            if 0 <= ii < 5 and 0 <= jj < 6:
+                                s += np.dot(x[n, ii, jj], w[co, dy, dx])
+                    assert abs(y[n, i, j, co] - s) < 1e-12
+
+
+def test_conv_backward_finite_differences():
+    x = rnd(4, 1, 4, 5, 3)
+    w = rnd(5, 2, 3, 3, 3)
+    b = rnd(6, 2)
+    g = rnd(7, 1, 4, 5, 2)
+    gx, gw, gb = U.conv3x3_backward(x, w, g)
+    f = lambda x_, w_, b_: float(np.sum(g * U.conv3x3(x_, w_, b_)))
+    h = 1e-6
+    for idx in [(0, 0, 0, 0), (0, 3, 4, 2), (0, 1, 2, 1)]:
+        e = np.zeros_like(x); e[idx] = h
+        assert abs((f(x + e, w, b) - f(x - e, w, b)) / (2 * h) - gx[idx]) < 1e-6
+    for idx in [(0, 0, 0, 0), (1, 2, 1, 2), (1, 1, 1, 1)]:
+        e = np.zeros_like(w); e[idx] = h
+        assert abs((f(x, w + e, b) - f(x, w - e, b)) / (2 * h) - gw[idx]) < 1e-6
+    assert np.allclose(gb, g.sum(axis=(0, 1, 2)))
+
+
+def test_network_gradient_finite_differences():
+    """The whole network's loss gradient (base 8 keeps it small) against
+    central differences on a sample of parameters of every layer."""
+    b, N, H, W = 8, 1, 8, 8
+    rng = np.random.default_rng(0)
+    params = rng.normal(0, 0.3, U.param_count(b))
+    I = rng.uniform(0, 1, (N, 3, H, W))
+    t = rng.uniform(0.1, 1, (N, H, W))
+    A = rng.uniform(0.8, 1, (N, 3))
+    tgt = rng.normal(0, 1, (N, 3, H, W))
+    loss, g = U.loss_and_grads(params, b, I, t, A, tgt)
+    h = 1e-6
+    idx = np.unique(np.linspace(0, params.size - 1, 60).astype(int))
+    for i in idx:
+        e = np.zeros_like(params); e[i] = h
+        lp, _ = U.loss_and_grads(params + e, b, I, t, A, tgt)
+        lm, _ = U.loss_and_grads(params - e, b, I, t, A, tgt)
+        num = (lp - lm) / (2 * h)
+        assert abs(num - g[i]) <= 1e-5 * max(1.0, abs(num)), (i, num, g[i])
