@@ -218,33 +218,38 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
 
 /* ---- Learned warm start (not in the paper, which only points at hybrids of
  * the PDE with learned models, Sec. I and V): a 4-level U-Net over (I, t, A)
- * predicts y = lambda * u*, and u0 = y / lambda starts the fixed-point loop.
+ * and Phi predicts y = lambda * u* as Phi + a learned correction (y = Phi, i.e.
+ * u0 = Phi / lambda, is the fixed point without diffusion and with G = 1), and
+ * u0 = y / lambda starts the fixed-point loop.
  * Architecture: 14 3x3 convolutions (zero padding, bias, ReLU) with `base`
  * (16 or 32) channels at full resolution doubling per level, 2x2 average
  * pooling, nearest 2x upsampling, skip concatenation (upsampled channels
- * first), a 1x1 head to 3 channels.  Parameters are one float32 vector:
+ * first), a 1x1 head to 3 channels added to Phi.  Parameters are one float32 vector:
  * per convolution k weights [cout][3][3][cin] then bias [cout]; then the head
  * weights [3][base] and bias [3].  The input has 16 channels (I^R, I^G, I^B, t,
- * A^R, A^G, A^B, zeros).  Activations are bf16 NHWC in the workspace;
+ * A^R, A^G, A^B, Phi^R, Phi^G, Phi^B, zeros).  Activations are bf16 NHWC in the workspace;
  * convolutions run on the tensor cores (bf16 in, fp32 accumulate).  Images
- * are N x H x W with H, W multiples of 8 and N*H*W <= 2^26.  I: N x 3 x H x W,
+ * are N x H x W with H, W multiples of 8 and N*H*W <= 2^26.  I, Phi: N x 3 x H x W,
  * t: N x H x W, A: N x 3, y / target: N x 3 x H x W, all float32 device. */
 size_t dh_unet_param_count(int base);
 size_t dh_unet_workspace_bytes(int base, int N, int H, int W, int train);
 /* He-normal weights from a counter-based generator, zero biases. */
 int dh_unet_init(float *params, int base, unsigned long long seed, void *stream);
-int dh_unet_forward(const float *params, int base, const float *I, const float *t, const float *A, int N,
-                    int H, int W, float *y, void *workspace, size_t workspace_bytes, void *stream);
+int dh_unet_forward(const float *params, int base, const float *I, const float *t, const float *A,
+                    const float *Phi, int N, int H, int W, float *y, void *workspace, size_t workspace_bytes,
+                    void *stream);
 /* Forward, MSE loss mean((y - target)^2) into loss (device float[1]), and the
  * gradient of every parameter into grads (same layout as params). */
 int dh_unet_backward(const float *params, int base, const float *I, const float *t, const float *A,
-                     const float *target, int N, int H, int W, float *grads, float *loss, void *workspace,
-                     size_t workspace_bytes, void *stream);
+                     const float *Phi, const float *target, int N, int H, int W, float *grads, float *loss,
+                     void *workspace, size_t workspace_bytes, void *stream);
 /* One Adam step (bias-corrected; step counts from 1) over n parameters. */
 int dh_unet_adam(float *params, const float *grads, float *m, float *v, size_t n, float lr, float beta1,
                  float beta2, float eps, int step, void *stream);
-/* u0^c = y^c / lambda (3xHxW planar, lambda HxW). */
+/* u0^c = y^c / lambda (3xHxW planar, lambda HxW), and the training target
+ * y^c = lambda * u^c of a solved u. */
 int dh_warm_start(const float *y, const float *lam, int H, int W, float *u0, void *stream);
+int dh_warm_target(const float *u, const float *lam, int H, int W, float *y, void *stream);
 /* One 3x3 convolution layer on bf16 NHWC data with channel pitch ldx / ldy
  * (C % 16 == 0, Cout % 8 == 0): y = [ReLU](conv(x, w) + bias), w bf16
  * [Cout][3][3][C]; and its weight / bias gradients (fp32) from dy, with

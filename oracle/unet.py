@@ -44,13 +44,15 @@ def param_count(b: int) -> int:
     return sum(cout * 9 * cin + cout for cin, cout in convs(b)) + 3 * b + 3
 
 
-def pack_input(I, t, A):
-    """(N,3,H,W), (N,H,W), (N,3) -> NHWC with channels I, t, A, zeros (16)."""
+def pack_input(I, t, A, Phi):
+    """(N,3,H,W), (N,H,W), (N,3), (N,3,H,W) -> NHWC with channels I, t, A,
+    Phi, zeros (16)."""
     N, _, H, W = I.shape
     x = np.zeros((N, H, W, 16))
     x[..., 0:3] = np.moveaxis(I, 1, -1)
     x[..., 3] = t
     x[..., 4:7] = A[:, None, None, :]
+    x[..., 7:10] = np.moveaxis(Phi, 1, -1)
     return x
 
 
@@ -100,11 +102,12 @@ def up_backward(g):
     return g.reshape(N, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
 
 
-def forward(params, b, I, t, A):
-    """Returns (y (N,3,H,W) = lambda*u* prediction, cache for backward)."""
+def forward(params, b, I, t, A, Phi):
+    """Returns (y (N,3,H,W) = lambda*u* prediction = Phi + head, cache)."""
     ws, bs, hw, hb = unpack(np.asarray(params, np.float64), b)
     c = {}
-    x0 = pack_input(np.asarray(I, np.float64), np.asarray(t, np.float64), np.asarray(A, np.float64))
+    Phi = np.asarray(Phi, np.float64)
+    x0 = pack_input(np.asarray(I, np.float64), np.asarray(t, np.float64), np.asarray(A, np.float64), Phi)
     c["x0"] = x0
     a1 = relu(conv3x3(x0, ws[0], bs[0])); c["a1"] = a1
     e1 = relu(conv3x3(a1, ws[1], bs[1])); c["e1"] = e1
@@ -127,14 +130,14 @@ def forward(params, b, I, t, A):
     d1a = relu(conv3x3(cat1, ws[12], bs[12])); c["d1a"] = d1a
     d1 = relu(conv3x3(d1a, ws[13], bs[13])); c["d1"] = d1
     y = d1 @ hw.T + hb  # (N,H,W,3)
-    return np.moveaxis(y, -1, 1), c
+    return np.moveaxis(y, -1, 1) + Phi, c
 
 
-def loss_and_grads(params, b, I, t, A, target):
+def loss_and_grads(params, b, I, t, A, Phi, target):
     """MSE loss mean((y - target)^2) and its gradient w.r.t. params."""
     params = np.asarray(params, np.float64)
     ws, bs, hw, hb = unpack(params, b)
-    y, c = forward(params, b, I, t, A)
+    y, c = forward(params, b, I, t, A, Phi)
     d = y - np.asarray(target, np.float64)
     loss = float(np.mean(d * d))
     gy = np.moveaxis(2.0 * d / d.size, 1, -1)  # NHWC

@@ -30,7 +30,8 @@ EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes
            "dh_dark_channel", "dh_atmospheric_light", "dh_transmission", "dh_fixed_point",
            "dh_dehaze", "dh_batch_workspace_bytes", "dh_dehaze_batch", "dh_sweep_variants", "dh_tune",
            "dh_tune_set", "dh_tune_get", "dh_unet_param_count", "dh_unet_workspace_bytes", "dh_unet_init",
-           "dh_unet_forward", "dh_unet_backward", "dh_unet_adam", "dh_warm_start", "dh_conv3x3_forward",
+           "dh_unet_forward", "dh_unet_backward", "dh_unet_adam", "dh_warm_start", "dh_warm_target",
+           "dh_conv3x3_forward",
            "dh_conv3x3_backward_weights", "dh_dehaze_warm", "dh_atmospheric_light_noalloc")
 
 
@@ -142,10 +143,11 @@ def lib(build_if_missing: bool = True):
             "dh_unet_param_count": ([I], S),
             "dh_unet_workspace_bytes": ([I, I, I, I, I], S),
             "dh_unet_init": ([P, I, ctypes.c_ulonglong, P], I),
-            "dh_unet_forward": ([P, I, P, P, P, I, I, I, P, P, S, P], I),
-            "dh_unet_backward": ([P, I, P, P, P, P, I, I, I, P, P, P, S, P], I),
+            "dh_unet_forward": ([P, I, P, P, P, P, I, I, I, P, P, S, P], I),
+            "dh_unet_backward": ([P, I, P, P, P, P, P, I, I, I, P, P, P, S, P], I),
             "dh_unet_adam": ([P, P, P, P, S, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, I, P], I),
             "dh_warm_start": ([P, P, I, I, P, P], I),
+            "dh_warm_target": ([P, P, I, I, P, P], I),
             "dh_conv3x3_forward": ([P, I, I, I, I, I, P, P, I, I, P, I, P], I),
             "dh_conv3x3_backward_weights": ([P, I, I, P, I, I, I, I, I, P, P, P, S, P], I),
             "dh_dehaze_warm": ([P, I, P, I, I, PP, P, P, P, P, P, S, P, S, P, PR], I),
@@ -278,15 +280,15 @@ def dh_unet_init(params, base, seed, stream=None) -> int:
     return lib().dh_unet_init(_p(params), base, seed, _stream(stream))
 
 
-def dh_unet_forward(params, base, I, t, A, N, H, W, y, workspace, workspace_bytes, stream=None) -> int:
-    return lib().dh_unet_forward(_p(params), base, _p(I), _p(t), _p(A), N, H, W, _p(y), _p(workspace),
+def dh_unet_forward(params, base, I, t, A, Phi, N, H, W, y, workspace, workspace_bytes, stream=None) -> int:
+    return lib().dh_unet_forward(_p(params), base, _p(I), _p(t), _p(A), _p(Phi), N, H, W, _p(y), _p(workspace),
                                  workspace_bytes, _stream(stream))
 
 
-def dh_unet_backward(params, base, I, t, A, target, N, H, W, grads, loss, workspace, workspace_bytes,
+def dh_unet_backward(params, base, I, t, A, Phi, target, N, H, W, grads, loss, workspace, workspace_bytes,
                      stream=None) -> int:
-    return lib().dh_unet_backward(_p(params), base, _p(I), _p(t), _p(A), _p(target), N, H, W, _p(grads), _p(loss),
-                                  _p(workspace), workspace_bytes, _stream(stream))
+    return lib().dh_unet_backward(_p(params), base, _p(I), _p(t), _p(A), _p(Phi), _p(target), N, H, W, _p(grads),
+                                  _p(loss), _p(workspace), workspace_bytes, _stream(stream))
 
 
 def dh_unet_adam(params, grads, m, v, n, lr, beta1, beta2, eps, step, stream=None) -> int:
@@ -295,6 +297,10 @@ def dh_unet_adam(params, grads, m, v, n, lr, beta1, beta2, eps, step, stream=Non
 
 def dh_warm_start(y, lam, H, W, u0, stream=None) -> int:
     return lib().dh_warm_start(_p(y), _p(lam), H, W, _p(u0), _stream(stream))
+
+
+def dh_warm_target(u, lam, H, W, y, stream=None) -> int:
+    return lib().dh_warm_target(_p(u), _p(lam), H, W, _p(y), _stream(stream))
 
 
 def dh_conv3x3_forward(x, ldx, C, N, H, W, w, bias, Cout, relu, y, ldy, stream=None) -> int:

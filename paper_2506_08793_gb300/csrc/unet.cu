@@ -1,8 +1,10 @@
 // Learned warm start for the fixed-point solver: a 4-level U-Net (base 32
 // channels, 3x3 convolutions, ReLU, 2x2 average pooling, nearest 2x
-// upsampling, skip concatenation, 1x1 head) over (I, t, A) that predicts
-// y = lambda * u*, so that u0 = y / lambda starts the iteration of App. A-A
-// near its fixed point.  The paper only points at such hybrids (Sec. I, V);
+// upsampling, skip concatenation, 1x1 head) over (I, t, A) and the data term
+// Phi that predicts y = lambda * u* as Phi plus a learned correction, so that
+// u0 = y / lambda starts the iteration of App. A-A near its fixed point
+// (y = Phi, i.e. u0 = Phi / lambda, is the fixed point without diffusion and
+// with G = identity).  The paper only points at such hybrids (Sec. I, V);
 // the network, its training and the warm start are this library's.
 //
 // Activations and their gradients are bf16, channels-last (NHWC) with a
@@ -319,9 +321,10 @@ __global__ void k_upsample_bwd(const bf16 *__restrict__ gout, int ldo, int C, in
     }
 }
 
-// network input: channels (I^R, I^G, I^B, t, A^R, A^G, A^B, 0 ...) padded to 16
+// network input: channels (I^R, I^G, I^B, t, A^R, A^G, A^B, Phi^R, Phi^G,
+// Phi^B, 0 ...) padded to 16
 __global__ void k_pack_input(const float *__restrict__ I, const float *__restrict__ t, const float *__restrict__ A,
-                             int Nimg, int H, int W, bf16 *x) {
+                             const float *__restrict__ Phi, int Nimg, int H, int W, bf16 *x) {
     const size_t HW = (size_t)H * W, n = (size_t)Nimg * HW;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
         const size_t nn = p / HW, q = p - nn * HW;
@@ -329,19 +332,21 @@ __global__ void k_pack_input(const float *__restrict__ I, const float *__restric
         for (int c = 0; c < 3; ++c) v[c] = I[(nn * 3 + c) * HW + q];
         v[3] = t[nn * HW + q];
         for (int c = 0; c < 3; ++c) v[4 + c] = A[nn * 3 + c];
-        for (int c = 7; c < 16; ++c) v[c] = 0.f;
+        for (int c = 0; c < 3; ++c) v[7 + c] = Phi[(nn * 3 + c) * HW + q];
+        for (int c = 10; c < 16; ++c) v[c] = 0.f;
         __nv_bfloat162 *d = reinterpret_cast<__nv_bfloat162 *>(x + p * 16);
         for (int c = 0; c < 8; ++c) d[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
     }
 }
 
-// 1x1 head: y[n][o][q] = hb[o] + sum_c hw[o][c] x[p][c] (fp32 out, planar)
+// 1x1 head on top of the analytic guess: y[n][o][q] = Phi[n][o][q] + hb[o] +
+// sum_c hw[o][c] x[p][c] (fp32 out, planar)
 __global__ void k_head(const bf16 *__restrict__ x, int ldx, int C, const float *__restrict__ hw, const float *__restrict__ hb,
-                       int Nimg, int H, int W, float *y) {
+                       const float *__restrict__ Phi, int Nimg, int H, int W, float *y) {
     const size_t HW = (size_t)H * W, n = (size_t)Nimg * HW;
     for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
         const size_t nn = p / HW, q = p - nn * HW;
-        float s[3] = {hb[0], hb[1], hb[2]};
+        float s[3] = {hb[0] + Phi[(nn * 3) * HW + q], hb[1] + Phi[(nn * 3 + 1) * HW + q], hb[2] + Phi[(nn * 3 + 2) * HW + q]};
         for (int c = 0; c < C; ++c) {
             const float v = __bfloat162float(x[p * ldx + c]);
             for (int o = 0; o < 3; ++o) s[o] = fmaf(hw[o * C + c], v, s[o]);
@@ -456,6 +461,12 @@ __global__ void k_init_normal(float *p, size_t n, float stdv, unsigned long long
         const float u1 = ((a >> 40) + 1) * (1.0f / 16777217.0f), u2 = (b >> 40) * (1.0f / 16777216.0f);
         p[i] = stdv * sqrtf(-2.f * logf(u1)) * cospif(2.f * u2);
     }
+}
+
+// y = lambda * u (per channel, planar): the network's training target
+__global__ void k_warm_target(const float *__restrict__ u, const float *__restrict__ lam, size_t HW, float *y) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < 3 * HW; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = __fmul_rn(u[i], lam[i % HW]);
 }
 
 // u0 = y / lambda (per channel, planar), the warm start
@@ -652,8 +663,9 @@ int sweep_tile_h(int depth);
     } while (0)
 
 // Forward pass; leaves every activation in the workspace (for the backward).
-static int net_forward(const float *params, int b, const float *I, const float *t, const float *A, int N, int H,
-                       int W, char *ws, const NetLayout &L, bool train, cudaStream_t s) {
+static int net_forward(const float *params, int b, const float *I, const float *t, const float *A,
+                       const float *Phi, int N, int H, int W, char *ws, const NetLayout &L, bool train,
+                       cudaStream_t s) {
     const ParamLayout P = param_layout(b);
     const auto convs = unet_convs(b);
     bf16 *wf = BF(L.wf), *wt = BF(L.wt);
@@ -661,7 +673,7 @@ static int net_forward(const float *params, int b, const float *I, const float *
         k_prep_weights<<<gs((size_t)convs[k].cout * 9 * convs[k].cin), 256, 0, s>>>(
             params + P.w[k], convs[k].cout, convs[k].cin, wf + P.w[k], train ? wt + P.w[k] : nullptr);
     const size_t M0 = (size_t)N * H * W;
-    k_pack_input<<<gs(M0), 256, 0, s>>>(I, t, A, N, H, W, BF(L.x0.off));
+    k_pack_input<<<gs(M0), 256, 0, s>>>(I, t, A, Phi, N, H, W, BF(L.x0.off));
     auto conv = [&](int k, const Act &x, const bf16 *xp, int lvl, bf16 *y, int ldy) {
         return conv_fwd(xp, x.ld, convs[k].cin, N, H >> lvl, W >> lvl, wf + P.w[k], params + P.b[k], convs[k].cout,
                         true, y, ldy, s);
@@ -689,7 +701,7 @@ static int net_forward(const float *params, int b, const float *I, const float *
     k_upsample<<<gs(M0 * 2 * b), 256, 0, s>>>(BF(L.d2.off), 2 * b, 2 * b, N, h1, w1, BF(L.cat1.off), 3 * b);
     RUN(conv(12, L.cat1, BF(L.cat1.off), 0, BF(L.d1a.off), b));
     RUN(conv(13, L.d1a, BF(L.d1a.off), 0, BF(L.d1.off), b));
-    k_head<<<gs(M0), 256, 0, s>>>(BF(L.d1.off), b, b, params + P.hw, params + P.hb, N, H, W,
+    k_head<<<gs(M0), 256, 0, s>>>(BF(L.d1.off), b, b, params + P.hw, params + P.hb, Phi, N, H, W,
                                   reinterpret_cast<float *>(ws + L.y));
     DH_CUDA_TRY(cudaGetLastError());
     return DH_OK;
@@ -800,36 +812,39 @@ int dh_unet_init(float *params, int base, unsigned long long seed, void *stream)
     DH_CUDA_TRY(cudaMemsetAsync(params, 0, P.total * sizeof(float), s));
     for (size_t k = 0; k < convs.size(); ++k) {
         const size_t n = (size_t)convs[k].cout * 9 * convs[k].cin;
-        const int fan_in = 9 * (k == 0 ? 7 : convs[k].cin);
+        const int fan_in = 9 * (k == 0 ? 10 : convs[k].cin);
         k_init_normal<<<gs(n), 256, 0, s>>>(params + P.w[k], n, sqrtf(2.f / fan_in), seed * 131 + k);
     }
-    k_init_normal<<<1, 256, 0, s>>>(params + P.hw, 3 * (size_t)base, sqrtf(1.f / base), seed * 131 + 99);
+    // a small head: the untrained network returns about the analytic guess y = Phi
+    k_init_normal<<<1, 256, 0, s>>>(params + P.hw, 3 * (size_t)base, 0.01f * sqrtf(1.f / base), seed * 131 + 99);
     DH_CUDA_TRY(cudaGetLastError());
     return DH_OK;
 }
 
-int dh_unet_forward(const float *params, int base, const float *I, const float *t, const float *A, int N, int H,
-                    int W, float *y, void *workspace, size_t workspace_bytes, void *stream) {
-    if (!params || !I || !t || !A || !y || !unet_shape_ok(base, N, H, W)) return DH_EINVAL;
+int dh_unet_forward(const float *params, int base, const float *I, const float *t, const float *A,
+                    const float *Phi, int N, int H, int W, float *y, void *workspace, size_t workspace_bytes,
+                    void *stream) {
+    if (!params || !I || !t || !A || !Phi || !y || !unet_shape_ok(base, N, H, W)) return DH_EINVAL;
     const NetLayout L = net_layout(base, N, H, W, false);
     if (!workspace || ((uintptr_t)workspace % kAlign) || workspace_bytes < L.total) return DH_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     char *ws = (char *)workspace;
-    int rc = net_forward(params, base, I, t, A, N, H, W, ws, L, false, s);
+    int rc = net_forward(params, base, I, t, A, Phi, N, H, W, ws, L, false, s);
     if (rc) return rc;
     DH_CUDA_TRY(cudaMemcpyAsync(y, ws + L.y, (size_t)3 * N * H * W * sizeof(float), cudaMemcpyDeviceToDevice, s));
     return DH_OK;
 }
 
 int dh_unet_backward(const float *params, int base, const float *I, const float *t, const float *A,
-                     const float *target, int N, int H, int W, float *grads, float *loss, void *workspace,
-                     size_t workspace_bytes, void *stream) {
-    if (!params || !I || !t || !A || !target || !grads || !loss || !unet_shape_ok(base, N, H, W)) return DH_EINVAL;
+                     const float *Phi, const float *target, int N, int H, int W, float *grads, float *loss,
+                     void *workspace, size_t workspace_bytes, void *stream) {
+    if (!params || !I || !t || !A || !Phi || !target || !grads || !loss || !unet_shape_ok(base, N, H, W))
+        return DH_EINVAL;
     const NetLayout L = net_layout(base, N, H, W, true);
     if (!workspace || ((uintptr_t)workspace % kAlign) || workspace_bytes < L.total) return DH_EWORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
     char *ws = (char *)workspace;
-    int rc = net_forward(params, base, I, t, A, N, H, W, ws, L, true, s);
+    int rc = net_forward(params, base, I, t, A, Phi, N, H, W, ws, L, true, s);
     if (rc) return rc;
     return net_backward(params, base, target, N, H, W, ws, L, grads, loss, s);
 }
@@ -847,6 +862,14 @@ int dh_warm_start(const float *y, const float *lam, int H, int W, float *u0, voi
     if (!y || !lam || !u0 || !shape_ok(H, W)) return DH_EINVAL;
     const size_t HW = (size_t)H * W;
     k_warm_start<<<gs(3 * HW), 256, 0, (cudaStream_t)stream>>>(y, lam, HW, u0);
+    DH_CUDA_TRY(cudaGetLastError());
+    return DH_OK;
+}
+
+int dh_warm_target(const float *u, const float *lam, int H, int W, float *y, void *stream) {
+    if (!u || !lam || !y || !shape_ok(H, W)) return DH_EINVAL;
+    const size_t HW = (size_t)H * W;
+    k_warm_target<<<gs(3 * HW), 256, 0, (cudaStream_t)stream>>>(u, lam, HW, y);
     DH_CUDA_TRY(cudaGetLastError());
     return DH_OK;
 }
@@ -895,7 +918,7 @@ int dh_dehaze_warm(const float *params, int base, const float *I, int H, int W, 
     RUN(launch_transmission(I, H, W, p, A, nullptr, t, lam, phi, nullptr, nullptr, s));
     RUN(launch_phin(phi, H, W, (float2 *)(ws + WL.phin_part), (SolveState *)(ws + WL.state), s));
     char *nws = (char *)net_workspace;
-    RUN(net_forward(params, base, I, t, A, 1, H, W, nws, NL, false, s));
+    RUN(net_forward(params, base, I, t, A, phi, 1, H, W, nws, NL, false, s));
     k_warm_start<<<gs((size_t)3 * H * W), 256, 0, s>>>(reinterpret_cast<const float *>(nws + NL.y), lam,
                                                       (size_t)H * W, u);
     int launches = 0;
