@@ -46,16 +46,23 @@ def measured_peaks():
         return None
 
 
+SWEEP_SOURCES = ("paper_2506_08793_gb300/csrc/sweep.cuh", "paper_2506_08793_gb300/csrc/solver.cu")
+
+
+def sweep_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def sweep_traffic():
-    """dram bytes per px*iter of the sweep from the committed ncu summary, or
-    None when the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "k_sweep_ncu.txt")
-    src = os.path.join(ROOT, "paper_2506_08793_gb300", "csrc", "solver.cu")
+    """DRAM bytes per px*iteration of the sweep kernel from the committed ncu
+    summary, or None when the kernel's sources changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "k_sweep_tma_4k.txt")
     try:
-        txt = open(path).read()
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        fields = dict(l.split("=", 1) for l in txt.splitlines() if "=" in l and not l.startswith("#"))
-        if fields.get("solver_cu_sha256_16", "").strip() != h:
+        fields = dict(l.split("=", 1) for l in open(path).read().splitlines() if "=" in l and not l.startswith("#"))
+        if fields.get("sweep_sources_sha256_16", "").strip() != sweep_source_hash():
             return None
         return float(fields["dram_bytes_per_px_iter"])
     except Exception:

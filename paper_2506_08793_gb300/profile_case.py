@@ -21,10 +21,23 @@ def main():
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--storage", type=int, default=0, help="0 f32, 1 bf16, 2 f16, 3 bf16->f32, 4 f16->f32")
     ap.add_argument("--tol", type=float, default=0.0)
+    ap.add_argument("--net", type=int, default=0, help="instead: N images through the warm-start network forward")
     ap.add_argument("--host-loop", action="store_true",
                     help="queue the sweeps from the host instead of the graph loop (profilers cannot "
                          "see kernels inside a graph with conditional nodes)")
     a = ap.parse_args()
+    if a.net:
+        from . import warmstart as WS
+
+        net = WS.WarmStartNet(32, seed=1)
+        I = torch.stack([torch.from_numpy(scenes.hazy_scene(a.seed + k, a.H, a.W)["I"]) for k in range(a.net)]).cuda()
+        t = torch.rand((a.net, a.H, a.W), device="cuda")
+        A = torch.rand((a.net, 3), device="cuda")
+        for _ in range(a.repeat):
+            y = net.predict(I, t, A, I)
+        torch.cuda.synchronize()
+        print(f"network forward on {a.net} x {a.H}x{a.W}: done")
+        return
     I = torch.from_numpy(scenes.hazy_scene(a.seed, a.H, a.W)["I"]).cuda()
     d = api.Dehazer(a.H, a.W, api.params(a.preset, tol=a.tol, max_iter=a.iters, storage=a.storage,
                                                    use_graph=0 if a.host_loop else 1))
