@@ -100,8 +100,8 @@ k_sweep(const SolveDesc *__restrict__ d) {
 // into shared memory by TMA, STAGES items ahead, together with the Phi and
 // lambda tiles when PL_SMEM (otherwise the walk reads those with vector
 // loads); the border halo is reflected in shared memory afterwards.
-template <int R, int NW, int STAGES, bool PL_SMEM, class T, bool EDGE>
-__global__ void __launch_bounds__(NW * 32)
+template <int R, int NW, int STAGES, bool PL_SMEM, class T, bool EDGE, int MINB = 0>
+__global__ void __launch_bounds__(NW * 32, MINB > 0 ? MINB : 16 / NW)
 k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
             const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
             const SolveDesc *__restrict__ d) {
@@ -526,8 +526,9 @@ __global__ void k_phase_state(SolveState *st) {
 // Sweep variants.  tma = 0: generic kernel, one CTA per (tile, channel);
 // tma = 1: persistent TMA kernel with `stages` items in flight per CTA.
 struct SweepCfg {
-    int R, NW, stages, tma;  // tma: 0 generic, 1 TMA (u, Phi, lambda), 2 TMA (u) + vector loads
+    int R, NW, stages, tma;  // tma: 0 generic, 1 TMA (u, Phi, lambda), 2 TMA (u) + vector loads, 3 streams
     bool edge;
+    int minb = 0;            // resident CTAs per SM the registers must allow (0: 16 warps' worth)
     int th() const { return R * NW; }
 };
 
@@ -553,13 +554,21 @@ static SweepFn sweep_fn(int R, int NW, bool edge) {
 }
 
 template <class T>
-static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge) {
-#define DH_ST(r, nw, st, pls)                                                                   \
-    if (R == r && NW == nw && stages == st && tma == (pls ? 1 : 2))                              \
-        return edge ? (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, true>                          \
-                    : (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, false>;
+static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge, int minb) {
+#define DH_STM(r, nw, st, pls, mb)                                                                  \
+    if (R == r && NW == nw && stages == st && tma == (pls ? 1 : 2) && minb == mb)                    \
+        return edge ? (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, true, mb>                          \
+                    : (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, false, mb>;
+#define DH_ST(r, nw, st, pls) DH_STM(r, nw, st, pls, 0)
     DH_ST(8, 4, 1, true)
     if (sizeof(T) == 4) {
+        DH_ST(6, 4, 1, true)
+        DH_ST(4, 4, 1, true)
+        DH_ST(16, 2, 1, true)
+        DH_ST(12, 2, 1, true)
+        DH_STM(8, 4, 1, true, 5)
+        DH_STM(6, 4, 1, true, 5)
+        DH_STM(4, 4, 1, true, 6)
         DH_ST(8, 4, 2, true)
         DH_ST(4, 8, 2, true)
         DH_ST(4, 8, 1, true)
@@ -626,6 +635,8 @@ static const SweepCfg kVariants[] = {
     {8, 8, 1, 2, true},  {16, 2, 2, 2, true}, {8, 4, 1, 3, true},  {8, 8, 1, 3, true},
     {16, 4, 1, 3, true}, {8, 2, 1, 3, true},  {8, 4, 1, 0, true},  {16, 4, 1, 0, true},
     {8, 8, 1, 0, true},
+    {6, 4, 1, 1, true},  {4, 4, 1, 1, true},  {16, 2, 1, 1, true}, {12, 2, 1, 1, true},
+    {8, 4, 1, 1, true, 5}, {6, 4, 1, 1, true, 5}, {4, 4, 1, 1, true, 6},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -733,11 +744,11 @@ struct GraphKey {
     int dev;
     const void *desc;
     const void *ptrs[4];
-    int H, W, R, NW, stages, tma, edge, storage;
+    int H, W, R, NW, stages, tma, edge, storage, minb;
     bool operator==(const GraphKey &o) const {
         return dev == o.dev && desc == o.desc && std::memcmp(ptrs, o.ptrs, sizeof(ptrs)) == 0 && H == o.H &&
                W == o.W && R == o.R && NW == o.NW && stages == o.stages && tma == o.tma && edge == o.edge &&
-               storage == o.storage;
+               storage == o.storage && minb == o.minb;
     }
 };
 
@@ -883,7 +894,7 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
         if (!rc) rc = encode_f32_map(&maps[2], v.phi, 3, W, H, 3, kTW, TH);
         if (!rc) rc = encode_f32_map(&maps[3], v.lam, 2, W, H, 1, kTW, TH);
         if (rc) return rc;
-        SweepTmaFn fn = sweep_tma_fn<T>(cfg.R, cfg.NW, cfg.stages, cfg.tma, cfg.edge);
+        SweepTmaFn fn = sweep_tma_fn<T>(cfg.R, cfg.NW, cfg.stages, cfg.tma, cfg.edge, cfg.minb);
         if (!fn) return DH_EINVAL;
         const unsigned smem = tma_smem_bytes(TH, cfg.stages, cfg.tma, esize);
         const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
@@ -904,7 +915,7 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
         int dev = 0;
         DH_CUDA_TRY(cudaGetDevice(&dev));
         GraphKey key{dev, desc_dev, {v.u[0], v.u[1], v.phi, v.lam}, H, W, cfg.R, cfg.NW, cfg.stages, cfg.tma,
-                     cfg.edge ? 1 : 0, v.storage};
+                     cfg.edge ? 1 : 0, v.storage, cfg.minb};
         GraphEntry ge;
         int rc = get_loop_graph(key, ls, &ge);
         if (rc != DH_OK) return rc;
