@@ -67,6 +67,10 @@ extern "C" {
 #define DH_STORE_BF16_F32 3
 #define DH_STORE_F16_F32 4
 
+/* boundary of the PDE (dh_params.boundary) */
+#define DH_BOUNDARY_REFLECT 0 /* half-sample symmetric extension: zero flux (default) */
+#define DH_BOUNDARY_ZERO 1    /* u = 0 outside the image: the H^1_0 setting of Sec. III */
+
 /* ablation switches (Sec. IV-E, Table II), OR-ed into dh_params.variant */
 #define DH_VAR_NO_ADAPTIVE 1 /* lambda(t) == lambda0 */
 #define DH_VAR_NO_EDGE 2     /* D == 1 (linear diffusion) */
@@ -92,6 +96,7 @@ typedef struct dh_params {
                            while condition (default); 0: host-queued launches */
     int sweep_variant;  /* sweep kernel variant (1..dh_sweep_variants()-1); 0 = the
                            tuned choice for this shape if dh_tune ran, else default */
+    int boundary;       /* DH_BOUNDARY_* for the flux stencil and the Gaussian */
 } dh_params;
 
 typedef struct dh_report {

@@ -50,6 +50,8 @@ class OrParams(ctypes.Structure):
         ("sigma", ctypes.c_double),
         ("radius", ctypes.c_int),
         ("tau", ctypes.c_double),
+        ("boundary", ctypes.c_int),
+        ("variant", ctypes.c_int),
     ]
 
 
@@ -58,7 +60,7 @@ class OrParams(ctypes.Structure):
 # preset differs only in eps = 1.0 (the paper's eps = 1e-3 breaks its own
 # step-size condition of App. A-A at tau = 0.2).
 PAPER = dict(patch=15, topk_permille=1, omega=0.95, t0=0.1, lambda0=0.5, beta=3.0,
-             eps=1e-3, sigma=2.0, radius=2, tau=0.2)
+             eps=1e-3, sigma=2.0, radius=2, tau=0.2, boundary=0, variant=0)
 STABLE = dict(PAPER, eps=1.0)
 
 
@@ -83,8 +85,8 @@ def lib():
                                           ctypes.POINTER(OrParams), P, P, P]
             L.or_gauss_weights.argtypes = [ctypes.c_double, ctypes.c_int, P]
             L.or_F.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrParams), P]
-            L.or_div.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, P]
-            L.or_gauss.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, P]
+            L.or_div.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P]
+            L.or_gauss.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P]
             L.or_solve.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrParams),
                                    ctypes.c_int, ctypes.c_double, P]
             L.or_solve.restype = ctypes.c_int
@@ -158,19 +160,19 @@ def F(u, Phi, lam, p: OrParams) -> np.ndarray:
     return out
 
 
-def div(u, eps) -> np.ndarray:
+def div(u, eps, boundary=0, no_edge=False) -> np.ndarray:
     u = _f64(u)
     H, W = u.shape
     out = np.empty_like(u)
-    lib().or_div(_ptr(u), H, W, eps, _ptr(out))
+    lib().or_div(_ptr(u), H, W, eps, boundary, int(no_edge), _ptr(out))
     return out
 
 
-def gauss(u, sigma=2.0, radius=2) -> np.ndarray:
+def gauss(u, sigma=2.0, radius=2, boundary=0) -> np.ndarray:
     u = _f64(u)
     H, W = u.shape
     out = np.empty_like(u)
-    lib().or_gauss(_ptr(u), H, W, sigma, radius, _ptr(out))
+    lib().or_gauss(_ptr(u), H, W, sigma, radius, boundary, _ptr(out))
     return out
 
 

@@ -118,6 +118,8 @@ void or_transmission(const float *I, const double A[3], const double *td, int H,
         const double ti = 1.0 - p->omega * td[i];
         t[i] = ti;
         lam[i] = p->lambda0 * exp(-p->beta * (1.0 - ti));
+        if (p->variant & 1) lam[i] = p->lambda0; /* w/o adaptive regularisation */
+        if (p->variant & 4) lam[i] = 0.0;        /* w/o nonlocal regularisation */
         const double den = ti > p->t0 ? ti : p->t0;
         for (int c = 0; c < 3; ++c)
             Phi[c * N + i] = ((double)I[c * N + i] - A[c] * (1.0 - ti)) / den;
@@ -135,7 +137,14 @@ void or_gauss_weights(double sigma, int radius, double *w) {
     for (int k = 0; k <= 2 * radius; ++k) w[k] /= s;
 }
 
-void or_gauss(const double *u, int H, int W, double sigma, int radius, double *out) {
+/* u at column i, row j outside the image: the reflecting boundary, or zero
+ * for the Dirichlet (H^1_0) setting */
+static double U(const double *u, int H, int W, long i, long j, int boundary) {
+    if (boundary == 1 && (i < 0 || i >= W || j < 0 || j >= H)) return 0.0;
+    return u[reflect(j, H) * W + reflect(i, W)];
+}
+
+void or_gauss(const double *u, int H, int W, double sigma, int radius, int boundary, double *out) {
     double w[64];
     or_gauss_weights(sigma, radius, w);
 #pragma omp parallel for schedule(static)
@@ -143,13 +152,9 @@ void or_gauss(const double *u, int H, int W, double sigma, int radius, double *o
         for (int x = 0; x < W; ++x) {
             /* G(u)(x) = sum_y K(x,y) u(y) with the separable normalised kernel */
             double g = 0.0;
-            for (int b = -radius; b <= radius; ++b) {
-                const long yy = reflect(y + b, H);
-                for (int a = -radius; a <= radius; ++a) {
-                    const long xx = reflect(x + a, W);
-                    g += w[b + radius] * w[a + radius] * u[yy * W + xx];
-                }
-            }
+            for (int b = -radius; b <= radius; ++b)
+                for (int a = -radius; a <= radius; ++a)
+                    g += w[b + radius] * w[a + radius] * U(u, H, W, x + a, y + b, boundary);
             out[(long)y * W + x] = g;
         }
     }
@@ -157,34 +162,32 @@ void or_gauss(const double *u, int H, int W, double sigma, int radius, double *o
 
 /* ------------------------------------------------------------- App. A-B-1 */
 
-/* u at column i, row j with the reflecting boundary */
-static double U(const double *u, int H, int W, long i, long j) {
-    return u[reflect(j, H) * W + reflect(i, W)];
-}
-
 /* D u_x on the x-face (i+1/2, j): forward difference in x, central difference
- * in y at cell (i, j), D = (|grad u| + eps)^-1, Delta x = Delta y = 1. */
-static double flux_x(const double *u, int H, int W, long i, long j, double eps) {
-    const double ux = U(u, H, W, i + 1, j) - U(u, H, W, i, j);
-    const double uy = (U(u, H, W, i, j + 1) - U(u, H, W, i, j - 1)) / 2.0;
-    const double D = 1.0 / (sqrt(ux * ux + uy * uy) + eps);
+ * in y at cell (i, j), D = (|grad u| + eps)^-1, Delta x = Delta y = 1
+ * (D == 1 for the "w/o edge-preserving term" ablation). */
+static double flux_x(const double *u, int H, int W, long i, long j, double eps, int bnd, int no_edge) {
+    const double ux = U(u, H, W, i + 1, j, bnd) - U(u, H, W, i, j, bnd);
+    const double uy = (U(u, H, W, i, j + 1, bnd) - U(u, H, W, i, j - 1, bnd)) / 2.0;
+    const double D = no_edge ? 1.0 : 1.0 / (sqrt(ux * ux + uy * uy) + eps);
     return D * ux;
 }
 
 /* D u_y on the y-face (i, j+1/2): the same with the roles of x and y swapped. */
-static double flux_y(const double *u, int H, int W, long i, long j, double eps) {
-    const double uy = U(u, H, W, i, j + 1) - U(u, H, W, i, j);
-    const double ux = (U(u, H, W, i + 1, j) - U(u, H, W, i - 1, j)) / 2.0;
-    const double D = 1.0 / (sqrt(ux * ux + uy * uy) + eps);
+static double flux_y(const double *u, int H, int W, long i, long j, double eps, int bnd, int no_edge) {
+    const double uy = U(u, H, W, i, j + 1, bnd) - U(u, H, W, i, j, bnd);
+    const double ux = (U(u, H, W, i + 1, j, bnd) - U(u, H, W, i - 1, j, bnd)) / 2.0;
+    const double D = no_edge ? 1.0 : 1.0 / (sqrt(ux * ux + uy * uy) + eps);
     return D * uy;
 }
 
-void or_div(const double *u, int H, int W, double eps, double *out) {
+void or_div(const double *u, int H, int W, double eps, int boundary, int no_edge, double *out) {
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < H; ++j) {
         for (int i = 0; i < W; ++i) {
-            const double dx = flux_x(u, H, W, i, j, eps) - flux_x(u, H, W, i - 1, j, eps);
-            const double dy = flux_y(u, H, W, i, j, eps) - flux_y(u, H, W, i, j - 1, eps);
+            const double dx = flux_x(u, H, W, i, j, eps, boundary, no_edge) -
+                              flux_x(u, H, W, i - 1, j, eps, boundary, no_edge);
+            const double dy = flux_y(u, H, W, i, j, eps, boundary, no_edge) -
+                              flux_y(u, H, W, i, j - 1, eps, boundary, no_edge);
             out[(long)j * W + i] = dx + dy;
         }
     }
@@ -196,8 +199,8 @@ void or_F(const double *u, const double *Phi, const double *lam, int H, int W,
     double *dv = (double *)malloc(sizeof(double) * (size_t)N);
     double *g = (double *)malloc(sizeof(double) * (size_t)N);
     for (int c = 0; c < 3; ++c) {
-        or_div(u + c * N, H, W, p->eps, dv);
-        or_gauss(u + c * N, H, W, p->sigma, p->radius, g);
+        or_div(u + c * N, H, W, p->eps, p->boundary, (p->variant & 2) != 0, dv);
+        or_gauss(u + c * N, H, W, p->sigma, p->radius, p->boundary, g);
         for (long i = 0; i < N; ++i)
             F[c * N + i] = dv[i] - lam[i] * g[i] + Phi[c * N + i];
     }

@@ -22,6 +22,8 @@
  *                          limit, 1-D step closed form, conservation)
  *   or_solve               pinned (constant-image trajectory closed form,
  *                          Newton root, uniqueness, resume)
+ *   boundary = 1 / variant  pinned (scipy zero-padded gaussian_filter and laplace;
+ *                          D == 1 is the 5-point Laplacian; lambda ablations)
  */
 #ifndef DEHAZE_ORACLE_H
 #define DEHAZE_ORACLE_H
@@ -41,6 +43,8 @@ typedef struct {
     double sigma;          /* Gaussian width, Sec. II-C: 2.0 */
     int    radius;         /* Gaussian half-width; 5x5 kernel => 2 (App. A-B-2) */
     double tau;            /* relaxation parameter, App. A-A: 0.2 */
+    int    boundary;       /* 0: half-sample reflection (zero flux); 1: u = 0 outside (H^1_0, Sec. III) */
+    int    variant;        /* ablations of Sec. IV-E: 1 lambda == lambda0, 2 D == 1, 4 lambda == 0 */
 } or_params;
 
 /* Sec. II-D dark channel: out(x) = min_c min_{y in Omega(x)} I^c(y)/A^c over a
@@ -70,11 +74,12 @@ void or_gauss_weights(double sigma, int radius, double *w);
 void or_F(const double *u, const double *Phi, const double *lam, int H, int W,
           const or_params *p, double *F);
 
-/* The diffusion term alone, div(D grad u), one channel (HxW). */
-void or_div(const double *u, int H, int W, double eps, double *out);
+/* The diffusion term alone, div(D grad u), one channel (HxW); boundary as in
+ * or_params; no_edge: D == 1. */
+void or_div(const double *u, int H, int W, double eps, int boundary, int no_edge, double *out);
 
 /* The Gaussian term alone, G(u), one channel (HxW). */
-void or_gauss(const double *u, int H, int W, double sigma, int radius, double *out);
+void or_gauss(const double *u, int H, int W, double sigma, int radius, int boundary, double *out);
 
 /* App. A-A fixed-point iteration u <- u + tau*F(u) from u (in/out).
  * For n = 0, 1, ...: rho_n^c = ||F^c(u^n)|| / ||Phi^c|| (||F^c|| when

@@ -24,6 +24,7 @@ DH_PRESET_PAPER = 0
 DH_PRESET_STABLE = 1
 DH_STORE_F32, DH_STORE_BF16, DH_STORE_F16, DH_STORE_BF16_F32, DH_STORE_F16_F32 = 0, 1, 2, 3, 4
 DH_VAR_NO_ADAPTIVE, DH_VAR_NO_EDGE, DH_VAR_NO_NONLOCAL = 1, 2, 4
+DH_BOUNDARY_REFLECT, DH_BOUNDARY_ZERO = 0, 1
 
 # Every symbol include/dehaze.h declares.
 EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes",
@@ -54,6 +55,7 @@ class DhParams(ctypes.Structure):
         ("variant", ctypes.c_int),
         ("use_graph", ctypes.c_int),
         ("sweep_variant", ctypes.c_int),
+        ("boundary", ctypes.c_int),
     ]
 
     def replace(self, **kw) -> "DhParams":

@@ -49,6 +49,7 @@ static bool params_ok(const dh_params *p) {
     if (p->storage < DH_STORE_F32 || p->storage > DH_STORE_F16_F32) return false;
     if (p->variant & ~(DH_VAR_NO_ADAPTIVE | DH_VAR_NO_EDGE | DH_VAR_NO_NONLOCAL)) return false;
     if (p->sweep_variant < 0 || p->sweep_variant >= sweep_variant_count()) return false;
+    if (p->boundary != DH_BOUNDARY_REFLECT && p->boundary != DH_BOUNDARY_ZERO) return false;
     return true;
 }
 
@@ -124,6 +125,7 @@ int dh_params_default(dh_params *p, int preset) {
     p->variant = 0;
     p->use_graph = 1;
     p->sweep_variant = 0;
+    p->boundary = DH_BOUNDARY_REFLECT;
     return DH_OK;
 }
 

@@ -195,7 +195,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
                 failed = true;
                 break;
             }
-            if (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + kBTH + 2 > H) {
+            if (!d->dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + kBTH + 2 > H)) {
                 for (int e = threadIdx.x; e < SH * SW; e += kBNW * 32) {
                     const int r = e / SW, q = e - r * SW;
                     const int gy = y0 - 2 + r, gx = x0 - 4 + q;
@@ -214,7 +214,11 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
             const float *u = static_cast<const float *>(d->u[cur]) + c * N;
             for (int e = threadIdx.x; e < SH * SW; e += kBNW * 32) {
                 const int r = e / SW, q = e - r * SW;
-                s[e] = u[(size_t)reflect_idx(y0 - 2 + r, H) * W + reflect_idx(x0 - 4 + q, W)];
+                const int yy = y0 - 2 + r, xx = x0 - 4 + q;
+                if (d->dirichlet)
+                    s[e] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? u[(size_t)yy * W + xx] : 0.f;
+                else
+                    s[e] = u[(size_t)reflect_idx(yy, H) * W + reflect_idx(xx, W)];
             }
             for (int e = threadIdx.x; e < kBTH * kTW; e += kBNW * 32) {
                 const int r = e / kTW, q = e - r * kTW;
@@ -436,6 +440,7 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
         d.tol = p->tol;
         d.tau = p->tau;
         d.eps = p->eps;
+        d.dirichlet = p->boundary == DH_BOUNDARY_ZERO;
         double wgt[3];
         for (int k = 0; k <= 2; ++k) wgt[k] = exp(-(double)(k * k) / (2.0 * (double)p->sigma * p->sigma));
         const double sum = wgt[0] + 2.0 * (wgt[1] + wgt[2]);

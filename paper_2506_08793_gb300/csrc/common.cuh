@@ -54,6 +54,7 @@ struct SolveDesc {
     int vec;             // W % 4 == 0 and every plane 16-byte aligned
     int storage;         // element type of u[]: 0 float, 1 bf16, 2 f16
     int phase_stop;      // 1: stop this phase when the residual stalls
+    int dirichlet;       // 1: u = 0 outside the image, else reflecting boundary
     int H, W;
     int max_iter;
     int depth;           // iterations fused per sweep launch

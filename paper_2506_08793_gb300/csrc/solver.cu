@@ -40,10 +40,15 @@ k_sweep(const SolveDesc *__restrict__ d) {
     const float *__restrict__ phi = d->phi + c * N;
     const float *__restrict__ lam = d->lam;
 
+    const bool dirichlet = d->dirichlet != 0;
     for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
         const int r = e / SW, q = e - r * SW;
-        const int gy = reflect_idx(y0 - 2 + r, H), gx = reflect_idx(x0 - 4 + q, W);
-        s[e] = Store<T>::get(u + (size_t)gy * W + gx);
+        const int yy = y0 - 2 + r, xx = x0 - 4 + q;
+        if (dirichlet) {
+            s[e] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? Store<T>::get(u + (size_t)yy * W + xx) : 0.f;
+        } else {
+            s[e] = Store<T>::get(u + (size_t)reflect_idx(yy, H) * W + reflect_idx(xx, W));
+        }
     }
     __syncthreads();
 
@@ -151,6 +156,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
+    const bool dirichlet = d->dirichlet != 0;
     const float *__restrict__ phi_all = d->phi;
     const float *__restrict__ glam = d->lam;
     float2 *__restrict__ part = d->part;
@@ -172,8 +178,9 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             failed = true;
             break;
         }
-        // reflect the halo cells that fall outside the image (TMA filled zeros)
-        if (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + TH + 2 > H) {
+        // reflect the halo cells that fall outside the image (TMA filled zeros,
+        // which is already the Dirichlet boundary)
+        if (!dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + TH + 2 > H)) {
             for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
                 const int r = e / SW, q = e - r * SW;
                 const int gy = y0 - 2 + r, gx = x0 - HALO + q;
@@ -684,6 +691,7 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) v = tune_get(dev, H, W, p->storage);
     }
+    if (p->boundary == DH_BOUNDARY_ZERO && v > 0 && v < kNumVariants && kVariants[v].tma == 3) v = 0;
     if (v > 0 && v < kNumVariants && (kVariants[v].tma == 0 || tma_ok)) {
         c = kVariants[v];
         c.edge = edge;
@@ -696,6 +704,7 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
             c.NW = nw;
             c.stages = st;
             c.tma = tma_ok ? t : 0;
+            if (c.tma == 3 && p->boundary == DH_BOUNDARY_ZERO) c.tma = 1;
         }
     }
     if (!c.tma && !sweep_fn<float>(c.R, c.NW, c.edge)) { c.R = 8; c.NW = 4; }
@@ -960,6 +969,7 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
     v.tol = p->tol;
     v.tau = p->tau;
     v.eps = p->eps;
+    v.dirichlet = p->boundary == DH_BOUNDARY_ZERO;
     {  // App. A-B-2: normalised 5-tap Gaussian, sigma = p->sigma
         double w[3];
         for (int k = 0; k <= 2; ++k) w[k] = exp(-(double)(k * k) / (2.0 * (double)p->sigma * p->sigma));

@@ -36,8 +36,8 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_struct_sizes_match_header():
-    # dh_params: 17 4-byte fields; dh_report: 2 ints, 6 floats, long long, 2 floats, int (+pad)
-    assert ctypes.sizeof(N.DhParams) == 68
+    # dh_params: 18 4-byte fields; dh_report: 2 ints, 6 floats, long long, 2 floats, int (+pad)
+    assert ctypes.sizeof(N.DhParams) == 72
     assert ctypes.sizeof(N.DhReport) == 56
 
 
@@ -70,6 +70,7 @@ def test_workspace_bytes():
     assert N.dh_workspace_bytes(4, 4, p.replace(patch=4)) == 0
     assert N.dh_workspace_bytes(4, 4, p.replace(radius=3)) == 0
     assert N.dh_workspace_bytes(4, 4, p.replace(eps=0.0)) == 0
+    assert N.dh_workspace_bytes(4, 4, p.replace(boundary=2)) == 0
     assert N.dh_workspace_bytes(4, 4, None) > 0
 
 

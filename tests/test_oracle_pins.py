@@ -311,3 +311,34 @@ def test_paper_preset_violates_step_condition(orc):
     _, n, rho = orc.solve(Phi, Phi, lam, p, 200, 1e-4)
     r = rho.max(axis=1)
     assert n == 200 and np.any(np.diff(r) > 0) and r[-1] > 1e-2
+
+
+# ------------------------------------------------------------ boundary option and ablations
+
+@pytest.mark.parametrize("H,W", [(3, 4), (17, 11)])
+def test_dirichlet_boundary_is_zero_padding(orc, H, W):
+    """u = 0 outside the image (H^1_0, Sec. III): the Gaussian is scipy's with
+    zero padding and eps*div tends to the zero-padded 5-point Laplacian."""
+    u = rnd(H * W + 5, H, W, lo=-2, hi=3)
+    want = ndi.gaussian_filter(u, 2.0, truncate=1.0, mode="constant", cval=0.0)
+    assert np.allclose(orc.gauss(u, boundary=1), want, rtol=0, atol=1e-13)
+    eps = 1e9
+    want = ndi.laplace(u, mode="constant", cval=0.0)
+    assert np.allclose(eps * orc.div(u, eps, boundary=1), want, rtol=0, atol=1e-6)
+
+
+def test_no_edge_ablation_is_linear_diffusion(orc):
+    """D == 1 (w/o edge-preserving term): div(grad u) is the 5-point Laplacian."""
+    u = rnd(8, 19, 23, lo=-1, hi=1)
+    assert np.allclose(orc.div(u, 1e-3, no_edge=True), ndi.laplace(u, mode="reflect"), rtol=0, atol=1e-13)
+
+
+def test_lambda_ablations(orc):
+    I = scenes.hazy_scene(12, 20, 30)["I"]
+    dc = orc.dark_channel(I, 15, None)
+    A, _, _ = orc.atmospheric_light(I, dc, 1)
+    td = orc.dark_channel(I, 15, A)
+    _, lam, Phi = orc.transmission(I, A, td, orc.params(variant=1))
+    assert np.all(lam == 0.5)
+    _, lam0, Phi0 = orc.transmission(I, A, td, orc.params(variant=4))
+    assert np.all(lam0 == 0.0) and np.array_equal(Phi, Phi0)
