@@ -132,6 +132,56 @@ def cpu_sample(I, H, W, iters, n_gpu_iters):
     return (t1 - t0) + per_iter * n_gpu_iters, oracle.num_threads(), (t1 - t0), per_iter
 
 
+def batch_extra(api, p, n=16, reps=3):
+    """Uneven-size batch (sizes drawn from the four photo sizes) in one batched
+    solve: images/s and MPix*iter/s (device time, inputs resident)."""
+    import torch
+
+    from paper_2506_08793_gb300 import scenes
+
+    sizes = scenes.batch_sizes(3000, n)
+    imgs = [torch.from_numpy(scenes.hazy_scene(3000 + k, H, W)["I"]).cuda() for k, (H, W) in enumerate(sizes)]
+    b = api.BatchDehazer(sizes, p)
+    b(imgs)  # warm-up (graph build)
+    ms = []
+    for _ in range(reps):
+        r = b(imgs)
+        ms.append(r[0].ms)
+    t = statistics.median(ms) / 1e3
+    units = sum(H * W * x.n_iter for (H, W), x in zip(sizes, r)) / 1e6
+    return {"images": n, "sizes": "uniform over 480x640, 720x1280, 1080x1920, 1200x1600 (seed 3000)",
+            "images_per_s": n / t, "value": units / t, "unit": UNIT, "ms": 1e3 * t,
+            "all_converged": all(x.status == 0 for x in r)}
+
+
+def warm_extra(api, p, im, train_n=256, steps=600):
+    """Learned warm start: a network trained here on train_n solver-generated
+    256x256 scenes (the library's own kernels), then the 1080p scene from the
+    cold start (u0 = Phi) and from the network's u0, to the same residual."""
+    import torch
+
+    from paper_2506_08793_gb300 import warmstart as WS
+
+    t0 = time.perf_counter()
+    data = WS.make_dataset(train_n, 256, 256, seed0=5_000_000, p=p)
+    net = WS.WarmStartNet(32, seed=1)
+    log = net.train(data, steps=steps, batch=8, lr=1e-3, lr_end=5e-5, log_every=steps)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    wd = WS.WarmDehazer(net, im["H"], im["W"], p)
+    wd(im["Id"])
+    reps = [wd(im["Id"]) for _ in range(5)]
+    cold = [im["dz"](im["Id"]) for _ in range(5)]
+    ms_w = statistics.median(r.ms for r in reps)
+    ms_c = statistics.median(r.ms for r in cold)
+    return {"image": f"{im['W']}x{im['H']}", "train_scenes": train_n, "train_steps": steps,
+            "train_s": t_train, "final_loss": log[-1][1],
+            "cold": {"n_iter": cold[0].n_iter, "ms": ms_c, "images_per_s": 1e3 / ms_c},
+            "warm": {"n_iter": reps[0].n_iter, "ms": ms_w, "images_per_s": 1e3 / ms_w,
+                     "rho": max(reps[0].rho)},
+            "speedup": ms_c / ms_w}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -179,6 +229,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=12)
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default variant)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched (uneven sizes) and learned-warm-start measurements")
     args = ap.parse_args()
     rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
@@ -295,6 +347,9 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["batch"] = batch_extra(api, p)
+        line["warm_start"] = warm_extra(api, p, imgs[0])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         im = imgs[0]
         secs, cores, fe, per_iter = cpu_sample(im["Inp"], im["H"], im["W"], args.cpu_iters, per_img[0]["n_iter"])
