@@ -33,8 +33,14 @@ struct SolveState {
     float phin2[3];    // ||Phi^c||^2
     int err;           // error raised inside a sweep (DH_ETIMEOUT), 0 if none
     int phase_start;   // first n of the current precision phase
-    int pad[2];
+    int depth;         // sweeps per launch of the current loop (SolveDesc::depth)
+    int pad;
     float rmax[kStallWindow];  // max_c rho_n of the last iterations (ring)
+    // Grid-barrier generation of the multi-iteration sweep, alone in its
+    // 128-byte line so that the CTAs polling it do not contend with the
+    // arrivals and state updates above.  Never reset: kernels read it first.
+    unsigned gen;
+    int pad_gen[31];
 };
 
 // status a 16-bit phase ends with when its residual stalls (internal)
@@ -57,7 +63,7 @@ struct SolveDesc {
     int dirichlet;       // 1: u = 0 outside the image, else reflecting boundary
     int H, W;
     int max_iter;
-    int depth;           // iterations fused per sweep launch
+    int depth;           // iterations per launch of the multi-iteration sweep (1 otherwise)
     int nblk;            // residual partials per channel (one per tile)
     float tol, tau, eps;
     float wg0, wg1, wg2; // Gaussian weights at offsets 0, +-1, +-2

@@ -104,8 +104,19 @@ k_sweep(const SolveDesc *__restrict__ d) {
 // (tile, channel) items; one thread streams each item's u^n tile (with halo)
 // into shared memory by TMA, STAGES items ahead, together with the Phi and
 // lambda tiles when PL_SMEM (otherwise the walk reads those with vector
-// loads); the border halo is reflected in shared memory afterwards.
-template <int R, int NW, int STAGES, bool PL_SMEM, class T, bool EDGE, int MINB = 0>
+// loads); the border halo is reflected in shared memory afterwards.  Each
+// item's tiles are first pulled into L2 one item before their load is issued.
+// Odd iterations walk a CTA's items in reverse order, so that an iteration
+// starts on the tiles the previous one touched last (still in L2).
+//
+// MULTI: a cooperative launch runs up to d->depth iterations.  Between two
+// iterations the CTAs meet at a grid barrier whose last arrival reduces the
+// residual and decides (finish_iteration), then bumps st->gen; the others
+// wait for the bump (bounded, DH_ETIMEOUT).  The u^{n+1} tiles that the next
+// iteration loads by TMA were written by generic stores of other CTAs: the
+// writers fence them to the async proxy before arriving and the issuing
+// thread fences again after the barrier.
+template <int R, int NW, int STAGES, bool PL_SMEM, class T, bool EDGE, int MINB = 0, bool MULTI = false>
 __global__ void __launch_bounds__(NW * 32, MINB > 0 ? MINB : 16 / NW)
 k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
             const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
@@ -119,40 +130,25 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t bar[STAGES];
     __shared__ float2 red[NW];
-    __shared__ int s_last;
+    __shared__ int s_last, s_timeout;
 
     SolveState *st = d->st;
     clear_condition(d);
     if (__ldcg(&st->done)) return;
+    unsigned gen = 0;
+    if (MULTI) gen = ld_acquire_gpu(&st->gen);  // before this CTA can arrive anywhere
     const int H = d->H, W = d->W;
-    const int cur = __ldcg(&st->cur);
-    const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
-    T *__restrict__ ubase = static_cast<T *>(d->u[cur ^ 1]);
     const size_t N = (size_t)H * W;
     const int ntx = (W + kTW - 1) / kTW, nty = (H + TH - 1) / TH;
     const int ntiles = ntx * nty, nitems = 3 * ntiles;
     const int G = gridDim.x;
+    const int m = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;  // items of this CTA
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < STAGES; ++k) mbar_init(&bar[k], 1);
         fence_mbar_init();
     }
     __syncthreads();
-
-    auto issue = [&](int item, int stage) {
-        const int tile = item / 3, c = item - 3 * tile;
-        const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * TH;
-        unsigned char *sb = smem + stage * P::STAGE;
-        mbar_arrive_expect_tx(&bar[stage], P::TX);
-        tma_load_3d(sb + P::U_OFF, tm_u, &bar[stage], x0 - HALO, y0 - 2, c);
-        if (PL_SMEM) {
-            tma_load_3d(sb + P::PHI_OFF, &tm_phi, &bar[stage], x0, y0, c);
-            tma_load_2d(sb + P::LAM_OFF, &tm_lam, &bar[stage], x0, y0);
-        }
-    };
-    if (threadIdx.x == 0)
-        for (int k = 0; k < STAGES; ++k)
-            if (blockIdx.x + k * G < nitems) issue(blockIdx.x + k * G, k);
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
@@ -161,93 +157,171 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     const float *__restrict__ glam = d->lam;
     float2 *__restrict__ part = d->part;
     const int nblk = d->nblk;
-    int k = 0;
+    const int iters = MULTI ? d->depth : 1;
+    int k = 0;  // items this CTA has started in the launch (stage and parity)
     bool failed = false;
-    for (int item = blockIdx.x; item < nitems; item += G, ++k) {
-        const int stage = k % STAGES;
-        const uint32_t parity = (k / STAGES) & 1;
-        const int tile = item / 3, c = item - 3 * tile;
-        const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * TH;
-        unsigned char *sb = smem + stage * P::STAGE;
-        T *s = reinterpret_cast<T *>(sb + P::U_OFF);
-        const float *sphi = reinterpret_cast<const float *>(sb + P::PHI_OFF);
-        const float *slam = reinterpret_cast<const float *>(sb + P::LAM_OFF);
-
-        const bool ok = mbar_wait_bounded(&bar[stage], parity, kWaitLimitCycles);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
+    for (int it = 0; it < iters; ++it) {
+        const int cur = __ldcg(&st->cur);
+        const bool rev = (__ldcg(&st->n) & 1) != 0;
+        const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
+        T *__restrict__ ubase = static_cast<T *>(d->u[cur ^ 1]);
+        auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
+        auto tile_xy = [&](int item, int &c, int &x0, int &y0) {
+            const int tile = item / 3;
+            c = item - 3 * tile;
+            x0 = (tile % ntx) * kTW;
+            y0 = (tile / ntx) * TH;
+            return tile;
+        };
+        auto issue = [&](int j, int stage) {
+            int c, x0, y0;
+            tile_xy(item_at(j), c, x0, y0);
+            unsigned char *sb = smem + stage * P::STAGE;
+            mbar_arrive_expect_tx(&bar[stage], P::TX);
+            tma_load_3d(sb + P::U_OFF, tm_u, &bar[stage], x0 - HALO, y0 - 2, c);
+            if (PL_SMEM) {
+                tma_load_3d(sb + P::PHI_OFF, &tm_phi, &bar[stage], x0, y0, c);
+                tma_load_2d(sb + P::LAM_OFF, &tm_lam, &bar[stage], x0, y0);
+            }
+        };
+        auto prefetch = [&](int j) {
+            int c, x0, y0;
+            tile_xy(item_at(j), c, x0, y0);
+            tma_prefetch_3d(tm_u, x0 - HALO, y0 - 2, c);
+            if (PL_SMEM) {
+                tma_prefetch_3d(&tm_phi, x0, y0, c);
+                tma_prefetch_2d(&tm_lam, x0, y0);
+            }
+        };
+        if (threadIdx.x == 0) {
+            if (MULTI && it > 0) fence_proxy_async_global();
+            for (int j = 0; j < STAGES && j < m; ++j) issue(j, (k + j) % STAGES);
         }
-        // reflect the halo cells that fall outside the image (TMA filled zeros,
-        // which is already the Dirichlet boundary)
-        if (!dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + TH + 2 > H)) {
-            for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
-                const int r = e / SW, q = e - r * SW;
-                const int gy = y0 - 2 + r, gx = x0 - HALO + q;
-                const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
-                const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
-                const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
-                if ((fy && (inx || fx)) || (fx && iny)) {
-                    const int sy = reflect_idx(gy, H) - (y0 - 2), sx = reflect_idx(gx, W) - (x0 - HALO);
-                    s[e] = s[sy * SW + sx];
+        int j = 0;
+        for (; j < m; ++j, ++k) {
+            const int stage = k % STAGES;
+            const uint32_t parity = (k / STAGES) & 1;
+            int c, x0, y0;
+            const int tile = tile_xy(item_at(j), c, x0, y0);
+            unsigned char *sb = smem + stage * P::STAGE;
+            T *s = reinterpret_cast<T *>(sb + P::U_OFF);
+            const float *sphi = reinterpret_cast<const float *>(sb + P::PHI_OFF);
+            const float *slam = reinterpret_cast<const float *>(sb + P::LAM_OFF);
+            if (threadIdx.x == 0 && j + STAGES < m) prefetch(j + STAGES);
+
+            const bool ok = mbar_wait_bounded(&bar[stage], parity, kWaitLimitCycles);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            // reflect the halo cells that fall outside the image (TMA filled zeros,
+            // which is already the Dirichlet boundary)
+            if (!dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + TH + 2 > H)) {
+                for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
+                    const int r = e / SW, q = e - r * SW;
+                    const int gy = y0 - 2 + r, gx = x0 - HALO + q;
+                    const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
+                    const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
+                    const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
+                    if ((fy && (inx || fx)) || (fx && iny)) {
+                        const int sy = reflect_idx(gy, H) - (y0 - 2), sx = reflect_idx(gx, W) - (x0 - HALO);
+                        s[e] = s[sy * SW + sx];
+                    }
+                }
+                fence_proxy_async_smem();  // these writes precede the stage's next TMA load
+            }
+            __syncthreads();
+
+            T *__restrict__ un = ubase + c * N;
+            const int x = x0 + 4 * lane;
+            float rs = 0.f, rc = 0.f;
+            const float *__restrict__ gphi = phi_all + c * N;
+            auto pl = [&](int ty, float *ph, float *la) {
+                float4 p4, l4;
+                if (PL_SMEM) {
+                    p4 = *reinterpret_cast<const float4 *>(sphi + ty * kTW + 4 * lane);
+                    l4 = *reinterpret_cast<const float4 *>(slam + ty * kTW + 4 * lane);
+                } else {
+                    const int y = y0 + ty;
+                    p4 = l4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (y < H && x < W) {
+                        p4 = __ldg(reinterpret_cast<const float4 *>(gphi + (size_t)y * W + x));
+                        l4 = __ldg(reinterpret_cast<const float4 *>(glam + (size_t)y * W + x));
+                    }
+                }
+                ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
+                la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
+            };
+            auto sink = [&](int ty, const float *nu, const float *F) {
+                const int y = y0 + ty;
+                if (y >= H || x >= W) return;  // W % 4 == 0: x < W covers all 4 columns
+                float q = 0.f;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) q = fmaf(F[jj], F[jj], q);
+                neumaier_add(rs, rc, q);
+                Store<T>::write4(un + (size_t)y * W + x, nu[0], nu[1], nu[2], nu[3]);
+            };
+            walk_rows<R, SW, T, EDGE>(s, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
+
+            const float2 tot = block_pair_sum<NW>(rs, rc, red);  // ends with a barrier
+            if (threadIdx.x == 0) {
+                part[(size_t)c * nblk + tile] = tot;
+                if (j + STAGES < m) {
+                    fence_proxy_async_smem();
+                    issue(j + STAGES, stage);
                 }
             }
-            fence_proxy_async_smem();  // these writes precede the stage's next TMA load
+            __syncthreads();  // red[] reuse
+        }
+        if (failed) {
+            // let every load already issued land (bounded) before going on
+            for (int q = 0; q < STAGES && j + q < m; ++q) {
+                const int kk = k + q;
+                mbar_wait_bounded(&bar[kk % STAGES], (kk / STAGES) & 1, kWaitLimitCycles);
+            }
+            if (threadIdx.x == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
+        }
+        if (!MULTI) break;
+
+        // grid barrier; the last CTA to arrive finishes the iteration
+        fence_proxy_async_global();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&st->arrive, 1u);
+            s_last = prev == (unsigned)G - 1u;
+            s_timeout = 0;
         }
         __syncthreads();
-
-        T *__restrict__ un = ubase + c * N;
-        const int x = x0 + 4 * lane;
-        float rs = 0.f, rc = 0.f;
-        const float *__restrict__ gphi = phi_all + c * N;
-        auto pl = [&](int ty, float *ph, float *la) {
-            float4 p4, l4;
-            if (PL_SMEM) {
-                p4 = *reinterpret_cast<const float4 *>(sphi + ty * kTW + 4 * lane);
-                l4 = *reinterpret_cast<const float4 *>(slam + ty * kTW + 4 * lane);
-            } else {
-                const int y = y0 + ty;
-                p4 = l4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (y < H && x < W) {
-                    p4 = __ldg(reinterpret_cast<const float4 *>(gphi + (size_t)y * W + x));
-                    l4 = __ldg(reinterpret_cast<const float4 *>(glam + (size_t)y * W + x));
+        if (s_last) {
+            finish_iteration(d, st);
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release_gpu(&st->gen, gen + 1u);
+            }
+        } else if (threadIdx.x == 0) {
+            const long long t0 = clock64();
+            while (ld_acquire_gpu(&st->gen) == gen) {
+                if (clock64() - t0 > kWaitLimitCycles) {
+                    s_timeout = 1;
+                    break;
                 }
-            }
-            ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
-            la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
-        };
-        auto sink = [&](int ty, const float *nu, const float *F) {
-            const int y = y0 + ty;
-            if (y >= H || x >= W) return;  // W % 4 == 0: x < W covers all 4 columns
-            float q = 0.f;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) q = fmaf(F[j], F[j], q);
-            neumaier_add(rs, rc, q);
-            Store<T>::write4(un + (size_t)y * W + x, nu[0], nu[1], nu[2], nu[3]);
-        };
-        walk_rows<R, SW, T, EDGE>(s, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
-
-        const float2 tot = block_pair_sum<NW>(rs, rc, red);  // ends with a barrier
-        if (threadIdx.x == 0) {
-            part[(size_t)c * nblk + tile] = tot;
-            const int nxt = item + STAGES * G;
-            if (nxt < nitems) {
-                fence_proxy_async_smem();
-                issue(nxt, stage);
+                __nanosleep(32);
             }
         }
-        __syncthreads();  // red[] reuse
-    }
-    if (failed) {
-        // let every load already issued land (bounded) before the CTA exits
-        for (int j = 0; j < STAGES; ++j) {
-            const int kk = k + j;
-            if (blockIdx.x + kk * G < nitems)
-                mbar_wait_bounded(&bar[kk % STAGES], (kk / STAGES) & 1, kWaitLimitCycles);
+        ++gen;
+        __syncthreads();
+        if (s_timeout) {  // another CTA never arrived: give up, report
+            if (threadIdx.x == 0) {
+                atomicCAS(&st->err, 0, DH_ETIMEOUT);
+                st->status = DH_ETIMEOUT;
+                st->done = 1;
+            }
+            return;
         }
-        if (threadIdx.x == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
+        if (__ldcg(&st->done) || failed) return;
     }
-    arrive_and_finish(d, st, &s_last);
+    if (!MULTI) arrive_and_finish(d, st, &s_last);
 }
 
 // Streaming sweep (W % 4 == 0, 16-byte aligned planes).  Each warp owns
@@ -473,8 +547,9 @@ k_sweep_stream(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant_
 // iteration state (n, history) carries over into the next precision phase.
 __global__ void k_set_desc(SolveDesc *dst, SolveDesc v, int reset) {
     *dst = v;
-    if (!reset) return;
     SolveState *st = v.st;
+    st->depth = v.depth;
+    if (!reset) return;
     st->arrive = 0;
     st->n = 0;
     st->cur = 0;
@@ -536,8 +611,13 @@ struct SweepCfg {
     int R, NW, stages, tma;  // tma: 0 generic, 1 TMA (u, Phi, lambda), 2 TMA (u) + vector loads, 3 streams
     bool edge;
     int minb = 0;            // resident CTAs per SM the registers must allow (0: 16 warps' worth)
+    int multi = 0;           // 1: cooperative launch of kItersPerLaunch iterations (tma == 1 only)
     int th() const { return R * NW; }
 };
+
+// Iterations one launch of a multi-iteration sweep runs at most; the graph's
+// while loop relaunches it until the stop rule holds.
+constexpr int kItersPerLaunch = 64;
 
 constexpr int kMinTileH = 16;  // smallest tile height any variant uses
 
@@ -561,14 +641,21 @@ static SweepFn sweep_fn(int R, int NW, bool edge) {
 }
 
 template <class T>
-static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge, int minb) {
-#define DH_STM(r, nw, st, pls, mb)                                                                  \
-    if (R == r && NW == nw && stages == st && tma == (pls ? 1 : 2) && minb == mb)                    \
-        return edge ? (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, true, mb>                          \
-                    : (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, false, mb>;
+static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge, int minb, int multi) {
+#define DH_STX(r, nw, st, pls, mb, mu)                                                              \
+    if (R == r && NW == nw && stages == st && tma == (pls ? 1 : 2) && minb == mb && multi == mu)     \
+        return edge ? (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, true, mb, mu>                      \
+                    : (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, false, mb, mu>;
+#define DH_STM(r, nw, st, pls, mb) DH_STX(r, nw, st, pls, mb, false)
 #define DH_ST(r, nw, st, pls) DH_STM(r, nw, st, pls, 0)
     DH_ST(8, 4, 1, true)
     if (sizeof(T) == 4) {
+        DH_STX(8, 4, 1, true, 0, true)
+        DH_STX(6, 4, 1, true, 5, true)
+        DH_STX(4, 4, 1, true, 6, true)
+        DH_STX(6, 4, 1, true, 0, true)
+        DH_STX(4, 4, 2, true, 0, true)
+        DH_ST(4, 4, 2, true)
         DH_ST(6, 4, 1, true)
         DH_ST(4, 4, 1, true)
         DH_ST(16, 2, 1, true)
@@ -588,6 +675,8 @@ static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge, in
         DH_ST(16, 2, 2, false)
     }
 #undef DH_ST
+#undef DH_STM
+#undef DH_STX
     return nullptr;
 }
 
@@ -644,6 +733,10 @@ static const SweepCfg kVariants[] = {
     {8, 8, 1, 0, true},
     {6, 4, 1, 1, true},  {4, 4, 1, 1, true},  {16, 2, 1, 1, true}, {12, 2, 1, 1, true},
     {8, 4, 1, 1, true, 5}, {6, 4, 1, 1, true, 5}, {4, 4, 1, 1, true, 6},
+    // 25-28: multi-iteration cooperative launches
+    {8, 4, 1, 1, true, 0, 1}, {6, 4, 1, 1, true, 5, 1}, {4, 4, 1, 1, true, 6, 1}, {6, 4, 1, 1, true, 0, 1},
+    // 29-30: 16-row tiles, two stages (the next item's tiles land while this one is computed)
+    {4, 4, 2, 1, true}, {4, 4, 2, 1, true, 0, 1},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -697,14 +790,15 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
         c.edge = edge;
         return c;
     }
-    if (const char *e = std::getenv("DH_SWEEP")) {
-        int r, nw, st, t;
-        if (std::sscanf(e, "%d,%d,%d,%d", &r, &nw, &st, &t) == 4) {
+    if (const char *e = std::getenv("DH_SWEEP")) {  // "R,NW,STAGES,TMA[,MULTI]"
+        int r, nw, st, t, mu = 0;
+        if (std::sscanf(e, "%d,%d,%d,%d,%d", &r, &nw, &st, &t, &mu) >= 4) {
             c.R = r;
             c.NW = nw;
             c.stages = st;
             c.tma = tma_ok ? t : 0;
             if (c.tma == 3 && p->boundary == DH_BOUNDARY_ZERO) c.tma = 1;
+            c.multi = c.tma == 1 ? (mu != 0) : 0;
         }
     }
     if (!c.tma && !sweep_fn<float>(c.R, c.NW, c.edge)) { c.R = 8; c.NW = 4; }
@@ -753,11 +847,11 @@ struct GraphKey {
     int dev;
     const void *desc;
     const void *ptrs[4];
-    int H, W, R, NW, stages, tma, edge, storage, minb;
+    int H, W, R, NW, stages, tma, edge, storage, minb, multi;
     bool operator==(const GraphKey &o) const {
         return dev == o.dev && desc == o.desc && std::memcmp(ptrs, o.ptrs, sizeof(ptrs)) == 0 && H == o.H &&
                W == o.W && R == o.R && NW == o.NW && stages == o.stages && tma == o.tma && edge == o.edge &&
-               storage == o.storage && minb == o.minb;
+               storage == o.storage && minb == o.minb && multi == o.multi;
     }
 };
 
@@ -778,6 +872,7 @@ struct LaunchSpec {
     dim3 grid, block;
     unsigned smem;
     void **args;
+    int coop = 0;  // cooperative launch (all CTAs resident at once)
 };
 
 // A graph holding one while node whose body is the sweep kernel; the sweep's
@@ -813,6 +908,11 @@ static int get_loop_graph(const GraphKey &key, const LaunchSpec &ls, GraphEntry 
         kp.kernelParams = ls.args;
         cudaGraphNode_t kn;
         err = cudaGraphAddKernelNode(&kn, body, nullptr, 0, &kp);
+        if (err == cudaSuccess && ls.coop) {
+            cudaLaunchAttributeValue av = {};
+            av.cooperative = 1;
+            err = cudaGraphKernelNodeSetAttribute(kn, cudaLaunchAttributeCooperative, &av);
+        }
     }
     cudaGraphExec_t exec = nullptr;
     if (err == cudaSuccess) err = cudaGraphInstantiate(&exec, g, 0);
@@ -903,13 +1003,17 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
         if (!rc) rc = encode_f32_map(&maps[2], v.phi, 3, W, H, 3, kTW, TH);
         if (!rc) rc = encode_f32_map(&maps[3], v.lam, 2, W, H, 1, kTW, TH);
         if (rc) return rc;
-        SweepTmaFn fn = sweep_tma_fn<T>(cfg.R, cfg.NW, cfg.stages, cfg.tma, cfg.edge, cfg.minb);
+        SweepTmaFn fn = sweep_tma_fn<T>(cfg.R, cfg.NW, cfg.stages, cfg.tma, cfg.edge, cfg.minb, cfg.multi);
         if (!fn) return DH_EINVAL;
         const unsigned smem = tma_smem_bytes(TH, cfg.stages, cfg.tma, esize);
         const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
         if (gmax <= 0) return DH_ECUDA;
         const int items = 3 * v.nblk;
         ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(cfg.NW * 32), smem, args_tma};
+        if (cfg.multi) {
+            ls.coop = 1;
+            v.depth = kItersPerLaunch;
+        }
     } else {
         const int TH = cfg.th();
         if (TH < kMinTileH) return DH_EINVAL;
@@ -924,7 +1028,7 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
         int dev = 0;
         DH_CUDA_TRY(cudaGetDevice(&dev));
         GraphKey key{dev, desc_dev, {v.u[0], v.u[1], v.phi, v.lam}, H, W, cfg.R, cfg.NW, cfg.stages, cfg.tma,
-                     cfg.edge ? 1 : 0, v.storage, cfg.minb};
+                     cfg.edge ? 1 : 0, v.storage, cfg.minb, cfg.multi};
         GraphEntry ge;
         int rc = get_loop_graph(key, ls, &ge);
         if (rc != DH_OK) return rc;
@@ -936,9 +1040,15 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
     } else {
         v.use_cond = 0;
         k_set_desc<<<1, 1, 0, s>>>(desc_dev, v, reset ? 1 : 0);
-        for (int n = 0; n <= p->max_iter; ++n)
-            DH_CUDA_TRY(cudaLaunchKernel(ls.func, ls.grid, ls.block, ls.args, ls.smem, s));
-        if (launches) *launches += p->max_iter + 1;  // queued; finished ones exit at once
+        // every launch runs v.depth sweeps at most; finished ones exit at once
+        const int nl = (p->max_iter + 1 + v.depth - 1) / v.depth;
+        for (int n = 0; n < nl; ++n) {
+            if (ls.coop)
+                DH_CUDA_TRY(cudaLaunchCooperativeKernel(ls.func, ls.grid, ls.block, ls.args, ls.smem, s));
+            else
+                DH_CUDA_TRY(cudaLaunchKernel(ls.func, ls.grid, ls.block, ls.args, ls.smem, s));
+        }
+        if (launches) *launches += nl;
     }
     if (launches) *launches += 1;  // k_set_desc
     return DH_OK;

@@ -47,24 +47,46 @@ __device__ __forceinline__ float gauss5(float vm2, float vm1, float v0, float vp
 __device__ __forceinline__ int ld_state_int(const int *p) { return __ldcg(p); }
 
 // Reduces the per-tile partials of the launch (last CTA only), decides whether
-// to stop, advances the state and sets the graph's while condition.
+// to stop, advances the state and sets the graph's while condition.  Every
+// thread of the CTA keeps 8 partial loads per channel in flight; the sums are
+// merged in a fixed order (thread stride, then lanes, then warps).
 static __device__ void finish_iteration(const SolveDesc *d, SolveState *st) {
+    constexpr int U = 8;
+    __shared__ float2 wsum[3][32];
     __shared__ float sq[3];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, nt = blockDim.x, w = tid >> 5, lane = tid & 31, nw = nt >> 5;
     __threadfence();
-    for (int ch = w; ch < 3; ch += blockDim.x >> 5) {
-        float s = 0.f, cc = 0.f;
-        const float2 *part = d->part + (size_t)ch * d->nblk;
-        for (int b = lane; b < d->nblk; b += 32) {
-            const float2 p = __ldcg(part + b);
-            neumaier_merge(s, cc, p.x, p.y);
-        }
+    const int nblk = d->nblk;
+    const float2 *part = d->part;
+    float s[3] = {0.f, 0.f, 0.f}, cc[3] = {0.f, 0.f, 0.f};
+    for (int b0 = tid; b0 < nblk; b0 += U * nt) {
+        float2 p[3][U];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int b = b0 + j * nt;
+                p[c][j] = b < nblk ? __ldcg(part + (size_t)c * nblk + b) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < U; ++j) neumaier_merge(s[c], cc[c], p[c][j].x, p[c][j].y);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
         for (int off = 16; off; off >>= 1) {
-            const float s2 = __shfl_down_sync(0xffffffffu, s, off);
-            const float c2 = __shfl_down_sync(0xffffffffu, cc, off);
-            neumaier_merge(s, cc, s2, c2);
+            const float s2 = __shfl_down_sync(0xffffffffu, s[c], off);
+            const float c2 = __shfl_down_sync(0xffffffffu, cc[c], off);
+            neumaier_merge(s[c], cc[c], s2, c2);
         }
-        if (lane == 0) sq[ch] = s + cc;
+        if (lane == 0) wsum[c][w] = make_float2(s[c], cc[c]);
+    }
+    __syncthreads();
+    if (tid < 3) {
+        float a = wsum[tid][0].x, b = wsum[tid][0].y;
+        for (int k = 1; k < nw; ++k) neumaier_merge(a, b, wsum[tid][k].x, wsum[tid][k].y);
+        sq[tid] = a + b;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;

@@ -21,6 +21,7 @@ def main():
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--storage", type=int, default=0, help="0 f32, 1 bf16, 2 f16, 3 bf16->f32, 4 f16->f32")
     ap.add_argument("--tol", type=float, default=0.0)
+    ap.add_argument("--variant", type=int, default=0, help="sweep variant (0: library default)")
     ap.add_argument("--net", type=int, default=0, help="instead: N images through the warm-start network forward")
     ap.add_argument("--host-loop", action="store_true",
                     help="queue the sweeps from the host instead of the graph loop (profilers cannot "
@@ -40,7 +41,7 @@ def main():
         return
     I = torch.from_numpy(scenes.hazy_scene(a.seed, a.H, a.W)["I"]).cuda()
     d = api.Dehazer(a.H, a.W, api.params(a.preset, tol=a.tol, max_iter=a.iters, storage=a.storage,
-                                                   use_graph=0 if a.host_loop else 1))
+                                                   use_graph=0 if a.host_loop else 1, sweep_variant=a.variant))
     for _ in range(a.repeat):
         rep = d(I)
     torch.cuda.synchronize()
