@@ -87,6 +87,7 @@ def lib():
             L.or_F.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrParams), P]
             L.or_div.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P]
             L.or_gauss.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P]
+            L.or_faces.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P]
             L.or_solve.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrParams),
                                    ctypes.c_int, ctypes.c_double, P]
             L.or_solve.restype = ctypes.c_int
@@ -174,6 +175,17 @@ def gauss(u, sigma=2.0, radius=2, boundary=0) -> np.ndarray:
     out = np.empty_like(u)
     lib().or_gauss(_ptr(u), H, W, sigma, radius, boundary, _ptr(out))
     return out
+
+
+def faces(u, eps, boundary=0, no_edge=False):
+    """Face coefficients D of u (one channel HxW): Dx (H, W+1) on the x-faces
+    i-1/2 .. W-1/2, Dy (H+1, W) on the y-faces j-1/2 .. H-1/2."""
+    u = _f64(u)
+    H, W = u.shape
+    Dx = np.empty((H, W + 1))
+    Dy = np.empty((H + 1, W))
+    lib().or_faces(_ptr(u), H, W, eps, boundary, int(no_edge), _ptr(Dx), _ptr(Dy))
+    return Dx, Dy
 
 
 def solve(u0, Phi, lam, p: OrParams, max_iter: int, tol: float):

@@ -162,22 +162,41 @@ void or_gauss(const double *u, int H, int W, double sigma, int radius, int bound
 
 /* ------------------------------------------------------------- App. A-B-1 */
 
-/* D u_x on the x-face (i+1/2, j): forward difference in x, central difference
- * in y at cell (i, j), D = (|grad u| + eps)^-1, Delta x = Delta y = 1
- * (D == 1 for the "w/o edge-preserving term" ablation). */
-static double flux_x(const double *u, int H, int W, long i, long j, double eps, int bnd, int no_edge) {
-    const double ux = U(u, H, W, i + 1, j, bnd) - U(u, H, W, i, j, bnd);
+/* D on the x-face (i+1/2, j): forward difference in x, central difference in
+ * y at cell (i, j), D = (|grad u| + eps)^-1, Delta x = Delta y = 1 (D == 1
+ * for the "w/o edge-preserving term" ablation); *ux receives the difference
+ * across the face. */
+static double coef_x(const double *u, int H, int W, long i, long j, double eps, int bnd, int no_edge, double *ux) {
+    *ux = U(u, H, W, i + 1, j, bnd) - U(u, H, W, i, j, bnd);
     const double uy = (U(u, H, W, i, j + 1, bnd) - U(u, H, W, i, j - 1, bnd)) / 2.0;
-    const double D = no_edge ? 1.0 : 1.0 / (sqrt(ux * ux + uy * uy) + eps);
-    return D * ux;
+    return no_edge ? 1.0 : 1.0 / (sqrt(*ux * *ux + uy * uy) + eps);
 }
 
-/* D u_y on the y-face (i, j+1/2): the same with the roles of x and y swapped. */
-static double flux_y(const double *u, int H, int W, long i, long j, double eps, int bnd, int no_edge) {
-    const double uy = U(u, H, W, i, j + 1, bnd) - U(u, H, W, i, j, bnd);
+/* The y-face (i, j+1/2): the same with the roles of x and y swapped. */
+static double coef_y(const double *u, int H, int W, long i, long j, double eps, int bnd, int no_edge, double *uy) {
+    *uy = U(u, H, W, i, j + 1, bnd) - U(u, H, W, i, j, bnd);
     const double ux = (U(u, H, W, i + 1, j, bnd) - U(u, H, W, i - 1, j, bnd)) / 2.0;
-    const double D = no_edge ? 1.0 : 1.0 / (sqrt(ux * ux + uy * uy) + eps);
+    return no_edge ? 1.0 : 1.0 / (sqrt(ux * ux + *uy * *uy) + eps);
+}
+
+/* D u_x on the x-face (i+1/2, j) and D u_y on the y-face (i, j+1/2). */
+static double flux_x(const double *u, int H, int W, long i, long j, double eps, int bnd, int no_edge) {
+    double ux;
+    const double D = coef_x(u, H, W, i, j, eps, bnd, no_edge, &ux);
+    return D * ux;
+}
+static double flux_y(const double *u, int H, int W, long i, long j, double eps, int bnd, int no_edge) {
+    double uy;
+    const double D = coef_y(u, H, W, i, j, eps, bnd, no_edge, &uy);
     return D * uy;
+}
+
+void or_faces(const double *u, int H, int W, double eps, int boundary, int no_edge, double *Dx, double *Dy) {
+    double d;
+    for (int j = 0; j < H; ++j)
+        for (int i = -1; i < W; ++i) Dx[(long)j * (W + 1) + i + 1] = coef_x(u, H, W, i, j, eps, boundary, no_edge, &d);
+    for (int j = -1; j < H; ++j)
+        for (int i = 0; i < W; ++i) Dy[(long)(j + 1) * W + i] = coef_y(u, H, W, i, j, eps, boundary, no_edge, &d);
 }
 
 void or_div(const double *u, int H, int W, double eps, int boundary, int no_edge, double *out) {

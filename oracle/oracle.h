@@ -24,6 +24,7 @@
  *                          Newton root, uniqueness, resume)
  *   boundary = 1 / variant  pinned (scipy zero-padded gaussian_filter and laplace;
  *                          D == 1 is the 5-point Laplacian; lambda ablations)
+ *   or_faces               pinned (the frozen operator applied to u equals -or_div(u))
  */
 #ifndef DEHAZE_ORACLE_H
 #define DEHAZE_ORACLE_H
@@ -77,6 +78,13 @@ void or_F(const double *u, const double *Phi, const double *lam, int H, int W,
 /* The diffusion term alone, div(D grad u), one channel (HxW); boundary as in
  * or_params; no_edge: D == 1. */
 void or_div(const double *u, int H, int W, double eps, int boundary, int no_edge, double *out);
+
+/* The face coefficients of the diffusion term frozen at u (one channel), for
+ * the semi-implicit scheme: D = (|grad u| + eps)^-1 (1 for no_edge) with the
+ * same differences as or_div.  x-faces (i+1/2, j), i = -1..W-1, at
+ * Dx[j*(W+1) + i+1]; y-faces (i, j+1/2), j = -1..H-1, at Dy[(j+1)*W + i].
+ * Border faces are included; what they couple to is the boundary rule's. */
+void or_faces(const double *u, int H, int W, double eps, int boundary, int no_edge, double *Dx, double *Dy);
 
 /* The Gaussian term alone, G(u), one channel (HxW). */
 void or_gauss(const double *u, int H, int W, double sigma, int radius, int boundary, double *out);
