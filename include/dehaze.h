@@ -285,6 +285,40 @@ int dh_dehaze_warm(const float *params, int base, const float *I, int H, int W, 
 int dh_atmospheric_light_noalloc(const float *I, const float *dc, int H, int W, int topk_permille,
                                  float *A_out, long long *index_out, void *stream);
 
+/* ---------------------------------------------------------------- semi-implicit scheme
+ * The explicit iteration of App. A-A is stable only for tau < 2/(||D Delta|| +
+ * lambda M), and ||D Delta|| grows like 8/eps (App. A-A): at the paper's
+ * eps = 1e-3 no usable tau exists.  dh_semi_implicit solves the same equation
+ * (Sec. II: -div(D grad u) + lambda G(u) = Phi) by the lagged-diffusivity
+ * scheme: each outer step freezes the face coefficients D of App. A-B-1 at
+ * u^n and solves (I/step + L_n) u^{n+1} = u^n/step - lambda G(u^n) + Phi,
+ * L_n v = -div(D(u^n) grad v), with cg_iters Jacobi-preconditioned
+ * conjugate-gradient iterations per channel started from u^n.  The paper has
+ * no such scheme; its fixed point is the explicit scheme's.
+ *
+ * Workspace: dh_semi_implicit_workspace_bytes(H, W) bytes, 256-byte aligned
+ * (about 108 B per pixel), owned by the caller; the call allocates nothing. */
+size_t dh_semi_implicit_workspace_bytes(int H, int W);
+
+/* u: 3xHxW float32 device, holds u^0 on entry and u^n on return (in place).
+ * The iterate is kept as a double-float pair u + u_lo: at eps = 1e-3 the face
+ * coefficients reach 1/eps, and a float32 iterate alone would leave F(u) a
+ * rounding floor of about ulp(u)/eps (rho ~ 3e-4 on typical scenes).  u_lo
+ * (3xHxW, may be NULL) is the trailing part, in and out (NULL: zero on entry,
+ * kept in the workspace); u alone is u^n rounded to float32.
+ * Phi: 3xHxW, lam: HxW (from dh_transmission).  p: eps, sigma, tol, max_iter,
+ * boundary and variant (DH_VAR_NO_EDGE) are used; storage must be
+ * DH_STORE_F32.  step: the outer step s > 0 (stable for s * lambda < 2; 2.0
+ * is a good default).  The residual, stop rule, n and rho_hist are those of
+ * dh_fixed_point: rho_n = ||F(u^n)|| / ||Phi||, F the residual of App. A-A.
+ * J (3xHxW, may be NULL) receives clamp(u^n, 0, 1).  One cooperative launch runs the whole solve on `stream`; report (may be
+ * NULL; when given the call synchronises the stream) as for dh_fixed_point.
+ * Returns DH_OK / DH_WNOCONV / DH_ENONFINITE / DH_ETIMEOUT, or DH_EINVAL,
+ * DH_EWORKSPACE, DH_ECUDA before any work is queued. */
+int dh_semi_implicit(float *u, float *u_lo, const float *Phi, const float *lam, int H, int W, const dh_params *p,
+                     float step, int cg_iters, float *rho_hist, float *J, void *workspace, size_t workspace_bytes,
+                     void *stream, dh_report *report);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,8 @@ EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes
            "dh_tune_set", "dh_tune_get", "dh_unet_param_count", "dh_unet_workspace_bytes", "dh_unet_init",
            "dh_unet_forward", "dh_unet_backward", "dh_unet_adam", "dh_warm_start", "dh_warm_target",
            "dh_conv3x3_forward",
-           "dh_conv3x3_backward_weights", "dh_dehaze_warm", "dh_atmospheric_light_noalloc")
+           "dh_conv3x3_backward_weights", "dh_dehaze_warm", "dh_atmospheric_light_noalloc",
+           "dh_semi_implicit_workspace_bytes", "dh_semi_implicit")
 
 
 class DhParams(ctypes.Structure):
@@ -153,6 +154,8 @@ def lib(build_if_missing: bool = True):
             "dh_conv3x3_forward": ([P, I, I, I, I, I, P, P, I, I, P, I, P], I),
             "dh_conv3x3_backward_weights": ([P, I, I, P, I, I, I, I, I, P, P, P, S, P], I),
             "dh_dehaze_warm": ([P, I, P, I, I, PP, P, P, P, P, P, S, P, S, P, PR], I),
+            "dh_semi_implicit_workspace_bytes": ([I, I], S),
+            "dh_semi_implicit": ([P, P, P, P, I, I, PP, ctypes.c_float, I, P, P, P, S, P, PR], I),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -222,6 +225,17 @@ def dh_fixed_point(u, Phi, lam, H, W, p: DhParams, rho_hist, workspace, workspac
                    report: DhReport | None = None) -> int:
     return lib().dh_fixed_point(_p(u), _p(Phi), _p(lam), H, W, ctypes.byref(p), _p(rho_hist),
                                 _p(workspace), workspace_bytes, _stream(stream), _ref(report))
+
+
+def dh_semi_implicit_workspace_bytes(H: int, W: int) -> int:
+    return lib().dh_semi_implicit_workspace_bytes(H, W)
+
+
+def dh_semi_implicit(u, u_lo, Phi, lam, H, W, p: DhParams, step, cg_iters, rho_hist, J, workspace,
+                     workspace_bytes, stream=None, report: DhReport | None = None) -> int:
+    return lib().dh_semi_implicit(_p(u), _p(u_lo), _p(Phi), _p(lam), H, W, ctypes.byref(p), float(step),
+                                  int(cg_iters), _p(rho_hist), _p(J), _p(workspace), workspace_bytes,
+                                  _stream(stream), _ref(report))
 
 
 def dh_dehaze(I, H, W, p: DhParams, u0, J, u, t, A, workspace, workspace_bytes, stream=None,

@@ -93,6 +93,36 @@ def fixed_point(u: torch.Tensor, Phi: torch.Tensor, lam: torch.Tensor, p: DhPara
     return rep, hist
 
 
+def semi_implicit(u: torch.Tensor, Phi: torch.Tensor, lam: torch.Tensor, p: DhParams | None = None,
+                  step: float = 2.0, cg_iters: int = 32, history: bool = False, J: torch.Tensor | None = None,
+                  u_lo: torch.Tensor | None = None, stream=None):
+    """The semi-implicit (lagged-diffusivity) scheme in place on u from u^0
+    (J, if given, receives clamp(u, 0, 1); u_lo, if given, is the trailing
+    float32 part of the double-float iterate, in and out); returns (report,
+    rho_hist or None).  Converges at the paper's eps = 1e-3."""
+    H, W = _img(u)
+    p = p or params("paper")
+    ws = torch.empty(N.dh_semi_implicit_workspace_bytes(H, W), dtype=torch.uint8, device=u.device)
+    hist = torch.full((p.max_iter + 1, 3), float("nan"), device=u.device) if history else None
+    rep = DhReport()
+    _check(N.dh_semi_implicit(u, u_lo, Phi, lam, H, W, p, step, cg_iters, hist, J, ws, ws.numel(),
+                              _stream(stream), rep), "dh_semi_implicit")
+    return rep, hist
+
+
+def dehaze_semi_implicit(I: torch.Tensor, p: DhParams | None = None, step: float = 2.0, cg_iters: int = 32):
+    """The whole method with the semi-implicit solver: dark channel, A, t,
+    lambda, Phi, then the scheme from u^0 = Phi.  Returns a dict like dehaze()."""
+    p = p or params("paper")
+    dc = dark_channel(I, p.patch)
+    A, idx, _ = atmospheric_light(I, dc, p.topk_permille)
+    _, t, lam, Phi = transmission(I, A, p)
+    u = Phi.clone()
+    J = torch.empty_like(u)
+    rep, _ = semi_implicit(u, Phi, lam, p, step, cg_iters, J=J)
+    return {"J": J, "u": u, "t": t, "A": A, "report": rep}
+
+
 class Dehazer:
     """The whole method for images of one shape, with the workspace and the
     outputs kept resident so that repeated calls reuse the cached loop graph."""

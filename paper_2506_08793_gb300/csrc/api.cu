@@ -26,6 +26,11 @@ bool sweep_variant_usable(int v, int W, bool aligned);
 void tune_set(int dev, int H, int W, int storage, int variant);
 int tune_get(int dev, int H, int W, int storage);
 
+size_t semi_workspace_bytes(int H, int W);
+int run_semi_implicit(float *u, float *u_lo, const float *Phi, const float *lam, int H, int W, const dh_params *p,
+                      float step, int cg_iters, float *rho_hist, float *J, void *workspace, cudaStream_t s);
+int read_semi_implicit(const void *workspace, cudaStream_t s, int *n_final, int *status, float rho[3]);
+
 int cuda_fail(cudaError_t) {
     cudaGetLastError();  // clear a non-sticky error so the next call starts clean
     return DH_ECUDA;
@@ -346,6 +351,41 @@ int dh_tune(const float *Phi, const float *lam, float *u_scratch, int H, int W, 
     if (res.best > 0) tune_set(dev, H, W, DH_STORE_F32, res.best);
     if (out) *out = res;
     return DH_OK;
+}
+
+size_t dh_semi_implicit_workspace_bytes(int H, int W) {
+    if (!shape_ok(H, W)) return 0;
+    return semi_workspace_bytes(H, W);
+}
+
+int dh_semi_implicit(float *u, float *u_lo, const float *Phi, const float *lam, int H, int W, const dh_params *p,
+                     float step, int cg_iters, float *rho_hist, float *J, void *workspace, size_t workspace_bytes,
+                     void *stream, dh_report *report) {
+    if (!u || !Phi || !lam || !shape_ok(H, W) || !params_ok(p)) return DH_EINVAL;
+    if (!(step > 0.f) || !std::isfinite(step) || cg_iters < 1 || cg_iters > 10000) return DH_EINVAL;
+    if (p->storage != DH_STORE_F32) return DH_EINVAL;
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < semi_workspace_bytes(H, W))
+        return DH_EWORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    Timer tm;
+    tm.start(s, report != nullptr);
+    cudaEvent_t lb = tm.loop_begin();
+    if (lb) DH_CUDA_TRY(cudaEventRecord(lb, s));
+    int rc = run_semi_implicit(u, u_lo, Phi, lam, H, W, p, step, cg_iters, rho_hist, J, workspace, s);
+    if (rc || !report) return rc;
+    if (tm.loop_end()) DH_CUDA_TRY(cudaEventRecord(tm.loop_end(), s));
+    std::memset(report, 0, sizeof(*report));
+    tm.stop(s, &report->ms, &report->ms_loop);
+    int n_final = 0, status = 0;
+    float rho[3] = {0.f, 0.f, 0.f};
+    rc = read_semi_implicit(workspace, s, &n_final, &status, rho);
+    if (rc) return rc;
+    report->status = status;
+    report->n_iter = n_final;
+    for (int c = 0; c < 3; ++c) report->rho[c] = rho[c];
+    report->a_index = -1;
+    report->launches = J ? 3 : 2;  // state reset + the cooperative solve (+ J)
+    return report->status;
 }
 
 }  // extern "C"

@@ -1,0 +1,530 @@
+// Semi-implicit (lagged-diffusivity) fixed-point scheme for
+// -div(D(grad u) grad u) + lambda G(u) = Phi (Sec. II, App. A).
+//
+// The explicit iteration of App. A-A needs tau < 2/(||D Delta|| + lambda M)
+// with ||D Delta|| up to 8/eps, so the paper's eps = 1e-3 leaves no usable
+// tau.  Here each outer step freezes the face coefficients D at u^n and takes
+// the diffusion implicitly, the nonlocal term explicitly:
+//
+//     (I/s + L_n) u^{n+1} = u^n/s - lambda G(u^n) + Phi,
+//     (L_n v)_i = sum over the faces f of pixel i of D_f(u^n) (v_i - v_nb(f)),
+//
+// v_nb extended by the boundary rule (reflecting: border faces drop out;
+// Dirichlet: the ghost is 0).  I/s + L_n is symmetric positive definite; it is
+// solved per channel by cg_iters Jacobi-preconditioned conjugate-gradient
+// iterations started from u^n, whose initial residual is exactly F(u^n) of
+// App. A-A, so rho_n = ||F(u^n)|| / ||Phi|| and the stop rule are the
+// explicit solver's.  A fixed point of the outer iteration solves the PDE
+// whatever the inner accuracy.
+//
+// One cooperative launch runs the whole solve: grid-stride passes over the
+// 3 x H x W elements separated by grid barriers (the last CTA to arrive
+// reduces the per-CTA partial sums in a fixed order and updates the scalars).
+// Every array the launch writes is read through L2 (ld.global.cg).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace dh {
+
+namespace {
+
+constexpr int kSiThreads = 256;
+constexpr int kSiMaxGrid = 4096;
+constexpr long long kSiWaitCycles = 4000000000LL;  // about 2 s
+
+struct SiState {
+    unsigned arrive;
+    int n, done, status, n_final, err;
+    float rho[3], phin2[3], rz[3], alpha[3], beta[3];
+    alignas(128) unsigned gen;  // barrier generation, alone in its line
+    int pad[31];
+};
+
+struct SiDesc {
+    float *x;                  // u^n (in/out), 3 planes: the leading part of the iterate
+    float *xlo;                // its trailing part (u = x + xlo, a double-float pair)
+    const float *phi, *lam;
+    float *r, *z, *p[2], *q, *dg;
+    float *fx, *fy;            // faces: 3 x H x (W+1), 3 x (H+1) x W
+    float2 *part;              // [6][grid] per-CTA (sum, compensation)
+    SiState *st;
+    float *rho_hist;
+    int H, W, max_iter, cg_iters, dirichlet, no_edge, zero_lo;
+    float tol, inv_s, eps, wg0, wg1, wg2;
+};
+
+// Reflecting (scipy 'reflect') or Dirichlet extension of one plane.
+__device__ __forceinline__ float ext(const float *v, int H, int W, int i, int j, bool dir) {
+    if (i < 0 || i >= W || j < 0 || j >= H) {
+        if (dir) return 0.f;
+        i = reflect_idx(i, W);
+        j = reflect_idx(j, H);
+    }
+    return __ldcg(v + (size_t)j * W + i);
+}
+
+// The iterate is a double-float pair (hi, lo): at eps = 1e-3 the face
+// coefficients reach 1000, so a float32 u would put a rounding floor of about
+// 1000 ulp(u) on F(u), well above a 1e-4 residual.  Differences of pairs are
+// taken as (hi_a - hi_b) + (lo_a - lo_b): the first difference is exact for
+// neighbouring values (Sterbenz), so the gradient carries ~2^-44 relative error.
+struct Pair {
+    float hi, lo;
+};
+__device__ __forceinline__ Pair ext2(const float *hi, const float *lo, int H, int W, int i, int j, bool dir) {
+    if (i < 0 || i >= W || j < 0 || j >= H) {
+        if (dir) return {0.f, 0.f};
+        i = reflect_idx(i, W);
+        j = reflect_idx(j, H);
+    }
+    const size_t o = (size_t)j * W + i;
+    return {__ldcg(hi + o), __ldcg(lo + o)};
+}
+__device__ __forceinline__ float pdiff(Pair a, Pair b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+
+__device__ __forceinline__ float coef(float a, float b, float eps, bool no_edge) {
+    return no_edge ? 1.f : 1.f / (sqrtf(fmaf(a, a, b * b)) + eps);
+}
+
+// (A v)_i = v_i/s + sum_f D_f (v_i - v_nb); `get(i, j)` reads v inside the image.
+template <class Get>
+__device__ __forceinline__ float apply_A(const SiDesc &d, const float *fxc, const float *fyc, int x, int y,
+                                         float v0, Get get, float *diag) {
+    const int H = d.H, W = d.W;
+    const bool dir = d.dirichlet != 0;
+    float a = d.inv_s * v0, dg = d.inv_s;
+    const float Dl = __ldcg(fxc + (size_t)y * (W + 1) + x), Dr = __ldcg(fxc + (size_t)y * (W + 1) + x + 1);
+    const float Du = __ldcg(fyc + (size_t)y * W + x), Dd = __ldcg(fyc + (size_t)(y + 1) * W + x);
+    if (x > 0) { a = fmaf(Dl, v0 - get(x - 1, y), a); dg += Dl; } else if (dir) { a = fmaf(Dl, v0, a); dg += Dl; }
+    if (x < W - 1) { a = fmaf(Dr, v0 - get(x + 1, y), a); dg += Dr; } else if (dir) { a = fmaf(Dr, v0, a); dg += Dr; }
+    if (y > 0) { a = fmaf(Du, v0 - get(x, y - 1), a); dg += Du; } else if (dir) { a = fmaf(Du, v0, a); dg += Du; }
+    if (y < H - 1) { a = fmaf(Dd, v0 - get(x, y + 1), a); dg += Dd; } else if (dir) { a = fmaf(Dd, v0, a); dg += Dd; }
+    if (diag) *diag = dg;
+    return a;
+}
+
+// Per-CTA partial sums of nk quantities (k = quantity*3 + channel), written
+// to part[k][blockIdx.x]; deterministic order.
+template <int NK>
+__device__ void cta_partials(float (&s)[NK], float (&c)[NK], float2 *part) {
+    __shared__ float2 red[kSiThreads / 32][6];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        for (int off = 16; off; off >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s[k], off);
+            const float c2 = __shfl_down_sync(0xffffffffu, c[k], off);
+            neumaier_merge(s[k], c[k], s2, c2);
+        }
+        if (lane == 0) red[w][k] = make_float2(s[k], c[k]);
+    }
+    __syncthreads();
+    if (threadIdx.x < NK) {
+        const int k = threadIdx.x;
+        float a = red[0][k].x, b = red[0][k].y;
+        for (int q = 1; q < kSiThreads / 32; ++q) neumaier_merge(a, b, red[q][k].x, red[q][k].y);
+        part[(size_t)k * gridDim.x + blockIdx.x] = make_float2(a, b);
+    }
+}
+
+// Last CTA: out[k] = fixed-order sum of part[k][0..grid) for k < nk.
+__device__ void reduce_partials(const float2 *part, int nk, float *out) {
+    __shared__ float2 red[kSiThreads / 32][6];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, G = gridDim.x;
+    for (int k = 0; k < nk; ++k) {
+        float s = 0.f, c = 0.f;
+        for (int b = threadIdx.x; b < G; b += kSiThreads) {
+            const float2 v = __ldcg(part + (size_t)k * G + b);
+            neumaier_merge(s, c, v.x, v.y);
+        }
+        for (int off = 16; off; off >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s, off);
+            const float c2 = __shfl_down_sync(0xffffffffu, c, off);
+            neumaier_merge(s, c, s2, c2);
+        }
+        if (lane == 0) red[w][k] = make_float2(s, c);
+    }
+    __syncthreads();
+    if (threadIdx.x < nk) {
+        const int k = threadIdx.x;
+        float a = red[0][k].x, b = red[0][k].y;
+        for (int q = 1; q < kSiThreads / 32; ++q) neumaier_merge(a, b, red[q][k].x, red[q][k].y);
+        out[k] = a + b;
+    }
+    __syncthreads();
+}
+
+// Grid barrier.  The last CTA to arrive runs fin() with all its threads, then
+// releases the others; a wait longer than about 2 s records DH_ETIMEOUT and
+// returns false.
+template <class Fin>
+__device__ bool grid_barrier(SiState *st, unsigned &gen, Fin fin) {
+    __shared__ int s_last, s_to;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&st->arrive, 1u) == gridDim.x - 1u;
+        s_to = 0;
+    }
+    __syncthreads();
+    if (s_last) {
+        __threadfence();
+        fin();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st->arrive = 0;
+            __threadfence();
+            st_release_gpu(&st->gen, gen + 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        const long long t0 = clock64();
+        while (ld_acquire_gpu(&st->gen) == gen) {
+            if (clock64() - t0 > kSiWaitCycles) {
+                s_to = 1;
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    ++gen;
+    __syncthreads();
+    if (s_to) {
+        if (threadIdx.x == 0) {
+            atomicCAS(&st->err, 0, DH_ETIMEOUT);
+            st->status = DH_ETIMEOUT;
+            st->done = 1;
+        }
+        return false;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_constant__ SiDesc d) {
+    SiState *st = d.st;
+    const int H = d.H, W = d.W;
+    const int N = H * W, E = 3 * N;
+    const int G = gridDim.x, T = G * kSiThreads;
+    const int e0 = blockIdx.x * kSiThreads + threadIdx.x;
+    const bool dir = d.dirichlet != 0, ne = d.no_edge != 0;
+    __shared__ float sc[6];
+    unsigned gen = ld_acquire_gpu(&st->gen);
+
+    // ||Phi^c||^2
+    {
+        float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+        for (int e = e0; e < E; e += T) {
+            const int ch = e / N;
+            const float v = __ldg(d.phi + e);
+            neumaier_add(s[ch], c[ch], v * v);
+            if (d.zero_lo) d.xlo[e] = 0.f;
+        }
+        cta_partials<3>(s, c, d.part);
+        if (!grid_barrier(st, gen, [&] {
+                reduce_partials(d.part, 3, sc);
+                if (threadIdx.x < 3) st->phin2[threadIdx.x] = sc[threadIdx.x];
+            }))
+            return;
+    }
+
+    for (;;) {
+        // faces of u^n
+        for (int e = e0; e < E; e += T) {
+            const int ch = e / N, pix = e - ch * N, y = pix / W, x = pix - y * W;
+            const float *xc = d.x + (size_t)ch * N, *lc = d.xlo + (size_t)ch * N;
+            float *fxc = d.fx + (size_t)ch * H * (W + 1), *fyc = d.fy + (size_t)ch * (H + 1) * W;
+            auto U = [&](int i, int j) { return ext2(xc, lc, H, W, i, j, dir); };
+            const Pair u0 = U(x, y);
+            {  // x-face (x+1/2, y), tangential difference at cell x
+                const float a = pdiff(U(x + 1, y), u0);
+                const float b = 0.5f * pdiff(U(x, y + 1), U(x, y - 1));
+                fxc[(size_t)y * (W + 1) + x + 1] = coef(a, b, d.eps, ne);
+            }
+            if (x == 0) {  // x-face (-1/2, y): tangential difference at the ghost cell
+                const float a = pdiff(u0, U(-1, y));
+                const float b = 0.5f * pdiff(U(-1, y + 1), U(-1, y - 1));
+                fxc[(size_t)y * (W + 1)] = coef(a, b, d.eps, ne);
+            }
+            {  // y-face (x, y+1/2)
+                const float a = pdiff(U(x, y + 1), u0);
+                const float b = 0.5f * pdiff(U(x + 1, y), U(x - 1, y));
+                fyc[(size_t)(y + 1) * W + x] = coef(a, b, d.eps, ne);
+            }
+            if (y == 0) {
+                const float a = pdiff(u0, U(x, -1));
+                const float b = 0.5f * pdiff(U(x + 1, -1), U(x - 1, -1));
+                fyc[x] = coef(a, b, d.eps, ne);
+            }
+        }
+        if (!grid_barrier(st, gen, [] {})) return;
+
+        // r = F(u^n) = Phi - lambda G(u^n) - L_n u^n, z = r / diag, p = z
+        {
+            float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, c[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float wg[5] = {d.wg2, d.wg1, d.wg0, d.wg1, d.wg2};
+            for (int e = e0; e < E; e += T) {
+                const int ch = e / N, pix = e - ch * N, y = pix / W, x = pix - y * W;
+                const float *xc = d.x + (size_t)ch * N, *lc = d.xlo + (size_t)ch * N;
+                const float *fxc = d.fx + (size_t)ch * H * (W + 1), *fyc = d.fy + (size_t)ch * (H + 1) * W;
+                float g = 0.f;
+                for (int b = -2; b <= 2; ++b) {
+                    float h = 0.f;
+                    for (int a = -2; a <= 2; ++a) h = fmaf(wg[a + 2], ext(xc, H, W, x + a, y + b, dir), h);
+                    g = fmaf(wg[b + 2], h, g);
+                }
+                // L_n u^n = sum_f D_f (u_i - u_nb) with pair differences;
+                // diag = 1/s + the faces that couple (all four under Dirichlet)
+                const Pair u0 = ext2(xc, lc, H, W, x, y, dir);
+                const float Dl = __ldcg(fxc + (size_t)y * (W + 1) + x), Dr = __ldcg(fxc + (size_t)y * (W + 1) + x + 1);
+                const float Du = __ldcg(fyc + (size_t)y * W + x), Dd = __ldcg(fyc + (size_t)(y + 1) * W + x);
+                float Lu = 0.f, dg = d.inv_s;
+                if (x > 0 || dir) { Lu = fmaf(Dl, pdiff(u0, ext2(xc, lc, H, W, x - 1, y, dir)), Lu); dg += Dl; }
+                if (x < W - 1 || dir) { Lu = fmaf(Dr, pdiff(u0, ext2(xc, lc, H, W, x + 1, y, dir)), Lu); dg += Dr; }
+                if (y > 0 || dir) { Lu = fmaf(Du, pdiff(u0, ext2(xc, lc, H, W, x, y - 1, dir)), Lu); dg += Du; }
+                if (y < H - 1 || dir) { Lu = fmaf(Dd, pdiff(u0, ext2(xc, lc, H, W, x, y + 1, dir)), Lu); dg += Dd; }
+                const float r = __ldg(d.phi + e) - __ldg(d.lam + pix) * g - Lu;
+                const float z = r / dg;
+                d.r[e] = r;
+                d.z[e] = z;
+                d.p[0][e] = z;
+                d.dg[e] = dg;
+                neumaier_add(s[ch], c[ch], r * r);
+                neumaier_add(s[3 + ch], c[3 + ch], r * z);
+            }
+            cta_partials<6>(s, c, d.part);
+        }
+        if (!grid_barrier(st, gen, [&] {
+                reduce_partials(d.part, 6, sc);
+                if (threadIdx.x != 0) return;
+                const int n = st->n;
+                float rho[3], worst = 0.f;
+                bool finite = true;
+                for (int ch = 0; ch < 3; ++ch) {
+                    const float pn = st->phin2[ch];
+                    rho[ch] = pn > 0.f ? sqrtf(sc[ch] / pn) : sqrtf(sc[ch]);
+                    if (!isfinite(rho[ch])) finite = false;
+                    else worst = fmaxf(worst, rho[ch]);
+                    if (d.rho_hist) d.rho_hist[3 * n + ch] = rho[ch];
+                    st->rz[ch] = sc[3 + ch];
+                }
+                const int err = st->err;
+                const bool conv = finite && worst <= d.tol;
+                if (err || conv || !finite || n >= d.max_iter) {
+                    st->done = 1;
+                    st->n_final = n;
+                    st->status = err ? err : (!finite ? DH_ENONFINITE : (conv ? DH_OK : DH_WNOCONV));
+                    for (int ch = 0; ch < 3; ++ch) st->rho[ch] = rho[ch];
+                }
+            }))
+            return;
+        if (__ldcg(&st->done)) return;
+
+        for (int k = 0; k < d.cg_iters; ++k) {
+            const float *pold = d.p[(k + 1) & 1];
+            float *pcur = d.p[k & 1];
+            // q = A p (p = z + beta p_old, formed where it is read), p.q
+            {
+                float beta[3];
+                for (int ch = 0; ch < 3; ++ch) beta[ch] = __ldcg(&st->beta[ch]);
+                float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+                for (int e = e0; e < E; e += T) {
+                    const int ch = e / N, pix = e - ch * N, y = pix / W, x = pix - y * W;
+                    const float *fxc = d.fx + (size_t)ch * H * (W + 1), *fyc = d.fy + (size_t)ch * (H + 1) * W;
+                    const size_t base = (size_t)ch * N;
+                    float pv, qv;
+                    if (k == 0) {
+                        const float *pc = pcur + base;
+                        pv = __ldcg(pc + pix);
+                        qv = apply_A(d, fxc, fyc, x, y, pv,
+                                     [&](int i, int j) { return __ldcg(pc + (size_t)j * W + i); }, nullptr);
+                    } else {
+                        const float *zc = d.z + base, *oc = pold + base;
+                        const float bt = beta[ch];
+                        auto get = [&](int i, int j) {
+                            const size_t o = (size_t)j * W + i;
+                            return fmaf(bt, __ldcg(oc + o), __ldcg(zc + o));
+                        };
+                        pv = get(x, y);
+                        pcur[e] = pv;
+                        qv = apply_A(d, fxc, fyc, x, y, pv, get, nullptr);
+                    }
+                    d.q[e] = qv;
+                    neumaier_add(s[ch], c[ch], pv * qv);
+                }
+                cta_partials<3>(s, c, d.part);
+            }
+            if (!grid_barrier(st, gen, [&] {
+                    reduce_partials(d.part, 3, sc);
+                    if (threadIdx.x < 3) {
+                        const int ch = threadIdx.x;
+                        const float pq = sc[ch];
+                        st->alpha[ch] = pq > 0.f ? st->rz[ch] / pq : 0.f;
+                    }
+                }))
+                return;
+            // x += alpha p, r -= alpha q, z = r / diag, r.z
+            {
+                float alpha[3];
+                for (int ch = 0; ch < 3; ++ch) alpha[ch] = __ldcg(&st->alpha[ch]);
+                float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
+                for (int e = e0; e < E; e += T) {
+                    const int ch = e / N;
+                    const float al = alpha[ch];
+                    {  // (hi, lo) += alpha p: two-sum, then renormalise
+                        const float hi = __ldcg(d.x + e), dlt = al * __ldcg(pcur + e);
+                        const float s1 = hi + dlt, bb = s1 - hi;
+                        const float err = (hi - (s1 - bb)) + (dlt - bb);
+                        const float lo = __ldcg(d.xlo + e) + err;
+                        const float h2 = s1 + lo;
+                        d.x[e] = h2;
+                        d.xlo[e] = lo - (h2 - s1);
+                    }
+                    const float r = fmaf(-al, __ldcg(d.q + e), __ldcg(d.r + e));
+                    const float z = r / __ldcg(d.dg + e);
+                    d.r[e] = r;
+                    d.z[e] = z;
+                    neumaier_add(s[ch], c[ch], r * z);
+                }
+                cta_partials<3>(s, c, d.part);
+            }
+            const bool last = k == d.cg_iters - 1;
+            if (!grid_barrier(st, gen, [&] {
+                    reduce_partials(d.part, 3, sc);
+                    if (threadIdx.x < 3) {
+                        const int ch = threadIdx.x;
+                        const float rz = st->rz[ch];
+                        st->beta[ch] = rz > 0.f ? sc[ch] / rz : 0.f;
+                        st->rz[ch] = sc[ch];
+                    }
+                    if (threadIdx.x == 0 && last) st->n = st->n + 1;
+                }))
+                return;
+        }
+    }
+}
+
+// J = clamp(u, 0, 1) (the restored image).
+__global__ void k_si_clamp(const float *__restrict__ u, float *__restrict__ J, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        J[i] = fminf(fmaxf(u[i], 0.f), 1.f);
+}
+
+__global__ void k_si_reset(SiState *st) {
+    st->arrive = 0;
+    st->n = 0;
+    st->done = 0;
+    st->status = 0;
+    st->n_final = 0;
+    st->err = 0;
+}
+
+struct SiLayout {
+    size_t state, part, planes, fx, fy, total;
+};
+
+SiLayout si_layout(int H, int W) {
+    SiLayout L;
+    const size_t N = (size_t)H * W;
+    size_t o = 0;
+    L.state = o; o = align_up(o + sizeof(SiState));
+    L.part = o; o = align_up(o + (size_t)6 * kSiMaxGrid * sizeof(float2));
+    L.planes = o; o = align_up(o + (size_t)7 * 3 * N * sizeof(float));  // r, z, p0, p1, q, diag, u's low part
+    L.fx = o; o = align_up(o + (size_t)3 * H * (W + 1) * sizeof(float));
+    L.fy = o; o = align_up(o + (size_t)3 * (H + 1) * W * sizeof(float));
+    L.total = o;
+    return L;
+}
+
+int si_grid(int E) {
+    static int cached = 0, cached_dev = -1;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cached_dev != dev) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_semi_implicit, kSiThreads, 0) != cudaSuccess)
+            return 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        cached = per_sm * sms;
+        cached_dev = dev;
+    }
+    int g = (E + kSiThreads - 1) / kSiThreads;
+    if (g > cached) g = cached;
+    if (g > kSiMaxGrid) g = kSiMaxGrid;
+    return g;
+}
+
+}  // namespace
+
+size_t semi_workspace_bytes(int H, int W) { return si_layout(H, W).total; }
+
+int run_semi_implicit(float *u, float *u_lo, const float *Phi, const float *lam, int H, int W, const dh_params *p,
+                      float step, int cg_iters, float *rho_hist, float *J, void *workspace, cudaStream_t s) {
+    const SiLayout L = si_layout(H, W);
+    char *ws = (char *)workspace;
+    const size_t n3 = (size_t)3 * H * W;
+    SiDesc d = {};
+    d.x = u;
+    d.phi = Phi;
+    d.lam = lam;
+    float *pl = (float *)(ws + L.planes);
+    d.r = pl;
+    d.z = pl + n3;
+    d.p[0] = pl + 2 * n3;
+    d.p[1] = pl + 3 * n3;
+    d.q = pl + 4 * n3;
+    d.dg = pl + 5 * n3;
+    d.xlo = u_lo ? u_lo : pl + 6 * n3;
+    d.zero_lo = u_lo ? 0 : 1;
+    d.fx = (float *)(ws + L.fx);
+    d.fy = (float *)(ws + L.fy);
+    d.part = (float2 *)(ws + L.part);
+    d.st = (SiState *)(ws + L.state);
+    d.rho_hist = rho_hist;
+    d.H = H;
+    d.W = W;
+    d.max_iter = p->max_iter;
+    d.cg_iters = cg_iters;
+    d.dirichlet = p->boundary == DH_BOUNDARY_ZERO;
+    d.no_edge = (p->variant & DH_VAR_NO_EDGE) != 0;
+    d.tol = p->tol;
+    d.inv_s = 1.0f / step;
+    d.eps = p->eps;
+    {  // App. A-B-2: normalised 5-tap Gaussian
+        double w[3];
+        for (int k = 0; k <= 2; ++k) w[k] = exp(-(double)(k * k) / (2.0 * (double)p->sigma * p->sigma));
+        const double sum = w[0] + 2.0 * (w[1] + w[2]);
+        d.wg0 = (float)(w[0] / sum);
+        d.wg1 = (float)(w[1] / sum);
+        d.wg2 = (float)(w[2] / sum);
+    }
+    const int G = si_grid((int)n3);
+    if (G <= 0) return DH_ECUDA;
+    k_si_reset<<<1, 1, 0, s>>>(d.st);
+    DH_CUDA_TRY(cudaGetLastError());
+    void *args[1] = {(void *)&d};
+    DH_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_semi_implicit, dim3(G), dim3(kSiThreads), args, 0, s));
+    if (J) {
+        const int g = (int)((n3 + 255) / 256 < 4096 ? (n3 + 255) / 256 : 4096);
+        k_si_clamp<<<g, 256, 0, s>>>(u, J, n3);
+        DH_CUDA_TRY(cudaGetLastError());
+    }
+    return DH_OK;
+}
+
+// Outcome of the last solve queued on this workspace (synchronises s).
+int read_semi_implicit(const void *workspace, cudaStream_t s, int *n_final, int *status, float rho[3]) {
+    SiState st;
+    const SiLayout L = si_layout(1, 1);
+    DH_CUDA_TRY(cudaMemcpyAsync(&st, (const char *)workspace + L.state, sizeof(st), cudaMemcpyDeviceToHost, s));
+    DH_CUDA_TRY(cudaStreamSynchronize(s));
+    *n_final = st.n_final;
+    *status = st.status;
+    for (int c = 0; c < 3; ++c) rho[c] = st.rho[c];
+    return DH_OK;
+}
+
+}  // namespace dh

@@ -97,3 +97,20 @@ def test_invalid_arguments_rejected_on_host():
     assert N.dh_workspace_bytes(4, 4, p.replace(sweep_variant=N.dh_sweep_variants())) == 0
     assert N.dh_tune(fake, fake, fake, 8, 8, p, 0, fake, 1 << 30) == N.DH_EINVAL
     assert N.dh_tune_set(8, 8, 0, 999) == N.DH_EINVAL
+
+
+def test_semi_implicit_arguments_rejected_on_host():
+    p = N.dh_params_default(N.DH_PRESET_PAPER)
+    fake = 1 << 20  # never dereferenced
+    b = N.dh_semi_implicit_workspace_bytes(64, 96)
+    assert b >= 4 * 3 * 64 * 96 * 6 and b < 4 * 3 * 64 * 96 * 9 + (1 << 20)
+    assert N.dh_semi_implicit_workspace_bytes(0, 96) == 0
+    args = (fake, None, fake, fake, 64, 96)
+    assert N.dh_semi_implicit(*args, p, 0.0, 16, None, None, fake, b) == N.DH_EINVAL
+    assert N.dh_semi_implicit(*args, p, float("nan"), 16, None, None, fake, b) == N.DH_EINVAL
+    assert N.dh_semi_implicit(*args, p, 2.0, 0, None, None, fake, b) == N.DH_EINVAL
+    assert N.dh_semi_implicit(*args, p.replace(storage=1), 2.0, 16, None, None, fake, b) == N.DH_EINVAL
+    assert N.dh_semi_implicit(*args, p.replace(eps=0.0), 2.0, 16, None, None, fake, b) == N.DH_EINVAL
+    assert N.dh_semi_implicit(*args, p, 2.0, 16, None, None, fake, b - 1) == N.DH_EWORKSPACE
+    assert N.dh_semi_implicit(*args, p, 2.0, 16, None, None, fake + 8, b) == N.DH_EWORKSPACE
+    assert N.dh_semi_implicit(None, None, fake, fake, 64, 96, p, 2.0, 16, None, None, fake, b) == N.DH_EINVAL
