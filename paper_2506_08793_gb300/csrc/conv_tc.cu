@@ -1,0 +1,270 @@
+// 3x3 convolution (zero padding, bias, optional ReLU) as an implicit GEMM on
+// the 5th-generation tensor cores: tcgen05.mma (kind::f16, bf16 operands,
+// fp32 accumulators in tensor memory), issued by one thread per CTA.
+//
+//   y[p][co] = bias[co] + sum_{tap, ci} x[p + tap][ci] * w[co][tap][ci]
+//
+// GEMM view: M = pixels (128 per CTA), N = output channels (NT per CTA),
+// K = 9 taps x C channels, walked in k-blocks of one tap and 32 channels.
+// Each k-block's operands are staged in shared memory by cp.async (16-byte
+// copies, zero-filled outside the image and past C) in the K-major layout
+// with the 64-byte swizzle: a 64-byte row per pixel / per output channel,
+// 16-byte chunk j of row r stored at chunk j ^ ((r >> 1) & 3).  A ring of
+// STAGES k-blocks keeps the loads ahead of the MMAs; each k-block's MMAs
+// (two K = 16 steps) are committed to that stage's mbarrier, which frees the
+// stage for the k-block STAGES ahead.  The epilogue reads the accumulators
+// with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = pixels), adds the
+// bias, applies ReLU, rounds to bf16 and stores.  The same kernel computes
+// the data gradient (x = dy, w flipped and transposed).
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace dh {
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kTcBM = 128;             // pixels per CTA = MMA M = TMEM lanes
+constexpr int kTcBK = 32;              // channels per k-block (64-byte rows)
+constexpr uint32_t kTcSmemBudget = 104 * 1024;  // two CTAs per SM (one's epilogue hides under the other's loop)
+constexpr long long kTcWaitCycles = 4000000000LL;  // about 2 s
+
+template <int NT>
+struct TcPlan {
+    static constexpr uint32_t A_BYTES = kTcBM * 64;
+    static constexpr uint32_t B_BYTES = NT * 64;
+    static constexpr uint32_t STAGE = A_BYTES + B_BYTES;  // multiple of 1024 (NT % 16 == 0)
+    static constexpr int STAGES = (int)(kTcSmemBudget / STAGE) < 16 ? (int)(kTcSmemBudget / STAGE) : 16;
+    static constexpr uint32_t SMEM = STAGES * STAGE + 1024;  // + alignment slack
+    static constexpr uint32_t TMEM_COLS = NT <= 32 ? 32 : NT <= 64 ? 64 : NT <= 128 ? 128 : 256;
+};
+
+// --- PTX wrappers (sm_100 family ISA) ---------------------------------------
+
+__device__ __forceinline__ void cp_async_16(uint32_t dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
+// 512 bytes apart (stride byte offset), leading byte offset unused (1),
+// descriptor version 1.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// Arrives on the mbarrier once every MMA this thread issued so far is done.
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128, 2)
+k_conv3x3_tc(const bf16 *__restrict__ x, int ldx, int C, int Nimg, int H, int W, const bf16 *__restrict__ w,
+             const float *__restrict__ bias, int Cout, int relu, bf16 *__restrict__ y, int ldy, int *err) {
+    using P = TcPlan<NT>;
+    constexpr int S = P::STAGES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t mma_bar[S];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int HW = H * W, M = Nimg * HW;
+    const int m0 = blockIdx.x * kTcBM, n0 = blockIdx.y * NT;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(P::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&mma_bar[s], 1);
+        mbar_init(&done_bar, 1);
+        fence_mbar_init();
+        s_fail = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    // this thread's A row: pixel m0 + tid
+    const int p = m0 + tid;
+    const bool pin = p < M;
+    const int pn = pin ? p / HW : 0, prem = pin ? p - pn * HW : 0;
+    const int py = prem / W, px = prem - py * W;
+    const int KC = (C + kTcBK - 1) / kTcBK, KB = 9 * KC;
+    const uint32_t sbase = smem_addr(smem);
+
+    auto load = [&](int kb, int stage) {
+        const int tap = kb / KC, c0 = (kb - tap * KC) * kTcBK;
+        const int yy = py + tap / 3 - 1, xx = px + tap % 3 - 1;
+        const uint32_t As = sbase + stage * P::STAGE, Bs = As + P::A_BYTES;
+        const bool ok = pin && yy >= 0 && yy < H && xx >= 0 && xx < W;
+        const bf16 *src = ok ? x + ((size_t)(pn * H + yy) * W + xx) * ldx + c0 : x;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool v = ok && c0 + 8 * j < C;
+            cp_async_16(As + tid * 64 + ((j ^ ((tid >> 1) & 3)) << 4), v ? src + 8 * j : x, v ? 16u : 0u);
+        }
+#pragma unroll
+        for (int i = 0; i < NT / 32; ++i) {
+            const int idx = tid + i * 128, r = idx >> 2, j = idx & 3, co = n0 + r;
+            const bool v = co < Cout && c0 + 8 * j < C;
+            const bf16 *ws = v ? w + ((size_t)co * 9 + tap) * C + c0 + 8 * j : w;
+            cp_async_16(Bs + r * 64 + ((j ^ ((r >> 1) & 3)) << 4), ws, v ? 16u : 0u);
+        }
+    };
+
+    constexpr uint32_t IDESC = f16_idesc(kTcBM, NT);
+    for (int s = 0; s < S - 1; ++s) {
+        if (s < KB) load(s, s);
+        cp_async_commit();
+    }
+    bool failed = false;
+    for (int kb = 0; kb < KB; ++kb) {
+        const int stage = kb % S;
+        cp_async_wait<S - 2>();     // this thread's copies of k-block kb have landed
+        fence_proxy_async_smem();   // ... and are visible to the tensor core's proxy
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const int c0 = (kb % KC) * kTcBK;
+            const int ksteps = C - c0 >= 32 ? 2 : 1;  // C % 16 == 0
+            const uint32_t As = sbase + stage * P::STAGE, Bs = As + P::A_BYTES;
+            for (int k = 0; k < ksteps; ++k)
+                tc_mma(tmem, sw64_desc(As + 32 * k), sw64_desc(Bs + 32 * k), IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit(&mma_bar[stage]);
+        }
+        // refill the stage that k-block kb-1 used once its MMAs are done
+        const int kn = kb + S - 1;
+        if (kn < KB) {
+            const int sn = kn % S;
+            if (kn >= S && !mbar_wait_bounded(&mma_bar[sn], ((kn / S) - 1) & 1, kTcWaitCycles)) failed = true;
+            load(kn, sn);
+        }
+        cp_async_commit();
+        if (__syncthreads_or(failed)) break;
+    }
+    if (tid == 0) tc_commit(&done_bar);
+    if (!mbar_wait_bounded(&done_bar, 0, kTcWaitCycles)) failed = true;
+    cp_async_wait<0>();
+    if (failed && err) atomicExch(err, DH_ETIMEOUT);
+    tc_fence_after();
+
+    // epilogue: warp w reads TMEM lanes 32w..32w+31, i.e. pixels m0 + 32w + lane
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c = 0; c < NT; c += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+        const int col = n0 + c;
+        if (row < M && col < Cout && !failed) {
+            uint32_t packed[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float v0 = __uint_as_float(r[2 * j]) + (bias ? __ldg(bias + col + 2 * j) : 0.f);
+                float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? __ldg(bias + col + 2 * j + 1) : 0.f);
+                if (relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                packed[j] = *reinterpret_cast<const uint32_t *>(&h);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(y + (size_t)row * ldy + col);
+            dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::TMEM_COLS)
+                     : "memory");
+}
+
+template <int NT>
+int launch_tc(const bf16 *x, int ldx, int C, int N, int H, int W, const bf16 *w, const float *b, int Cout, bool relu,
+              bf16 *y, int ldy, int *err, cudaStream_t s) {
+    using P = TcPlan<NT>;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return DH_ECUDA;
+    if (!attr_set[dev]) {
+        DH_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM));
+        attr_set[dev] = true;
+    }
+    const int M = N * H * W;
+    dim3 grid((M + kTcBM - 1) / kTcBM, (Cout + NT - 1) / NT);
+    k_conv3x3_tc<NT><<<grid, 128, P::SMEM, s>>>(x, ldx, C, N, H, W, w, b, Cout, relu ? 1 : 0, y, ldy, err);
+    DH_CUDA_TRY(cudaGetLastError());
+    return DH_OK;
+}
+
+}  // namespace
+
+// Tensor-core (tcgen05) 3x3 convolution; C % 16 == 0, Cout % 16 == 0, ldx and
+// ldy multiples of 8 (16-byte rows).  N tile: the smallest of 32, 64, 96,
+// 128, 192, 256 that holds Cout, else 256-wide tiles.
+int conv3x3_tc(const void *x, int ldx, int C, int N, int H, int W, const void *w, const float *b, int Cout, bool relu,
+               void *y, int ldy, int *err, cudaStream_t s) {
+    if (C % 16 || Cout % 16 || ldx % 8 || ldy % 8) return DH_EINVAL;
+    const bf16 *X = (const bf16 *)x, *Wt = (const bf16 *)w;
+    bf16 *Y = (bf16 *)y;
+    if (Cout <= 32) return launch_tc<32>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+    if (Cout <= 64) return launch_tc<64>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+    if (Cout <= 96) return launch_tc<96>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+    if (Cout <= 128) return launch_tc<128>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+    if (Cout <= 192) return launch_tc<192>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+    return launch_tc<256>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+}
+
+}  // namespace dh
