@@ -725,7 +725,7 @@ static uint32_t tma_smem_bytes(int th, int stages, int tma, int esize) {
 // tma: 0 generic gather, 1 TMA tiles with Phi/lambda staged, 2 TMA u tile with
 // Phi/lambda vector loads, 3 per-warp row streams (R = ring slots).
 static const SweepCfg kVariants[] = {
-    {8, 4, 1, 1, true},  // 0: library default (also the auto choice)
+    {6, 4, 1, 1, true, 5, 1},  // 0: library default: 24-row tiles, 5 CTAs/SM, multi-iteration launches
     {8, 4, 1, 1, true},  {8, 4, 2, 1, true},  {4, 8, 2, 1, true},  {4, 8, 1, 1, true},
     {8, 4, 1, 2, true},  {8, 4, 2, 2, true},  {4, 8, 1, 2, true},  {16, 4, 1, 2, true},
     {8, 8, 1, 2, true},  {16, 2, 2, 2, true}, {8, 4, 1, 3, true},  {8, 8, 1, 3, true},
@@ -777,8 +777,11 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
     const bool edge = !(p->variant & DH_VAR_NO_EDGE);
     SweepCfg c = kVariants[0];
     c.edge = edge;
+    if (is16) {  // 16-bit storage: one tiling, single-iteration launches
+        c = SweepCfg{8, 4, 1, tma_ok ? 1 : 0, edge};
+        return c;
+    }
     if (!tma_ok) c.tma = 0;
-    if (is16) return c;  // 16-bit storage: the default tiling only
     int v = p->sweep_variant;
     if (v <= 0) {
         int dev = 0;
@@ -790,12 +793,13 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
         c.edge = edge;
         return c;
     }
-    if (const char *e = std::getenv("DH_SWEEP")) {  // "R,NW,STAGES,TMA[,MULTI]"
-        int r, nw, st, t, mu = 0;
-        if (std::sscanf(e, "%d,%d,%d,%d,%d", &r, &nw, &st, &t, &mu) >= 4) {
+    if (const char *e = std::getenv("DH_SWEEP")) {  // "R,NW,STAGES,TMA[,MULTI[,MINB]]"
+        int r, nw, st, t, mu = 0, mb = 0;
+        if (std::sscanf(e, "%d,%d,%d,%d,%d,%d", &r, &nw, &st, &t, &mu, &mb) >= 4) {
             c.R = r;
             c.NW = nw;
             c.stages = st;
+            c.minb = mb;
             c.tma = tma_ok ? t : 0;
             if (c.tma == 3 && p->boundary == DH_BOUNDARY_ZERO) c.tma = 1;
             c.multi = c.tma == 1 ? (mu != 0) : 0;
@@ -803,6 +807,8 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
     }
     if (!c.tma && !sweep_fn<float>(c.R, c.NW, c.edge)) { c.R = 8; c.NW = 4; }
     if (!c.tma) c.stages = 1;
+    if (c.tma != 1) c.multi = 0;
+    if (c.tma == 0) c.minb = 0;
     return c;
 }
 

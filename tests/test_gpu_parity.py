@@ -235,7 +235,7 @@ def test_sweep_variants_bit_identical(N, api, orc, H, W, monkeypatch):
     _, _, Phi, lam = _problem(orc, 31 + H, H, W, "stable")
     outs = {}
     for cfg in ("8,4,2,0", "8,4,2,1", "8,4,1,1", "4,8,2,1", "8,4,1,2", "4,8,2,2", "16,4,1,2", "16,4,2,0",
-                "8,4,1,3", "8,8,1,3", "16,4,1,3", "8,2,1,3", "4,8,1,3"):
+                "8,4,1,3", "8,8,1,3", "16,4,1,3", "8,2,1,3", "4,8,1,3", "6,4,1,1,1,5", "8,4,1,1,1,0"):
         monkeypatch.setenv("DH_SWEEP", cfg)
         u = dev(Phi.copy())
         rep, _ = api.fixed_point(u, dev(Phi), dev(lam), api.params("stable", tol=0.0, max_iter=12))
