@@ -200,8 +200,7 @@ static void fill_solve_report(dh_report *r, const SolveState &st, int launches, 
     r->status = st.status;
     r->n_iter = st.n_final;
     for (int c = 0; c < 3; ++c) r->rho[c] = st.rho[c];
-    const int depth = st.depth > 0 ? st.depth : 1;  // sweeps per launch
-    r->launches = launches + (graph ? (st.n_final + depth) / depth : 0);
+    r->launches = launches + (graph ? (int)st.launches : 0);  // sweep launches counted on the device
 }
 
 int dh_fixed_point(float *u, const float *Phi, const float *lam, int H, int W, const dh_params *p,

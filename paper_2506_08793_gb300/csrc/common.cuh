@@ -17,6 +17,9 @@ constexpr size_t kAlign = 256;
 // One CTA owns a TW x TH tile of one channel.  Each thread owns 4 adjacent
 // columns and walks R rows; a warp covers the 128 columns of the tile.
 constexpr int kTW = 128;
+// The two-iteration sweep writes 120 output columns per tile (its first
+// iteration covers the 128 columns around them).
+constexpr int kTW2 = 120;
 
 // ---------------------------------------------------------------- device state
 // Iteration state of one image, in the workspace.
@@ -34,13 +37,14 @@ struct SolveState {
     int err;           // error raised inside a sweep (DH_ETIMEOUT), 0 if none
     int phase_start;   // first n of the current precision phase
     int depth;         // sweeps per launch of the current loop (SolveDesc::depth)
-    int pad;
+    int tb2;           // temporally blocked sweep: 1 while two iterations per tile load are taken
     float rmax[kStallWindow];  // max_c rho_n of the last iterations (ring)
     // Grid-barrier generation of the multi-iteration sweep, alone in its
     // 128-byte line so that the CTAs polling it do not contend with the
     // arrivals and state updates above.  Never reset: kernels read it first.
     unsigned gen;
-    int pad_gen[31];
+    unsigned launches;  // sweep launches since the last reset (counted by CTA 0 of each)
+    int pad_gen[30];
 };
 
 // status a 16-bit phase ends with when its residual stalls (internal)
@@ -100,7 +104,9 @@ static inline WsLayout ws_layout(int H, int W, int depth, int tile_h) {
     const size_t N = (size_t)H * W;
     L.depth = depth;
     L.tile_h = tile_h;
-    L.nblk_sweep = ((W + kTW - 1) / kTW) * ((H + tile_h - 1) / tile_h);
+    // tiles of the widest tiling any sweep uses (128 columns, or 120 for the
+    // two-iteration sweep) and the shortest (tile_h rows)
+    L.nblk_sweep = ((W + kTW2 - 1) / kTW2) * ((H + tile_h - 1) / tile_h);
     L.nblk_dcp = dcp_blocks(H, W);
     L.nblk_sel = kSelBlocks;
     size_t o = 0;

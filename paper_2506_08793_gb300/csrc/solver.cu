@@ -324,6 +324,349 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     if (!MULTI) arrive_and_finish(d, st, &s_last);
 }
 
+// ---------------------------------------------------------------- two iterations per tile load
+// Temporally blocked sweep (float iterates, W % 4 == 0, 16-byte aligned
+// planes).  An item is a 120 x TH output tile of one channel.  TMA loads u^n
+// on the output tile plus a 4-cell ring (136 x (TH+8)), Phi and lambda on the
+// tile plus a (2-row, 4-column) ring (128 x (TH+4)).  Step 1 walks the 128 x
+// (TH+4) region around the tile and keeps u^{n+1} in shared memory; after the
+// border ring is reflected, step 2 walks the tile from it and writes u^{n+2}.
+// The residual of step 1 over the tile is F(u^n) and that of step 2 is
+// F(u^{n+1}), the same quantities one iteration at a time would give.  The
+// last CTA at the grid barrier decides with both (finish_tb2): stop at n, or
+// advance by two, or - when u^{n+1} is the iterate to return (its residual
+// meets tol, or n+1 = max_iter) - switch the rest of the solve to one
+// iteration per load (step 1 writing the tile to global memory), which
+// recomputes u^{n+1} and stops there.
+template <int R2, int NW>
+struct Tb2Plan {
+    static constexpr int TH = R2 * NW;
+    static constexpr int R1 = R2 + 4 / NW;        // rows per warp in step 1 (TH + 4 rows)
+    static constexpr int SW = kTW + 8;            // 136 floats per shared row
+    static constexpr uint32_t U0_BYTES = (TH + 8) * SW * 4;
+    static constexpr uint32_t PL_BYTES = (TH + 4) * kTW * 4;
+    static constexpr uint32_t U1_BYTES = (TH + 4) * SW * 4;
+    static constexpr uint32_t U0_OFF = 0;
+    static constexpr uint32_t PHI_OFF = (U0_BYTES + 1023) / 1024 * 1024;
+    static constexpr uint32_t LAM_OFF = PHI_OFF + PL_BYTES;
+    static constexpr uint32_t U1_OFF = (LAM_OFF + PL_BYTES + 1023) / 1024 * 1024;
+    static constexpr uint32_t SMEM = U1_OFF + U1_BYTES + 1024;  // + alignment slack
+    static constexpr uint32_t TX = U0_BYTES + 2 * PL_BYTES;
+    static_assert(4 % NW == 0, "the TH + 4 step-1 rows must split evenly over the warps");
+};
+
+// Last CTA of a two-iteration sweep: residuals of both levels, decision.
+static __device__ void finish_tb2(const SolveDesc *d, SolveState *st) {
+    constexpr int U = 4;
+    __shared__ float2 wsum[6][32];
+    __shared__ float sq[6];
+    const int tid = threadIdx.x, nt = blockDim.x, w = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    __threadfence();
+    const int nblk = d->nblk;
+    const float2 *part = d->part;
+    float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, cc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int b0 = tid; b0 < nblk; b0 += U * nt) {
+        float2 pv[6][U];
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int b = b0 + j * nt;
+                pv[k][j] = b < nblk ? __ldcg(part + (size_t)k * nblk + b) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+#pragma unroll
+            for (int j = 0; j < U; ++j) neumaier_merge(s[k], cc[k], pv[k][j].x, pv[k][j].y);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        for (int off = 16; off; off >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s[k], off);
+            const float c2 = __shfl_down_sync(0xffffffffu, cc[k], off);
+            neumaier_merge(s[k], cc[k], s2, c2);
+        }
+        if (lane == 0) wsum[k][w] = make_float2(s[k], cc[k]);
+    }
+    __syncthreads();
+    if (tid < 6) {
+        float a = wsum[tid][0].x, b = wsum[tid][0].y;
+        for (int k = 1; k < nw; ++k) neumaier_merge(a, b, wsum[tid][k].x, wsum[tid][k].y);
+        sq[tid] = a + b;
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    const int n = st->n, two = st->tb2;
+    auto rho_of = [&](int lv, float *rho, float &worst) {
+        bool finite = true;
+        worst = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            const float pn = st->phin2[c], q = sq[3 * lv + c];
+            rho[c] = pn > 0.f ? sqrtf(q / pn) : sqrtf(q);
+            if (!isfinite(rho[c])) finite = false;
+            else worst = fmaxf(worst, rho[c]);
+        }
+        return finite;
+    };
+    float rho0[3], w0;
+    const bool fin0 = rho_of(0, rho0, w0);
+    if (d->rho_hist)
+        for (int c = 0; c < 3; ++c) d->rho_hist[3 * n + c] = rho0[c];
+    const int err = __ldcg(&st->err);
+    const bool conv = fin0 && w0 <= d->tol;
+    unsigned cont = 1;
+    if (err || conv || !fin0 || n >= d->max_iter) {
+        st->done = 1;
+        st->n_final = n;
+        st->status = err ? err : (!fin0 ? DH_ENONFINITE : (conv ? DH_OK : DH_WNOCONV));
+        for (int c = 0; c < 3; ++c) st->rho[c] = rho0[c];
+        cont = 0;
+    } else if (!two) {
+        st->n = n + 1;
+        st->cur ^= 1;
+    } else {
+        float rho1[3], w1;
+        const bool fin1 = rho_of(1, rho1, w1);
+        if (!fin1 || w1 <= d->tol || n + 1 >= d->max_iter) {
+            st->tb2 = 0;  // u^{n+1} may be the answer: redo it one iteration at a time
+        } else {
+            if (d->rho_hist)
+                for (int c = 0; c < 3; ++c) d->rho_hist[3 * (n + 1) + c] = rho1[c];
+            st->n = n + 2;
+            st->cur ^= 1;
+        }
+    }
+    st->arrive = 0;
+    __threadfence();
+    if (d->use_cond) cudaGraphSetConditional(d->cond, cont);
+}
+
+template <int R2, int NW, bool EDGE, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB)
+k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
+            const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
+            const SolveDesc *__restrict__ d) {
+    using P = Tb2Plan<R2, NW>;
+    constexpr int TH = P::TH, R1 = P::R1, SW = P::SW;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float2 red[2][NW];
+    __shared__ int s_last, s_timeout;
+    float *s0 = reinterpret_cast<float *>(smem + P::U0_OFF);
+    const float *sphi = reinterpret_cast<const float *>(smem + P::PHI_OFF);
+    const float *slam = reinterpret_cast<const float *>(smem + P::LAM_OFF);
+    float *s1 = reinterpret_cast<float *>(smem + P::U1_OFF);
+
+    SolveState *st = d->st;
+    clear_condition(d);
+    if (__ldcg(&st->done)) return;
+    unsigned gen = ld_acquire_gpu(&st->gen);
+    const int H = d->H, W = d->W;
+    const size_t N = (size_t)H * W;
+    const int ntx = (W + kTW2 - 1) / kTW2, nty = (H + TH - 1) / TH;
+    const int nitems = 3 * ntx * nty;
+    const int G = gridDim.x;
+    const int m = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
+    const bool dirichlet = d->dirichlet != 0;
+    float2 *__restrict__ part = d->part;
+    const int nblk = d->nblk;
+    int k = 0;
+    bool failed = false;
+    for (int it = 0; it < d->depth; ++it) {
+        const int cur = __ldcg(&st->cur);
+        const bool rev = (__ldcg(&st->n) & 1) != 0;
+        const bool two = __ldcg(&st->tb2) != 0;
+        const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
+        float *__restrict__ uout = static_cast<float *>(d->u[cur ^ 1]);
+        auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
+        auto tile_xy = [&](int item, int &c, int &x0, int &y0) {
+            const int tile = item / 3;
+            c = item - 3 * tile;
+            x0 = (tile % ntx) * kTW2;
+            y0 = (tile / ntx) * TH;
+            return tile;
+        };
+        auto issue = [&](int j) {
+            int c, x0, y0;
+            tile_xy(item_at(j), c, x0, y0);
+            mbar_arrive_expect_tx(&bar, P::TX);
+            tma_load_3d(smem + P::U0_OFF, tm_u, &bar, x0 - 8, y0 - 4, c);
+            tma_load_3d(smem + P::PHI_OFF, &tm_phi, &bar, x0 - 4, y0 - 2, c);
+            tma_load_2d(smem + P::LAM_OFF, &tm_lam, &bar, x0 - 4, y0 - 2);
+        };
+        auto prefetch = [&](int j) {
+            int c, x0, y0;
+            tile_xy(item_at(j), c, x0, y0);
+            tma_prefetch_3d(tm_u, x0 - 8, y0 - 4, c);
+            tma_prefetch_3d(&tm_phi, x0 - 4, y0 - 2, c);
+            tma_prefetch_2d(&tm_lam, x0 - 4, y0 - 2);
+        };
+        if (threadIdx.x == 0) {
+            if (it > 0) fence_proxy_async_global();
+            if (m > 0) issue(0);
+        }
+        int j = 0;
+        for (; j < m; ++j, ++k) {
+            int c, x0, y0;
+            const int tile = tile_xy(item_at(j), c, x0, y0);
+            if (threadIdx.x == 0 && j + 1 < m) prefetch(j + 1);
+            const bool ok = mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            // the reflecting boundary on the u^n tile (rows / columns 1-2 outside)
+            if (!dirichlet && (x0 < 8 || y0 < 4 || x0 + kTW2 + 8 > W || y0 + TH + 4 > H)) {
+                for (int e = threadIdx.x; e < (TH + 8) * SW; e += NW * 32) {
+                    const int r = e / SW, q = e - r * SW;
+                    const int gy = y0 - 4 + r, gx = x0 - 8 + q;
+                    const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
+                    const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
+                    const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
+                    if ((fy && (inx || fx)) || (fx && iny)) {
+                        const int sy = reflect_idx(gy, H) - (y0 - 4), sx = reflect_idx(gx, W) - (x0 - 8);
+                        s0[e] = s0[sy * SW + sx];
+                    }
+                }
+                fence_proxy_async_smem();  // these writes precede the next TMA load into this buffer
+            }
+            __syncthreads();
+
+            // step 1: region rows y0-2 .. y0+TH+1, columns x0-4 .. x0+123 (frame row t, column 4*lane + j)
+            float rs0 = 0.f, rc0 = 0.f, rs1 = 0.f, rc1 = 0.f;
+            {
+                const int xo = x0 - 4 + 4 * lane;  // output column of this lane's first pixel
+                const bool colin = lane >= 1 && lane <= 30 && xo < W;
+                float *__restrict__ gout = uout + c * N;
+                auto pl = [&](int t, float *ph, float *la) {
+                    const float4 p4 = *reinterpret_cast<const float4 *>(sphi + t * kTW + 4 * lane);
+                    const float4 l4 = *reinterpret_cast<const float4 *>(slam + t * kTW + 4 * lane);
+                    ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
+                    la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
+                };
+                auto sink = [&](int t, const float *nu, const float *F) {
+                    const int yo = y0 - 2 + t;
+                    const bool in = colin && t >= 2 && t < TH + 2 && yo < H;
+                    if (in) {
+                        float q = 0.f;
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) q = fmaf(F[jj], F[jj], q);
+                        neumaier_add(rs0, rc0, q);
+                    }
+                    if (two) {
+                        *reinterpret_cast<float4 *>(s1 + t * SW + 4 * lane) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+                    } else if (in) {
+                        *reinterpret_cast<float4 *>(gout + (size_t)yo * W + xo) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+                    }
+                };
+                walk_rows<R1, SW, float, EDGE>(s0 + 0 * SW, w * R1, lane, eps, tau, wg0, wg1, wg2, pl, sink);
+            }
+            if (two) {
+                __syncthreads();
+                // boundary rule on u^{n+1} (shared rows y0-2.., columns x0-4..)
+                if (dirichlet || x0 < 4 || y0 < 4 || x0 + kTW2 + 4 > W || y0 + TH + 4 > H) {
+                    for (int e = threadIdx.x; e < (TH + 4) * kTW; e += NW * 32) {
+                        const int r = e / kTW, q = e - r * kTW;
+                        const int gy = y0 - 2 + r, gx = x0 - 4 + q;
+                        const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
+                        if (iny && inx) continue;
+                        if (dirichlet) {
+                            s1[r * SW + q] = 0.f;
+                        } else {
+                            const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
+                            const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
+                            if ((fy && (inx || fx)) || (fx && iny)) {
+                                const int sy = reflect_idx(gy, H) - (y0 - 2), sx = reflect_idx(gx, W) - (x0 - 4);
+                                s1[r * SW + q] = s1[sy * SW + sx];
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+                // step 2: the tile (frame row t = output row y0 + t, column x0 + 4*lane + j)
+                const int xo = x0 + 4 * lane;
+                const bool colin = lane < 30 && xo < W;
+                float *__restrict__ gout = uout + c * N;
+                auto pl = [&](int t, float *ph, float *la) {
+                    const float4 p4 = *reinterpret_cast<const float4 *>(sphi + (t + 2) * kTW + 4 + 4 * lane);
+                    const float4 l4 = *reinterpret_cast<const float4 *>(slam + (t + 2) * kTW + 4 + 4 * lane);
+                    ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
+                    la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
+                };
+                auto sink = [&](int t, const float *nu, const float *F) {
+                    const int yo = y0 + t;
+                    if (!colin || yo >= H) return;
+                    float q = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) q = fmaf(F[jj], F[jj], q);
+                    neumaier_add(rs1, rc1, q);
+                    *reinterpret_cast<float4 *>(gout + (size_t)yo * W + xo) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+                };
+                walk_rows<R2, SW, float, EDGE>(s1, w * R2, lane, eps, tau, wg0, wg1, wg2, pl, sink);
+            }
+            const float2 t0 = block_pair_sum<NW>(rs0, rc0, red[0]);  // ends with a barrier
+            const float2 t1 = block_pair_sum<NW>(rs1, rc1, red[1]);
+            if (threadIdx.x == 0) {
+                part[(size_t)c * nblk + tile] = t0;
+                part[(size_t)(3 + c) * nblk + tile] = t1;
+                if (j + 1 < m) {
+                    fence_proxy_async_smem();
+                    issue(j + 1);
+                }
+            }
+            __syncthreads();
+        }
+        if (failed) {
+            if (j < m) mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);  // the load in flight
+            if (threadIdx.x == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
+        }
+        // grid barrier; the last CTA to arrive decides
+        fence_proxy_async_global();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(&st->arrive, 1u) == (unsigned)G - 1u;
+            s_timeout = 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            finish_tb2(d, st);
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release_gpu(&st->gen, gen + 1u);
+            }
+        } else if (threadIdx.x == 0) {
+            const long long t0 = clock64();
+            while (ld_acquire_gpu(&st->gen) == gen) {
+                if (clock64() - t0 > kWaitLimitCycles) {
+                    s_timeout = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        ++gen;
+        __syncthreads();
+        if (s_timeout) {
+            if (threadIdx.x == 0) {
+                atomicCAS(&st->err, 0, DH_ETIMEOUT);
+                st->status = DH_ETIMEOUT;
+                st->done = 1;
+            }
+            return;
+        }
+        if (__ldcg(&st->done) || failed) return;
+    }
+}
+
 // Streaming sweep (W % 4 == 0, 16-byte aligned planes).  Each warp owns
 // segments of a 128-column strip of one channel (tasks) and walks their rows
 // top to bottom.  Lane 0 streams rows into a per-warp ring of NSLOT row slots
@@ -558,6 +901,8 @@ __global__ void k_set_desc(SolveDesc *dst, SolveDesc v, int reset) {
     st->n_final = 0;
     st->err = 0;
     st->phase_start = 0;
+    st->tb2 = 1;
+    st->launches = 0;
 }
 
 // J = clamp(u^n, 0, 1) and u^n as float32 into u_out (skipped when u^n is
@@ -621,7 +966,7 @@ constexpr int kItersPerLaunch = 64;
 
 constexpr int kMinTileH = 16;  // smallest tile height any variant uses
 
-int sweep_depth(const dh_params *) { return 1; }
+int sweep_depth(const dh_params *) { return 2; }  // residual levels per tile (two-iteration sweep)
 int sweep_tile_h(int) { return kMinTileH; }
 
 typedef void (*SweepFn)(const SolveDesc *);
@@ -678,6 +1023,21 @@ static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge, in
 #undef DH_STM
 #undef DH_STX
     return nullptr;
+}
+
+static SweepTmaFn sweep_tb2_fn(int R, int NW, bool edge) {
+#define DH_TB(r, nw, mb) \
+    if (R == r && NW == nw) return edge ? (SweepTmaFn)k_sweep_tb2<r, nw, true, mb> : (SweepTmaFn)k_sweep_tb2<r, nw, false, mb>;
+    DH_TB(4, 4, 4)
+    DH_TB(6, 4, 3)
+#undef DH_TB
+    return nullptr;
+}
+
+static uint32_t tb2_smem_bytes(int R, int NW) {
+    if (R == 4 && NW == 4) return Tb2Plan<4, 4>::SMEM;
+    if (R == 6 && NW == 4) return Tb2Plan<6, 4>::SMEM;
+    return 0;
 }
 
 typedef void (*SweepStreamFn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const SolveDesc *, int);
@@ -737,6 +1097,8 @@ static const SweepCfg kVariants[] = {
     {8, 4, 1, 1, true, 0, 1}, {6, 4, 1, 1, true, 5, 1}, {4, 4, 1, 1, true, 6, 1}, {6, 4, 1, 1, true, 0, 1},
     // 29-30: 16-row tiles, two stages (the next item's tiles land while this one is computed)
     {4, 4, 2, 1, true}, {4, 4, 2, 1, true, 0, 1},
+    // 31-32: two iterations per tile load (120 x 16 / 120 x 24 output tiles), multi-iteration launches
+    {4, 4, 1, 4, true, 0, 1}, {6, 4, 1, 4, true, 0, 1},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
@@ -802,12 +1164,12 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
             c.minb = mb;
             c.tma = tma_ok ? t : 0;
             if (c.tma == 3 && p->boundary == DH_BOUNDARY_ZERO) c.tma = 1;
-            c.multi = c.tma == 1 ? (mu != 0) : 0;
+            c.multi = c.tma == 1 ? (mu != 0) : (c.tma == 4 ? 1 : 0);
         }
     }
     if (!c.tma && !sweep_fn<float>(c.R, c.NW, c.edge)) { c.R = 8; c.NW = 4; }
     if (!c.tma) c.stages = 1;
-    if (c.tma != 1) c.multi = 0;
+    if (c.tma != 1 && c.tma != 4) c.multi = 0;
     if (c.tma == 0) c.minb = 0;
     return c;
 }
@@ -997,6 +1359,26 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
         if (v.nblk > L.nblk_sweep) return DH_EINVAL;
         const int g = (3 * v.nblk + cfg.NW - 1) / cfg.NW;
         ls = LaunchSpec{(void *)fn, dim3(g < gmax ? g : gmax), dim3(cfg.NW * 32), smem, args_stream};
+    } else if (cfg.tma == 4 && esize == 4) {
+        // two iterations per tile load: 120 x TH output tiles
+        const int TH = cfg.th();
+        if (TH < kMinTileH) return DH_EINVAL;
+        v.nblk = ((W + kTW2 - 1) / kTW2) * ((H + TH - 1) / TH);
+        if (v.nblk > L.nblk_sweep || L.depth < 2) return DH_EINVAL;
+        int rc = encode_f32_map(&maps[0], v.u[0], 3, W, H, 3, kTW + 8, TH + 8);
+        if (!rc) rc = encode_f32_map(&maps[1], v.u[1], 3, W, H, 3, kTW + 8, TH + 8);
+        if (!rc) rc = encode_f32_map(&maps[2], v.phi, 3, W, H, 3, kTW, TH + 4);
+        if (!rc) rc = encode_f32_map(&maps[3], v.lam, 2, W, H, 1, kTW, TH + 4);
+        if (rc) return rc;
+        SweepTmaFn fn = sweep_tb2_fn(cfg.R, cfg.NW, cfg.edge);
+        const unsigned smem = tb2_smem_bytes(cfg.R, cfg.NW);
+        if (!fn || !smem) return DH_EINVAL;
+        const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
+        if (gmax <= 0) return DH_ECUDA;
+        const int items = 3 * v.nblk;
+        ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(cfg.NW * 32), smem, args_tma};
+        ls.coop = 1;
+        v.depth = kItersPerLaunch;
     } else if (cfg.tma == 1 || cfg.tma == 2) {
         const int TH = cfg.th();
         if (TH < kMinTileH) return DH_EINVAL;

@@ -133,9 +133,12 @@ static __device__ void finish_iteration(const SolveDesc *d, SolveState *st) {
 // launch that failed to count its CTAs cannot spin forever.  CTA (0,0,0)
 // clears it before it arrives, hence before the last CTA decides.
 __device__ __forceinline__ void clear_condition(const SolveDesc *d) {
-    if (d->use_cond && (blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) {
-        cudaGraphSetConditional(d->cond, 0);
-        __threadfence();
+    if ((blockIdx.x | blockIdx.y | blockIdx.z | threadIdx.x) == 0) {
+        atomicAdd(&d->st->launches, 1u);
+        if (d->use_cond) {
+            cudaGraphSetConditional(d->cond, 0);
+            __threadfence();
+        }
     }
 }
 
