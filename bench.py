@@ -132,7 +132,7 @@ def cpu_sample(I, H, W, iters, n_gpu_iters):
     return (t1 - t0) + per_iter * n_gpu_iters, oracle.num_threads(), (t1 - t0), per_iter
 
 
-def batch_extra(api, p, n=16, reps=3):
+def batch_extra(api, p, n=64, reps=3):
     """Uneven-size batch (sizes drawn from the four photo sizes) in one batched
     solve: images/s and MPix*iter/s (device time, inputs resident)."""
     import torch

@@ -23,7 +23,7 @@ int encode_f32_map(CUtensorMap *m, const void *base, int rank, int W, int H, int
 int sweep_tile_h(int depth);
 
 constexpr int kMaxBatch = 256;
-constexpr int kBR = 8, kBNW = 4, kBTH = kBR * kBNW;  // 128 x 32 tiles, 4 warps
+constexpr int kBR = 6, kBNW = 4, kBTH = kBR * kBNW;  // 128 x 24 tiles, 4 warps, 5 CTAs per SM
 
 // Per-image loop data in device memory.
 struct __align__(128) BImg {
@@ -36,6 +36,7 @@ struct BatchHdr {
     BImg *imgs;
     int nimg;
     int nactive;
+    int iter;          // loop iterations so far (odd ones walk the items in reverse)
     unsigned arrive;
     int use_cond;
     unsigned long long cond;
@@ -99,6 +100,7 @@ __global__ void k_batch_init(BatchHdr *h, BImg *imgs, int n, int use_cond, unsig
     h->imgs = imgs;
     h->nimg = n;
     h->nactive = n;
+    h->iter = 0;
     h->arrive = 0;
     h->use_cond = use_cond;
     h->cond = cond;
@@ -112,7 +114,7 @@ __global__ void k_batch_init(BatchHdr *h, BImg *imgs, int n, int use_cond, unsig
 }
 
 template <bool EDGE>
-__global__ void __launch_bounds__(kBNW * 32)
+__global__ void __launch_bounds__(kBNW * 32, 5)
 k_sweep_batch(BatchHdr *__restrict__ hb) {
     using P = TmaPlan<kBTH, true, float>;
     constexpr int SW = P::SW, SH = P::SH;
@@ -123,6 +125,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
     __shared__ int s_last, s_img_last;
     __shared__ int s_active[kMaxBatch];
     __shared__ int s_prefix[kMaxBatch + 1];
+    __shared__ int s_cur[kMaxBatch];  // buffer holding u^n of each active image (fixed for the launch)
 
     if (hb->use_cond && (blockIdx.x | threadIdx.x) == 0) {
         cudaGraphSetConditional(hb->cond, 0);  // the last CTA sets it back while images remain
@@ -131,6 +134,8 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
     const int nact = __ldcg(&hb->nactive);
     for (int k = threadIdx.x; k < nact; k += blockDim.x) s_active[k] = __ldcg(&hb->active[k]);
     for (int k = threadIdx.x; k <= nact; k += blockDim.x) s_prefix[k] = __ldcg(&hb->prefix[k]);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nact; k += blockDim.x) s_cur[k] = __ldcg(&hb->imgs[s_active[k]].d.st->cur);
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -144,42 +149,55 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
     float *slam = reinterpret_cast<float *>(sb + P::LAM_OFF);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 
-    // item -> (image, tile, channel)
-    auto locate = [&](int item, int &img, int &tile, int &c) {
+    // item -> (active slot, image, tile, channel)
+    auto locate = [&](int item, int &slot, int &img, int &tile, int &c) {
         int lo = 0, hi = nact - 1;  // last k with prefix[k] <= item
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (s_prefix[mid] <= item) lo = mid; else hi = mid - 1;
         }
+        slot = lo;
         img = s_active[lo];
         const int j = item - s_prefix[lo];
         tile = j / 3;
         c = j - 3 * tile;
     };
-    auto issue = [&](int item) {  // thread 0, TMA images only
-        int img, tile, c;
-        locate(item, img, tile, c);
+    // this CTA's items: blockIdx.x + j*G; odd loop iterations take them in
+    // reverse, starting on the tiles the previous iteration touched last
+    const int m = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / G + 1 : 0;
+    const bool rev = (__ldcg(&hb->iter) & 1) != 0;
+    auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
+    // thread 0, TMA images only: load an item's tiles.  The maps were written
+    // on the device (k_batch_put): acquire them for the tensor-map proxy when
+    // the image changes from the previous load of this CTA.
+    int acq_img = -1;
+    auto issue = [&](int item) {
+        int slot, img, tile, c;
+        locate(item, slot, img, tile, c);
         BImg *im = imgs + img;
         if (!im->tma) return;
-        const SolveDesc &d = im->d;
-        const int x0 = (tile % im->ntx) * kTW, y0 = (tile / im->ntx) * kBTH;
-        const int cur = __ldcg(&d.st->cur);
-        const CUtensorMap *tu = &im->tm[cur];
-        tensormap_acquire(tu);
-        tensormap_acquire(&im->tm[2]);
-        tensormap_acquire(&im->tm[3]);
+        const int ntx = im->ntx;
+        const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * kBTH;
+        const CUtensorMap *tu = &im->tm[s_cur[slot]];
+        if (img != acq_img) {
+            tensormap_acquire(tu);
+            tensormap_acquire(&im->tm[2]);
+            tensormap_acquire(&im->tm[3]);
+            acq_img = img;
+        }
         mbar_arrive_expect_tx(&bar, P::TX);
         tma_load_3d(sb + P::U_OFF, tu, &bar, x0 - 4, y0 - 2, c);
         tma_load_3d(sb + P::PHI_OFF, &im->tm[2], &bar, x0, y0, c);
         tma_load_2d(sb + P::LAM_OFF, &im->tm[3], &bar, x0, y0);
     };
-    if (threadIdx.x == 0 && (int)blockIdx.x < total) issue(blockIdx.x);
+    if (threadIdx.x == 0 && m > 0) issue(item_at(0));
 
     int kt = 0;  // TMA items waited for so far (barrier phase)
     bool failed = false;
-    for (int item = blockIdx.x; item < total; item += G) {
-        int img, tile, c;
-        locate(item, img, tile, c);
+    for (int j = 0; j < m; ++j) {
+        const int item = item_at(j);
+        int slot, img, tile, c;
+        locate(item, slot, img, tile, c);
         BImg *im = imgs + img;
         const SolveDesc *d = &im->d;
         SolveState *st = d->st;
@@ -187,7 +205,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         const size_t N = (size_t)H * W;
         const int ntx = im->ntx;
         const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * kBTH;
-        const int cur = __ldcg(&st->cur);
+        const int cur = s_cur[slot];
         if (im->tma) {
             const bool ok = mbar_wait_bounded(&bar, kt & 1, kWaitLimitCycles);
             ++kt;
@@ -260,8 +278,12 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         };
         walk_rows<kBR, SW, float, EDGE>(s, w * kBR, lane, d->eps, d->tau, d->wg0, d->wg1, d->wg2, pl, sink);
 
-        const float2 tot = block_pair_sum<kBNW>(rs, rc, red);  // ends with a barrier
+        const float2 tot = block_pair_sum<kBNW>(rs, rc, red);  // every thread is past its walk
         if (threadIdx.x == 0) {
+            if (j + 1 < m) {  // the stage is free: start the next load first
+                fence_proxy_async_smem();
+                issue(item_at(j + 1));
+            }
             d->part[(size_t)c * d->nblk + tile] = tot;
             __threadfence();
             const unsigned prev = atomicAdd(&st->arrive, 1u);
@@ -269,10 +291,6 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         }
         __syncthreads();
         if (s_img_last) finish_iteration(d, st);  // this image's iteration is complete
-        if (threadIdx.x == 0 && item + G < total) {
-            fence_proxy_async_smem();
-            issue(item + G);
-        }
         __syncthreads();
     }
     if (failed) {
@@ -309,6 +327,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         }
         hb->prefix[k] = acc;
         hb->nactive = k;
+        hb->iter = hb->iter + 1;
         hb->arrive = 0;
         __threadfence();
         if (hb->use_cond && k > 0) cudaGraphSetConditional(hb->cond, 1);
