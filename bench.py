@@ -182,6 +182,18 @@ def warm_extra(api, p, im, train_n=256, steps=600):
             "speedup": ms_c / ms_w}
 
 
+def reduce_max(x: float, world: int, device) -> float:
+    """Maximum of x over the ranks (the slowest rank's time); x itself at N = 1."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -197,7 +209,7 @@ def run_reference(args, rank, world):
     A, _, _ = oracle.atmospheric_light(I, dc, op.topk_permille)
     td = oracle.dark_channel(I, op.patch, A)
     _, lam, Phi = oracle.transmission(I, A, td, op)
-    iters = 8
+    iters = args.ref_iters
     u = Phi.copy()
     for _ in range(args.warmup):
         u, _, _ = oracle.solve(u, Phi, lam, op, iters, 0.0)
@@ -228,6 +240,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=12)
+    ap.add_argument("--ref-iters", type=int, default=8, help="oracle iterations per step of the reference arm")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library default variant)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched (uneven sizes) and learned-warm-start measurements")
@@ -293,11 +306,7 @@ def main():
         torch.cuda.synchronize()
         clocks = sampler.stop() if sampler else None
         barrier()
-        ms = ev0.elapsed_time(ev1)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = reduce_max(ev0.elapsed_time(ev1), world, "cuda")
         return ms, reps, clocks
 
     ms, reps, clocks = timed(False)
