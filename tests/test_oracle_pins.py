@@ -278,6 +278,39 @@ def test_fixed_point_is_newton_root(orc):
     assert np.abs(u - v).max() < 1e-9
 
 
+def test_linear_limit_root_and_instability(orc):
+    """eps = 1e6: D = 1/eps to 1e-12 relative, so F(u) = Lap(u)/eps - lambda G(u)
+    + Phi is linear.  Its root, from operator matrices built by applying scipy's
+    reflecting laplace and gaussian_filter to unit vectors and a dense solve,
+    zeroes the oracle's F.  The explicit iteration does not reach it: the
+    truncated Gaussian's symbol is negative near 1.94 rad (Sec. III-C's
+    coercivity claim fails), and without diffusion to damp those modes
+    u + tau F amplifies them by 1 + tau lambda |g| per step."""
+    I, p, lam, Phi = _small_problem(orc, 24, 7, 9, orc.STABLE)
+    eps = 1e6
+    p.eps = eps
+    H, W = lam.shape
+    m = H * W
+    Lap = np.empty((m, m))
+    Gm = np.empty((m, m))
+    for k in range(m):
+        e = np.zeros(m)
+        e[k] = 1.0
+        e = e.reshape(H, W)
+        Lap[:, k] = ndi.laplace(e, mode="reflect").ravel()
+        Gm[:, k] = ndi.gaussian_filter(e, 2.0, mode="reflect", truncate=1.0).ravel()
+    A = -Lap / eps + lam.ravel()[:, None] * Gm
+    want = np.stack([np.linalg.solve(A, Phi[c].ravel()).reshape(H, W) for c in range(3)])
+    # (lambda G is nearly singular where the symbol crosses zero and D deviates
+    # from 1/eps by |grad u|/eps: the root holds to ~1e-6 of |Phi|)
+    f = orc.F(want, Phi, lam, p)
+    assert np.abs(f).max() <= 1e-5 * np.abs(Phi).max()
+    # the explicit iteration drifts away from it
+    _, n, rho = orc.solve(Phi, Phi, lam, p, 6000, 0.0)
+    r = rho.max(axis=1)
+    assert n == 6000 and r[-1] > 10 * r.min()
+
+
 def test_uniqueness_from_different_initial_guesses(orc):
     """Sec. III-D claims a unique solution; the stable preset reaches the same
     u from u0 = Phi, 0, I and a random field."""
