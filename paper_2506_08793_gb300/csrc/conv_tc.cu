@@ -249,6 +249,218 @@ int launch_tc(const bf16 *x, int ldx, int C, int N, int H, int W, const bf16 *w,
     return DH_OK;
 }
 
+// ---------------------------------------------------------------- shallow layers
+// Layers with few channels (C <= 96 in, <= 96 out) are bound by reading their
+// input, which the general kernel above stages once per tap.  Here a tile is
+// a 128-pixel segment of one image row; its three input rows with a one-pixel
+// margin (3 x 130 pixels x C) are staged once, and each of the nine taps is
+// the same staging viewed through a shifted descriptor.  That needs the
+// non-swizzled K-major layout ("core matrices" of 8 rows x 16 bytes): channel
+// chunk q (8 channels) of pixel p of halo row r at ((r*QC + q)*130 + p)*16
+// bytes, so that for any start pixel the M = 128 rows of a tap are core
+// matrices 128 bytes apart (stride byte offset) and the two 8-channel chunks
+// of a K = 16 step are 130*16 bytes apart (leading byte offset).  All the
+// weights stay in shared memory for the CTA's lifetime, in the same layout
+// ([tap][chunk][cout] rows).  CTAs are persistent over the tiles; the next
+// tile's input is staged while the current tile's MMAs and epilogue run.
+template <int C, int CO>
+struct HaloPlan {
+    static constexpr int QC = C / 8;                         // 8-channel chunks
+    static constexpr uint32_t W_BYTES = 9u * QC * CO * 16;
+    static constexpr uint32_t HALO_BYTES = 3u * QC * 130 * 16;
+    static constexpr uint32_t W_OFF = 0;
+    static constexpr uint32_t H_OFF = (W_BYTES + 1023) / 1024 * 1024;
+    static constexpr uint32_t H_STRIDE = (HALO_BYTES + 1023) / 1024 * 1024;
+    static constexpr uint32_t SMEM = H_OFF + 2 * H_STRIDE + 1024;
+    static constexpr uint32_t TMEM_COLS = CO <= 32 ? 32 : CO <= 64 ? 64 : 128;
+    static_assert(C % 16 == 0 && CO % 16 == 0 && CO <= 128, "channel counts");
+};
+
+// K-major, no swizzle: leading byte offset = K-direction core-matrix stride,
+// stride byte offset = M/N-direction core-matrix stride.
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;  // layout type 0: no swizzle
+}
+
+template <int C, int CO>
+__global__ void __launch_bounds__(128)
+k_conv3x3_halo(const bf16 *__restrict__ x, int ldx, int Nimg, int H, int W, const bf16 *__restrict__ w,
+               const float *__restrict__ bias, int relu, bf16 *__restrict__ y, int ldy, int *err) {
+    using P = HaloPlan<C, CO>;
+    constexpr int QC = P::QC;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int segs = (W + 127) / 128;
+    const int T = Nimg * H * segs;
+    const uint32_t sbase = smem_addr(smem);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(P::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(&mma_bar, 1);
+        fence_mbar_init();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    // weights [co][tap][ci] -> shared [tap][chunk][co] 16-byte rows
+    for (int e = tid; e < 9 * QC * CO; e += 128) {
+        const int co = e % CO, rest = e / CO, q = rest % QC, tap = rest / QC;
+        cp_async_16(sbase + P::W_OFF + (uint32_t)e * 16, w + ((size_t)co * 9 + tap) * C + 8 * q, 16u);
+    }
+    // thread tid stages halo pixel tid (and tids 0, 1 also pixels 128, 129):
+    // all C channels of it in the three rows
+    auto stage_halo = [&](int t, int stg) {
+        const int seg = t % segs, row = t / segs, n = row / H, yy = row - n * H;
+        const int x0 = seg * 128;
+        const uint32_t hb = sbase + P::H_OFF + stg * P::H_STRIDE;
+        for (int pp = 0; pp < 2; ++pp) {
+            const int p = tid + 128 * pp;
+            if (p >= 130) break;
+            const int gx = x0 + p - 1;
+            const bool colok = gx >= 0 && gx < W;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int gy = yy + r - 1;
+                const bool ok = colok && gy >= 0 && gy < H;
+                const bf16 *src = ok ? x + ((size_t)(n * H + gy) * W + gx) * ldx : x;
+                const uint32_t dst = hb + (uint32_t)((r * QC * 130 + p) * 16);
+#pragma unroll
+                for (int q = 0; q < QC; ++q)
+                    cp_async_16(dst + (uint32_t)(q * 130 * 16), ok ? src + 8 * q : x, ok ? 16u : 0u);
+            }
+        }
+    };
+    const int G = gridDim.x;
+    int t = blockIdx.x;
+    if (t < T) stage_halo(t, 0);
+    cp_async_commit();
+    constexpr uint32_t IDESC = f16_idesc(kTcBM, CO);
+    bool failed = false;
+    for (int i = 0; t < T; ++i, t += G) {
+        const int stg = i & 1;
+        if (t + G < T) stage_halo(t + G, stg ^ 1);  // that stage's MMAs finished last iteration
+        cp_async_commit();
+        cp_async_wait<1>();
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t hb = sbase + P::H_OFF + stg * P::H_STRIDE;
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap % 3;  // halo row, start pixel
+                for (int kk = 0; kk < QC / 2; ++kk) {
+                    const uint32_t a = hb + (uint32_t)(((dy * QC + 2 * kk) * 130 + dx) * 16);
+                    const uint32_t b = sbase + P::W_OFF + (uint32_t)((tap * QC + 2 * kk) * CO * 16);
+                    tc_mma(tmem, kmajor_desc(a, 130 * 16, 128), kmajor_desc(b, CO * 16, 128), IDESC,
+                           (tap > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            tc_commit(&mma_bar);
+        }
+        if (!mbar_wait_bounded(&mma_bar, i & 1, kTcWaitCycles)) failed = true;
+        tc_fence_after();
+        // epilogue: TMEM lane = pixel of the segment
+        const int seg = t % segs, row = t / segs;
+        const int px = seg * 128 + warp * 32 + lane;
+#pragma unroll
+        for (int c = 0; c < CO; c += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+            if (px < W && !failed) {
+                uint32_t packed[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float v0 = __uint_as_float(r[2 * j]) + (bias ? __ldg(bias + c + 2 * j) : 0.f);
+                    float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? __ldg(bias + c + 2 * j + 1) : 0.f);
+                    if (relu) {
+                        v0 = fmaxf(v0, 0.f);
+                        v1 = fmaxf(v1, 0.f);
+                    }
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+                    packed[j] = *reinterpret_cast<const uint32_t *>(&h2);
+                }
+                uint4 *dst = reinterpret_cast<uint4 *>(y + ((size_t)row * W + px) * ldy + c);
+                dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+            }
+        }
+        tc_fence_before();
+        if (__syncthreads_or(failed)) break;  // TMEM and the stage are free for the next tile
+    }
+    cp_async_wait<0>();
+    if (failed && err) atomicExch(err, DH_ETIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::TMEM_COLS)
+                     : "memory");
+}
+
+template <int C, int CO>
+int launch_halo(const bf16 *x, int ldx, int N, int H, int W, const bf16 *w, const float *b, bool relu, bf16 *y,
+                int ldy, int *err, cudaStream_t s) {
+    using P = HaloPlan<C, CO>;
+    static int grid_cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return DH_ECUDA;
+    if (!grid_cache[dev]) {
+        DH_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3_halo<C, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)P::SMEM));
+        // CTAs per SM as shared memory and tensor memory allow (the CTAs are
+        // independent: a grid larger than what is resident is still correct)
+        int smem_sm = 0, sms = 0;
+        DH_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        DH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int per_sm = smem_sm / (int)(P::SMEM + 2048);  // + static shared memory and the per-CTA reserve
+        if (per_sm > (int)(512 / P::TMEM_COLS)) per_sm = 512 / P::TMEM_COLS;
+        if (per_sm > 8) per_sm = 8;
+        if (per_sm < 1) per_sm = 1;
+        grid_cache[dev] = per_sm * sms;
+    }
+    const long long T = (long long)N * H * ((W + 127) / 128);
+    const int grid = (int)(T < grid_cache[dev] ? T : grid_cache[dev]);
+    k_conv3x3_halo<C, CO><<<grid, 128, P::SMEM, s>>>(x, ldx, N, H, W, w, b, relu ? 1 : 0, y, ldy, err);
+    DH_CUDA_TRY(cudaGetLastError());
+    return DH_OK;
+}
+
+}  // namespace
+
+// Shallow-layer kernel for the channel pairs it is built for; DH_EINVAL
+// (nothing queued) for any other.
+int conv3x3_halo(const void *x, int ldx, int C, int N, int H, int W, const void *w, const float *b, int Cout,
+                 bool relu, void *y, int ldy, int *err, cudaStream_t s) {
+    if (ldx % 8 || ldy % 8) return DH_EINVAL;
+    const bf16 *X = (const bf16 *)x, *Wt = (const bf16 *)w;
+    bf16 *Y = (bf16 *)y;
+#define DH_HALO(c, co) \
+    if (C == c && Cout == co) return launch_halo<c, co>(X, ldx, N, H, W, Wt, b, relu, Y, ldy, err, s);
+    DH_HALO(16, 32)
+    DH_HALO(32, 32)
+    DH_HALO(96, 32)
+    DH_HALO(32, 64)
+    DH_HALO(64, 64)
+    DH_HALO(64, 32)
+    DH_HALO(32, 96)
+#undef DH_HALO
+    return DH_EINVAL;
+}
+
+namespace {
 }  // namespace
 
 // Tensor-core (tcgen05) 3x3 convolution; C % 16 == 0, Cout % 16 == 0, ldx and

@@ -603,13 +603,18 @@ static bool unet_shape_ok(int base, int N, int H, int W) {
 
 int conv3x3_tc(const void *x, int ldx, int C, int N, int H, int W, const void *w, const float *b, int Cout, bool relu,
                void *y, int ldy, int *err, cudaStream_t s);
+int conv3x3_halo(const void *x, int ldx, int C, int N, int H, int W, const void *w, const float *b, int Cout,
+                 bool relu, void *y, int ldy, int *err, cudaStream_t s);
 
 // tcgen05 kernel when the channel counts allow it (every layer of the
 // network does), else the mma.sync kernel below.
 static int conv_fwd(const bf16 *x, int ldx, int C, int N, int H, int W, const bf16 *w, const float *b, int Cout,
                     bool relu, bf16 *y, int ldy, cudaStream_t s) {
-    if (C % 16 == 0 && Cout % 16 == 0 && ldx % 8 == 0 && ldy % 8 == 0)
+    if (C % 16 == 0 && Cout % 16 == 0 && ldx % 8 == 0 && ldy % 8 == 0) {
+        const int rc = conv3x3_halo(x, ldx, C, N, H, W, w, b, Cout, relu, y, ldy, nullptr, s);
+        if (rc != DH_EINVAL) return rc;  // DH_EINVAL: not one of its channel pairs
         return conv3x3_tc(x, ldx, C, N, H, W, w, b, Cout, relu, y, ldy, nullptr, s);
+    }
     const int M = N * H * W;
     dim3 grid((M + kCBM - 1) / kCBM, (Cout + kCBN - 1) / kCBN);
     if (C % 32 == 0)

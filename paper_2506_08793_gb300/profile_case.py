@@ -23,10 +23,27 @@ def main():
     ap.add_argument("--tol", type=float, default=0.0)
     ap.add_argument("--variant", type=int, default=0, help="sweep variant (0: library default)")
     ap.add_argument("--net", type=int, default=0, help="instead: N images through the warm-start network forward")
+    ap.add_argument("--conv", default="", help="instead: one 3x3 convolution 'C,Cout' on 1 x H x W, --repeat times")
     ap.add_argument("--host-loop", action="store_true",
                     help="queue the sweeps from the host instead of the graph loop (profilers cannot "
                          "see kernels inside a graph with conditional nodes)")
     a = ap.parse_args()
+    if a.conv:
+        from . import _native as N
+
+        C, Cout = (int(v) for v in a.conv.split(","))
+        g = torch.Generator().manual_seed(a.seed)
+        x = (torch.rand(a.H * a.W * C, generator=g) - 0.5).to(torch.bfloat16).cuda()
+        w = ((torch.rand(Cout * 9 * C, generator=g) - 0.5) * 0.1).to(torch.bfloat16).cuda()
+        b = torch.zeros(Cout, device="cuda")
+        y = torch.empty(a.H * a.W * Cout, dtype=torch.bfloat16, device="cuda")
+        for _ in range(a.repeat):
+            rc = N.dh_conv3x3_forward(x, C, C, 1, a.H, a.W, w, b, Cout, 1, y, Cout)
+            if rc:
+                raise SystemExit(f"dh_conv3x3_forward: {rc}")
+        torch.cuda.synchronize()
+        print(f"conv {C}->{Cout} on {a.H}x{a.W} x{a.repeat}: done")
+        return
     if a.net:
         from . import warmstart as WS
 

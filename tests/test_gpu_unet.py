@@ -34,7 +34,13 @@ def host(t):
 
 
 @pytest.mark.parametrize("n,H,W,C,ldx,Cout,relu", [(2, 7, 13, 16, 16, 32, 1), (1, 9, 20, 32, 48, 64, 0),
-                                                   (1, 12, 8, 96, 96, 96, 1), (3, 5, 5, 64, 64, 128, 0)])
+                                                   (1, 12, 8, 96, 96, 96, 1), (3, 5, 5, 64, 64, 128, 0),
+                                                   # the shallow-layer (halo) kernel: every channel pair,
+                                                   # row segments of 128 pixels with ragged ends
+                                                   (1, 3, 200, 96, 96, 32, 1), (2, 4, 130, 32, 32, 32, 0),
+                                                   (1, 5, 129, 64, 64, 64, 1), (1, 6, 140, 64, 80, 32, 0),
+                                                   (1, 4, 257, 32, 32, 96, 1), (1, 2, 128, 16, 16, 32, 1),
+                                                   (2, 3, 64, 32, 40, 64, 0)])
 def test_conv_forward(N, n, H, W, C, ldx, Cout, relu):
     from oracle import unet as U
 
