@@ -20,7 +20,10 @@
 // One cooperative launch runs the whole solve: grid-stride passes over the
 // 3 x H x W elements separated by grid barriers (the last CTA to arrive
 // reduces the per-CTA partial sums in a fixed order and updates the scalars).
-// Every array the launch writes is read through L2 (ld.global.cg).
+// Arrays the launch writes are read with plain L1-cached loads only in the
+// phases after the grid barrier that follows their writing (the barrier's
+// acquire makes the writes visible); the scalars and partial sums go through
+// L2 (ld.global.cg).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -65,7 +68,7 @@ __device__ __forceinline__ float ext(const float *v, int H, int W, int i, int j,
         i = reflect_idx(i, W);
         j = reflect_idx(j, H);
     }
-    return __ldcg(v + (size_t)j * W + i);
+    return __ldca(v + (size_t)j * W + i);
 }
 
 // The iterate is a double-float pair (hi, lo): at eps = 1e-3 the face
@@ -83,7 +86,7 @@ __device__ __forceinline__ Pair ext2(const float *hi, const float *lo, int H, in
         j = reflect_idx(j, H);
     }
     const size_t o = (size_t)j * W + i;
-    return {__ldcg(hi + o), __ldcg(lo + o)};
+    return {__ldca(hi + o), __ldca(lo + o)};
 }
 __device__ __forceinline__ float pdiff(Pair a, Pair b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 
@@ -98,8 +101,8 @@ __device__ __forceinline__ float apply_A(const SiDesc &d, const float *fxc, cons
     const int H = d.H, W = d.W;
     const bool dir = d.dirichlet != 0;
     float a = d.inv_s * v0, dg = d.inv_s;
-    const float Dl = __ldcg(fxc + (size_t)y * (W + 1) + x), Dr = __ldcg(fxc + (size_t)y * (W + 1) + x + 1);
-    const float Du = __ldcg(fyc + (size_t)y * W + x), Dd = __ldcg(fyc + (size_t)(y + 1) * W + x);
+    const float Dl = __ldca(fxc + (size_t)y * (W + 1) + x), Dr = __ldca(fxc + (size_t)y * (W + 1) + x + 1);
+    const float Du = __ldca(fyc + (size_t)y * W + x), Dd = __ldca(fyc + (size_t)(y + 1) * W + x);
     if (x > 0) { a = fmaf(Dl, v0 - get(x - 1, y), a); dg += Dl; } else if (dir) { a = fmaf(Dl, v0, a); dg += Dl; }
     if (x < W - 1) { a = fmaf(Dr, v0 - get(x + 1, y), a); dg += Dr; } else if (dir) { a = fmaf(Dr, v0, a); dg += Dr; }
     if (y > 0) { a = fmaf(Du, v0 - get(x, y - 1), a); dg += Du; } else if (dir) { a = fmaf(Du, v0, a); dg += Du; }
@@ -279,8 +282,8 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
                 // L_n u^n = sum_f D_f (u_i - u_nb) with pair differences;
                 // diag = 1/s + the faces that couple (all four under Dirichlet)
                 const Pair u0 = ext2(xc, lc, H, W, x, y, dir);
-                const float Dl = __ldcg(fxc + (size_t)y * (W + 1) + x), Dr = __ldcg(fxc + (size_t)y * (W + 1) + x + 1);
-                const float Du = __ldcg(fyc + (size_t)y * W + x), Dd = __ldcg(fyc + (size_t)(y + 1) * W + x);
+                const float Dl = __ldca(fxc + (size_t)y * (W + 1) + x), Dr = __ldca(fxc + (size_t)y * (W + 1) + x + 1);
+                const float Du = __ldca(fyc + (size_t)y * W + x), Dd = __ldca(fyc + (size_t)(y + 1) * W + x);
                 float Lu = 0.f, dg = d.inv_s;
                 if (x > 0 || dir) { Lu = fmaf(Dl, pdiff(u0, ext2(xc, lc, H, W, x - 1, y, dir)), Lu); dg += Dl; }
                 if (x < W - 1 || dir) { Lu = fmaf(Dr, pdiff(u0, ext2(xc, lc, H, W, x + 1, y, dir)), Lu); dg += Dr; }
@@ -338,15 +341,15 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
                     float pv, qv;
                     if (k == 0) {
                         const float *pc = pcur + base;
-                        pv = __ldcg(pc + pix);
+                        pv = __ldca(pc + pix);
                         qv = apply_A(d, fxc, fyc, x, y, pv,
-                                     [&](int i, int j) { return __ldcg(pc + (size_t)j * W + i); }, nullptr);
+                                     [&](int i, int j) { return __ldca(pc + (size_t)j * W + i); }, nullptr);
                     } else {
                         const float *zc = d.z + base, *oc = pold + base;
                         const float bt = beta[ch];
                         auto get = [&](int i, int j) {
                             const size_t o = (size_t)j * W + i;
-                            return fmaf(bt, __ldcg(oc + o), __ldcg(zc + o));
+                            return fmaf(bt, __ldca(oc + o), __ldca(zc + o));
                         };
                         pv = get(x, y);
                         pcur[e] = pv;
@@ -451,7 +454,8 @@ int si_grid(int E) {
         cached = per_sm * sms;
         cached_dev = dev;
     }
-    int g = (E + kSiThreads - 1) / kSiThreads;
+    // at least 8 elements per thread: fewer CTAs make the grid barriers cheaper
+    int g = (E + 8 * kSiThreads - 1) / (8 * kSiThreads);
     if (g > cached) g = cached;
     if (g > kSiMaxGrid) g = kSiMaxGrid;
     return g;
