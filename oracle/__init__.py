@@ -52,6 +52,9 @@ class OrParams(ctypes.Structure):
         ("tau", ctypes.c_double),
         ("boundary", ctypes.c_int),
         ("variant", ctypes.c_int),
+        ("dc_scales", ctypes.c_int),
+        ("gf_radius", ctypes.c_int),
+        ("gf_eps", ctypes.c_double),
     ]
 
 
@@ -60,7 +63,8 @@ class OrParams(ctypes.Structure):
 # preset differs only in eps = 1.0 (the paper's eps = 1e-3 breaks its own
 # step-size condition of App. A-A at tau = 0.2).
 PAPER = dict(patch=15, topk_permille=1, omega=0.95, t0=0.1, lambda0=0.5, beta=3.0,
-             eps=1e-3, sigma=2.0, radius=2, tau=0.2, boundary=0, variant=0)
+             eps=1e-3, sigma=2.0, radius=2, tau=0.2, boundary=0, variant=0,
+             dc_scales=1, gf_radius=0, gf_eps=1e-3)
 STABLE = dict(PAPER, eps=1.0)
 
 
@@ -88,6 +92,7 @@ def lib():
             L.or_div.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P]
             L.or_gauss.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P]
             L.or_faces.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P]
+            L.or_guided_filter.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, P]
             L.or_solve.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(OrParams),
                                    ctypes.c_int, ctypes.c_double, P]
             L.or_solve.restype = ctypes.c_int
@@ -131,6 +136,27 @@ def atmospheric_light(I, dc, permille=1):
     idx = ctypes.c_long(-1)
     clamped = lib().or_atmospheric_light(_ptr(I), _ptr(dc), H, W, permille, _ptr(A), ctypes.byref(idx))
     return A, idx.value, bool(clamped)
+
+
+def scale_patches(patch: int, scales: int):
+    """Patch sizes of the multiscale dark channel: patch/2 (odd), patch, 2*patch+1."""
+    if scales == 1:
+        return [patch]
+    return [(patch // 2) | 1, patch, 2 * patch + 1]
+
+
+def dark_channel_ms(I, patch, scales, A):
+    """Mean of the normalised dark channels at the patch sizes of scale_patches."""
+    ds = [dark_channel(I, q, A) for q in scale_patches(patch, scales)]
+    return sum(ds) / len(ds)
+
+
+def guided_filter(g, p, r, eps) -> np.ndarray:
+    g, p = _f64(g), _f64(p)
+    H, W = g.shape
+    q = np.empty_like(g)
+    lib().or_guided_filter(_ptr(g), _ptr(p), H, W, r, eps, _ptr(q))
+    return q
 
 
 def transmission(I, A, td, p: OrParams):
@@ -206,7 +232,7 @@ def dehaze(I, p: OrParams, max_iter: int, tol: float, u0=None):
     I = _f32(I)
     dc = dark_channel(I, p.patch, None)
     A, idx, clamped = atmospheric_light(I, dc, p.topk_permille)
-    td = dark_channel(I, p.patch, A)
+    td = dark_channel_ms(I, p.patch, p.dc_scales, A)
     t, lam, Phi = transmission(I, A, td, p)
     u, n, rho = solve(Phi if u0 is None else u0, Phi, lam, p, max_iter, tol)
     return dict(dc=dc, A=A, a_index=idx, clamped=clamped, td=td, t=t, lam=lam, Phi=Phi,

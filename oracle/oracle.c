@@ -110,13 +110,63 @@ int or_atmospheric_light(const float *I, const double *dc, int H, int W, int per
 
 /* ------------------------------------------------- Sec. II-D and Sec. II-A */
 
+/* mean of v over the (2r+1)x(2r+1) window at (x, y), clipped to the image */
+static double box_mean(const double *v, int H, int W, int x, int y, int r) {
+    const int x0 = x - r < 0 ? 0 : x - r, x1 = x + r >= W ? W - 1 : x + r;
+    const int y0 = y - r < 0 ? 0 : y - r, y1 = y + r >= H ? H - 1 : y + r;
+    double s = 0.0;
+    for (int j = y0; j <= y1; ++j)
+        for (int i = x0; i <= x1; ++i) s += v[(long)j * W + i];
+    return s / (double)((x1 - x0 + 1) * (y1 - y0 + 1));
+}
+
+void or_guided_filter(const double *g, const double *p, int H, int W, int r, double eps, double *q) {
+    const long N = (long)H * W;
+    double *gp = (double *)malloc(sizeof(double) * (size_t)N), *gg = (double *)malloc(sizeof(double) * (size_t)N);
+    double *a = (double *)malloc(sizeof(double) * (size_t)N), *b = (double *)malloc(sizeof(double) * (size_t)N);
+    for (long i = 0; i < N; ++i) {
+        gp[i] = g[i] * p[i];
+        gg[i] = g[i] * g[i];
+    }
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const double mg = box_mean(g, H, W, x, y, r), mp = box_mean(p, H, W, x, y, r);
+            const double cov = box_mean(gp, H, W, x, y, r) - mg * mp;
+            const double var = box_mean(gg, H, W, x, y, r) - mg * mg;
+            const long i = (long)y * W + x;
+            a[i] = cov / (var + eps);
+            b[i] = mp - a[i] * mg;
+        }
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const long i = (long)y * W + x;
+            q[i] = box_mean(a, H, W, x, y, r) * g[i] + box_mean(b, H, W, x, y, r);
+        }
+    free(gp);
+    free(gg);
+    free(a);
+    free(b);
+}
+
 void or_transmission(const float *I, const double A[3], const double *td, int H, int W,
                      const or_params *p, double *t, double *lam, double *Phi) {
     const long N = (long)H * W;
+    for (long i = 0; i < N; ++i) t[i] = 1.0 - p->omega * td[i];
+    if (p->gf_radius > 0) {
+        double *g = (double *)malloc(sizeof(double) * (size_t)N), *t0 = (double *)malloc(sizeof(double) * (size_t)N);
+        for (long i = 0; i < N; ++i) {
+            g[i] = (((double)I[i] + (double)I[N + i]) + (double)I[2 * N + i]) / 3.0;
+            t0[i] = t[i];
+        }
+        or_guided_filter(g, t0, H, W, p->gf_radius, p->gf_eps, t);
+        free(g);
+        free(t0);
+    }
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < N; ++i) {
-        const double ti = 1.0 - p->omega * td[i];
-        t[i] = ti;
+        const double ti = t[i];
         lam[i] = p->lambda0 * exp(-p->beta * (1.0 - ti));
         if (p->variant & 1) lam[i] = p->lambda0; /* w/o adaptive regularisation */
         if (p->variant & 4) lam[i] = 0.0;        /* w/o nonlocal regularisation */

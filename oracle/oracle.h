@@ -25,6 +25,8 @@
  *   boundary = 1 / variant  pinned (scipy zero-padded gaussian_filter and laplace;
  *                          D == 1 is the 5-point Laplacian; lambda ablations)
  *   or_faces               pinned (the frozen operator applied to u equals -or_div(u))
+ *   or_guided_filter       pinned (scipy uniform_filter composition, constant input, eps -> infinity,
+ *                          linear guide)
  */
 #ifndef DEHAZE_ORACLE_H
 #define DEHAZE_ORACLE_H
@@ -46,6 +48,11 @@ typedef struct {
     double tau;            /* relaxation parameter, App. A-A: 0.2 */
     int    boundary;       /* 0: half-sample reflection (zero flux); 1: u = 0 outside (H^1_0, Sec. III) */
     int    variant;        /* ablations of Sec. IV-E: 1 lambda == lambda0, 2 D == 1, 4 lambda == 0 */
+    int    dc_scales;      /* 1: one patch; 3: mean of the normalised dark channels at patch/2|1, patch,
+                              2*patch+1 (the "multiscale dark channel" of Sec. IV-E; used by the Python
+                              composition, not by the C functions) */
+    int    gf_radius;      /* > 0: guided-filter refinement of t (Sec. IV-E "guided filter") */
+    double gf_eps;         /* its regularisation */
 } or_params;
 
 /* Sec. II-D dark channel: out(x) = min_c min_{y in Omega(x)} I^c(y)/A^c over a
@@ -63,9 +70,19 @@ int or_atmospheric_light(const float *I, const double *dc, int H, int W, int per
                          double A[3], long *index);
 
 /* Sec. II-D and II-A: t = 1 - omega*td, lambda = lambda0*exp(-beta*(1-t)),
- * Phi^c = (I^c - A^c (1-t)) / max(t, t0).  t, lam: HxW; Phi: 3xHxW. */
+ * Phi^c = (I^c - A^c (1-t)) / max(t, t0).  t, lam: HxW; Phi: 3xHxW.
+ * With p->gf_radius > 0, t is first refined by or_guided_filter with the
+ * gray guide g = ((I^R + I^G) + I^B) / 3 (t, lambda and Phi then use it). */
 void or_transmission(const float *I, const double A[3], const double *td, int H, int W,
                      const or_params *p, double *t, double *lam, double *Phi);
+
+/* The guided filter of He, Sun and Tang (the paper names it in Sec. IV-E
+ * without defining it): with mean_r(v)(x) the average of v over the
+ * (2r+1)x(2r+1) window around x clipped to the image,
+ *   a = (mean(g p) - mean(g) mean(p)) / (mean(g g) - mean(g)^2 + eps),
+ *   b = mean(p) - a mean(g),   q = mean(a) g + mean(b).
+ * g, p, q: HxW. */
+void or_guided_filter(const double *g, const double *p, int H, int W, int r, double eps, double *q);
 
 /* App. A-B-2: the 2*radius+1 normalised 1-D Gaussian weights. */
 void or_gauss_weights(double sigma, int radius, double *w);
