@@ -97,6 +97,14 @@ typedef struct dh_params {
     int sweep_variant;  /* sweep kernel variant (1..dh_sweep_variants()-1); 0 = the
                            tuned choice for this shape if dh_tune ran, else default */
     int boundary;       /* DH_BOUNDARY_* for the flux stencil and the Gaussian */
+    /* Front-end refinements the Sec. IV-E ablation names ("multiscale dark
+     * channel", "guided filter") without defining them; both off by default.
+     * They need workspace (dh_workspace_bytes accounts for them). */
+    int dc_scales;      /* 1: one patch; 3: t_d = mean of the normalised dark channels at
+                           patch sizes patch/2 (odd), patch and 2*patch+1 (patch <= 15) */
+    int gf_radius;      /* 0: off; 1..24: t refined by the guided filter (He et al.) with
+                           the gray guide (I^R + I^G + I^B)/3 over (2r+1)^2 windows */
+    float gf_eps;       /* its regularisation (default 1e-3) */
 } dh_params;
 
 typedef struct dh_report {
@@ -151,6 +159,14 @@ int dh_atmospheric_light(const float *I, const float *dc, int H, int W, int topk
  * t, lam: HxW; Phi: 3xHxW; td may be NULL. */
 int dh_transmission(const float *I, const float *A, int H, int W, const dh_params *p,
                     float *td, float *t, float *lam, float *Phi, void *stream);
+
+/* dh_transmission with the front-end refinements of p (dc_scales = 3: t_d is
+ * the mean of the three normalised dark channels; gf_radius > 0: t is refined
+ * by the guided filter before lambda and Phi; window sums in FP64), which
+ * need scratch: workspace of dh_workspace_bytes(H, W, p) bytes, 256-byte
+ * aligned (dh_transmission itself returns DH_EINVAL for those parameters). */
+int dh_transmission_ws(const float *I, const float *A, int H, int W, const dh_params *p, float *td, float *t,
+                       float *lam, float *Phi, void *workspace, size_t workspace_bytes, void *stream);
 
 /* App. A-A fixed-point iteration, per channel, from u (in: u^0, out: u^n):
  *   F(u) = div(D(grad u) grad u) - lambda G(u) + Phi   (App. A-B-1, A-B-2)

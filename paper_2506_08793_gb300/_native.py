@@ -34,7 +34,7 @@ EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes
            "dh_unet_forward", "dh_unet_backward", "dh_unet_adam", "dh_warm_start", "dh_warm_target",
            "dh_conv3x3_forward",
            "dh_conv3x3_backward_weights", "dh_dehaze_warm", "dh_atmospheric_light_noalloc",
-           "dh_semi_implicit_workspace_bytes", "dh_semi_implicit")
+           "dh_semi_implicit_workspace_bytes", "dh_semi_implicit", "dh_transmission_ws")
 
 
 class DhParams(ctypes.Structure):
@@ -57,6 +57,9 @@ class DhParams(ctypes.Structure):
         ("use_graph", ctypes.c_int),
         ("sweep_variant", ctypes.c_int),
         ("boundary", ctypes.c_int),
+        ("dc_scales", ctypes.c_int),
+        ("gf_radius", ctypes.c_int),
+        ("gf_eps", ctypes.c_float),
     ]
 
     def replace(self, **kw) -> "DhParams":
@@ -155,6 +158,7 @@ def lib(build_if_missing: bool = True):
             "dh_conv3x3_backward_weights": ([P, I, I, P, I, I, I, I, I, P, P, P, S, P], I),
             "dh_dehaze_warm": ([P, I, P, I, I, PP, P, P, P, P, P, S, P, S, P, PR], I),
             "dh_semi_implicit_workspace_bytes": ([I, I], S),
+            "dh_transmission_ws": ([P, P, I, I, PP, P, P, P, P, P, S, P], I),
             "dh_semi_implicit": ([P, P, P, P, I, I, PP, ctypes.c_float, I, P, P, P, S, P, PR], I),
         }
         for name, (args, res) in sig.items():
@@ -219,6 +223,11 @@ def dh_atmospheric_light(I, dc, H, W, topk_permille, A_out, index_out, workspace
 def dh_transmission(I, A, H, W, p: DhParams, td, t, lam, Phi, stream=None) -> int:
     return lib().dh_transmission(_p(I), _p(A), H, W, ctypes.byref(p), _p(td), _p(t), _p(lam), _p(Phi),
                                  _stream(stream))
+
+
+def dh_transmission_ws(I, A, H, W, p: DhParams, td, t, lam, Phi, workspace, workspace_bytes, stream=None) -> int:
+    return lib().dh_transmission_ws(_p(I), _p(A), H, W, ctypes.byref(p), _p(td), _p(t), _p(lam), _p(Phi),
+                                    _p(workspace), workspace_bytes, _stream(stream))
 
 
 def dh_fixed_point(u, Phi, lam, H, W, p: DhParams, rho_hist, workspace, workspace_bytes, stream=None,

@@ -76,7 +76,12 @@ def transmission(I: torch.Tensor, A: torch.Tensor, p: DhParams | None = None, st
     t = torch.empty_like(td)
     lam = torch.empty_like(td)
     Phi = torch.empty_like(I)
-    _check(N.dh_transmission(I, A, H, W, p, td, t, lam, Phi, _stream(stream)), "dh_transmission")
+    if p.dc_scales > 1 or p.gf_radius > 0:  # the refinements need workspace
+        ws = workspace(H, W, p, I.device)
+        _check(N.dh_transmission_ws(I, A, H, W, p, td, t, lam, Phi, ws, ws.numel(), _stream(stream)),
+               "dh_transmission_ws")
+    else:
+        _check(N.dh_transmission(I, A, H, W, p, td, t, lam, Phi, _stream(stream)), "dh_transmission")
     return td, t, lam, Phi
 
 

@@ -11,7 +11,7 @@ namespace dh {
 int launch_dark_channel(const float *I, int H, int W, int patch, const float *A, float *out,
                         cudaStream_t s);
 int launch_transmission(const float *I, int H, int W, const dh_params *p, const float *A, float *td,
-                        float *t, float *lam, float *phi, float *u0, float2 *phin_part,
+                        float *t, float *lam, float *phi, float *u0, float2 *phin_part, void *scratch,
                         cudaStream_t s);
 int launch_phin(const float *phi, int H, int W, float2 *part, SolveState *st, cudaStream_t s);
 int launch_phin_final(const float2 *part, int H, int W, SolveState *st, cudaStream_t s);
@@ -55,12 +55,15 @@ static bool params_ok(const dh_params *p) {
     if (p->variant & ~(DH_VAR_NO_ADAPTIVE | DH_VAR_NO_EDGE | DH_VAR_NO_NONLOCAL)) return false;
     if (p->sweep_variant < 0 || p->sweep_variant >= sweep_variant_count()) return false;
     if (p->boundary != DH_BOUNDARY_REFLECT && p->boundary != DH_BOUNDARY_ZERO) return false;
+    if (p->dc_scales != 1 && !(p->dc_scales == 3 && p->patch <= 15)) return false;
+    if (p->gf_radius < 0 || p->gf_radius > 24) return false;
+    if (p->gf_radius > 0 && (!(p->gf_eps > 0.f) || !std::isfinite(p->gf_eps))) return false;
     return true;
 }
 
 static WsLayout layout_for(int H, int W, const dh_params *p) {
     const int depth = sweep_depth(p);
-    return ws_layout(H, W, depth, sweep_tile_h(depth));
+    return ws_layout(H, W, depth, sweep_tile_h(depth), refine_bytes(H, W, p));
 }
 
 static int ws_ok(const void *ws, size_t bytes, const WsLayout &L) {
@@ -131,6 +134,9 @@ int dh_params_default(dh_params *p, int preset) {
     p->use_graph = 1;
     p->sweep_variant = 0;
     p->boundary = DH_BOUNDARY_REFLECT;
+    p->dc_scales = 1;
+    p->gf_radius = 0;
+    p->gf_eps = 1e-3f;
     return DH_OK;
 }
 
@@ -193,7 +199,17 @@ int dh_atmospheric_light(const float *I, const float *dc, int H, int W, int topk
 int dh_transmission(const float *I, const float *A, int H, int W, const dh_params *p, float *td, float *t,
                     float *lam, float *Phi, void *stream) {
     if (!I || !A || !shape_ok(H, W) || !params_ok(p)) return DH_EINVAL;
-    return launch_transmission(I, H, W, p, A, td, t, lam, Phi, nullptr, nullptr, (cudaStream_t)stream);
+    return launch_transmission(I, H, W, p, A, td, t, lam, Phi, nullptr, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int dh_transmission_ws(const float *I, const float *A, int H, int W, const dh_params *p, float *td, float *t,
+                       float *lam, float *Phi, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!I || !A || !t || !lam || !Phi || !shape_ok(H, W) || !params_ok(p)) return DH_EINVAL;
+    const WsLayout L = layout_for(H, W, p);
+    const int rc = ws_ok(workspace, workspace_bytes, L);
+    if (rc) return rc;
+    return launch_transmission(I, H, W, p, A, td, t, lam, Phi, nullptr, nullptr, (char *)workspace + L.refine,
+                               (cudaStream_t)stream);
 }
 
 static void fill_solve_report(dh_report *r, const SolveState &st, int launches, bool graph) {
@@ -251,7 +267,7 @@ int dh_dehaze(const float *I, int H, int W, const dh_params *p, const float *u0,
     rc = launch_select_A(I, dc, H, W, p->topk_permille, A, nullptr, ws, L, s);
     if (rc) return rc;
     rc = launch_transmission(I, H, W, p, A, nullptr, t, lam, phi, u0 ? nullptr : u,
-                             (float2 *)(ws + L.phin_part), s);
+                             (float2 *)(ws + L.phin_part), ws + L.refine, s);
     if (rc) return rc;
     if (u0) DH_CUDA_TRY(cudaMemcpyAsync(u, u0, (size_t)3 * H * W * sizeof(float), cudaMemcpyDeviceToDevice, s));
     rc = launch_phin_final((const float2 *)(ws + L.phin_part), H, W, (SolveState *)(ws + L.state), s);

@@ -14,7 +14,7 @@ namespace dh {
 
 int launch_dark_channel(const float *I, int H, int W, int patch, const float *A, float *out, cudaStream_t s);
 int launch_transmission(const float *I, int H, int W, const dh_params *p, const float *A, float *td, float *t,
-                        float *lam, float *phi, float *u0, float2 *phin_part, cudaStream_t s);
+                        float *lam, float *phi, float *u0, float2 *phin_part, void *scratch, cudaStream_t s);
 int launch_phin_final(const float2 *part, int H, int W, SolveState *st, cudaStream_t s);
 int launch_select_A(const float *I, const float *dc, int H, int W, int permille, float *A,
                     long long *index_out, char *ws, const WsLayout &L, cudaStream_t s);
@@ -49,9 +49,11 @@ struct BatchLayout {
     std::vector<size_t> off;  // per-image workspace offsets
 };
 
-static WsLayout img_layout(int H, int W) { return ws_layout(H, W, 1, sweep_tile_h(1)); }
+static WsLayout img_layout(int H, int W, const dh_params *p) {
+    return ws_layout(H, W, 1, sweep_tile_h(1), refine_bytes(H, W, p));
+}
 
-static BatchLayout batch_layout(int n, const dh_image *im) {
+static BatchLayout batch_layout(int n, const dh_image *im, const dh_params *p) {
     BatchLayout B;
     size_t o = 0;
     B.hdr = o; o = align_up(o + sizeof(BatchHdr));
@@ -59,7 +61,7 @@ static BatchLayout batch_layout(int n, const dh_image *im) {
     B.img0 = o;
     for (int i = 0; i < n; ++i) {
         B.off.push_back(o);
-        o = align_up(o + img_layout(im[i].H, im[i].W).total);
+        o = align_up(o + img_layout(im[i].H, im[i].W, p).total);
     }
     B.total = o;
     return B;
@@ -407,7 +409,7 @@ size_t dh_batch_workspace_bytes(int n, const dh_image *imgs, const dh_params *p)
     for (int i = 0; i < n; ++i)
         if (!shape_ok(imgs[i].H, imgs[i].W)) return 0;
     if (dh_workspace_bytes(1, 1, p) == 0) return 0;
-    return batch_layout(n, imgs).total;
+    return batch_layout(n, imgs, p).total;
 }
 
 int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *workspace, size_t workspace_bytes,
@@ -416,7 +418,7 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
     if (dh_workspace_bytes(1, 1, p) == 0 || p->storage != DH_STORE_F32) return DH_EINVAL;
     for (int i = 0; i < n; ++i)
         if (!image_ok(imgs[i])) return DH_EINVAL;
-    const BatchLayout B = batch_layout(n, imgs);
+    const BatchLayout B = batch_layout(n, imgs, p);
     if (!workspace || ((uintptr_t)workspace % kAlign) || workspace_bytes < B.total) return DH_EWORKSPACE;
     char *ws = (char *)workspace;
     cudaStream_t s = (cudaStream_t)stream;
@@ -432,12 +434,12 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
     for (int i = 0; i < n; ++i) {
         const dh_image &m = imgs[i];
         char *iw = ws + B.off[i];
-        const WsLayout L = img_layout(m.H, m.W);
+        const WsLayout L = img_layout(m.H, m.W, p);
         float *dc = (float *)(iw + L.dc), *lam = (float *)(iw + L.lam), *phi = (float *)(iw + L.phi);
         int rc = launch_dark_channel(m.I, m.H, m.W, p->patch, nullptr, dc, s);
         if (!rc) rc = launch_select_A(m.I, dc, m.H, m.W, p->topk_permille, m.A, nullptr, iw, L, s);
         if (!rc) rc = launch_transmission(m.I, m.H, m.W, p, m.A, nullptr, m.t, lam, phi, m.u0 ? nullptr : m.u,
-                                          (float2 *)(iw + L.phin_part), s);
+                                          (float2 *)(iw + L.phin_part), iw + L.refine, s);
         if (rc) return rc;
         if (m.u0)
             DH_CUDA_TRY(cudaMemcpyAsync(m.u, m.u0, (size_t)3 * m.H * m.W * sizeof(float), cudaMemcpyDeviceToDevice, s));
@@ -529,7 +531,7 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
     for (int i = 0; i < n; ++i) {
         SolveState st;
         SelectState sel;
-        const WsLayout L = img_layout(imgs[i].H, imgs[i].W);
+        const WsLayout L = img_layout(imgs[i].H, imgs[i].W, p);
         DH_CUDA_TRY(cudaMemcpy(&st, ws + B.off[i] + L.state, sizeof(st), cudaMemcpyDeviceToHost));
         DH_CUDA_TRY(cudaMemcpy(&sel, ws + B.off[i] + L.sel, sizeof(sel), cudaMemcpyDeviceToHost));
         dh_report &r = reports[i];

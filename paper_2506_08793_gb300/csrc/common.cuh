@@ -87,7 +87,7 @@ struct SelectState {
 };
 
 struct WsLayout {
-    size_t state, desc, sel, hist, blk, phin_part, part, dc, lam, phi, ub, total;
+    size_t state, desc, sel, hist, blk, phin_part, part, dc, lam, phi, ub, refine, total;
     int nblk_sweep, nblk_dcp, nblk_sel, depth, tile_h;
 };
 
@@ -99,7 +99,11 @@ int dcp_blocks(int H, int W);
 constexpr int kSelBlocks = 1024;
 
 // Layout of the caller's workspace for an HxW image.
-static inline WsLayout ws_layout(int H, int W, int depth, int tile_h) {
+// Scratch of the front-end refinements (multiscale dark channel, guided
+// filter) for these parameters; 0 when both are off.
+size_t refine_bytes(int H, int W, const dh_params *p);
+
+static inline WsLayout ws_layout(int H, int W, int depth, int tile_h, size_t refine = 0) {
     WsLayout L;
     const size_t N = (size_t)H * W;
     L.depth = depth;
@@ -121,6 +125,7 @@ static inline WsLayout ws_layout(int H, int W, int depth, int tile_h) {
     L.lam = o; o = align_up(o + N * sizeof(float));
     L.phi = o; o = align_up(o + 3 * N * sizeof(float));
     L.ub = o; o = align_up(o + 3 * N * sizeof(float) + kAlign);  // f32 buffer, or two 16-bit ones
+    L.refine = o; o = align_up(o + refine);
     L.total = o;
     return L;
 }

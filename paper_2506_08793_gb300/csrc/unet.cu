@@ -656,7 +656,7 @@ namespace dh {
 
 int launch_dark_channel(const float *I, int H, int W, int patch, const float *A, float *out, cudaStream_t s);
 int launch_transmission(const float *I, int H, int W, const dh_params *p, const float *A, float *td, float *t,
-                        float *lam, float *phi, float *u0, float2 *phin_part, cudaStream_t s);
+                        float *lam, float *phi, float *u0, float2 *phin_part, void *scratch, cudaStream_t s);
 int launch_phin(const float *phi, int H, int W, float2 *part, SolveState *st, cudaStream_t s);
 int launch_select_A(const float *I, const float *dc, int H, int W, int permille, float *A,
                     long long *index_out, char *ws, const WsLayout &L, cudaStream_t s);
@@ -910,7 +910,7 @@ int dh_dehaze_warm(const float *params, int base, const float *I, int H, int W, 
     if (!params || !I || !J || !u || !t || !A || !p || !shape_ok(H, W) || !unet_shape_ok(base, 1, H, W))
         return DH_EINVAL;
     if (dh_workspace_bytes(H, W, p) == 0) return DH_EINVAL;
-    const WsLayout WL = ws_layout(H, W, sweep_depth(p), sweep_tile_h(sweep_depth(p)));
+    const WsLayout WL = ws_layout(H, W, sweep_depth(p), sweep_tile_h(sweep_depth(p)), refine_bytes(H, W, p));
     if (!workspace || ((uintptr_t)workspace % kAlign) || workspace_bytes < WL.total) return DH_EWORKSPACE;
     const NetLayout NL = net_layout(base, 1, H, W, false);
     if (!net_workspace || ((uintptr_t)net_workspace % kAlign) || net_workspace_bytes < NL.total) return DH_EWORKSPACE;
@@ -927,7 +927,7 @@ int dh_dehaze_warm(const float *params, int base, const float *I, int H, int W, 
     float *dc = (float *)(ws + WL.dc), *lam = (float *)(ws + WL.lam), *phi = (float *)(ws + WL.phi);
     RUN(launch_dark_channel(I, H, W, p->patch, nullptr, dc, s));
     RUN(launch_select_A(I, dc, H, W, p->topk_permille, A, nullptr, ws, WL, s));
-    RUN(launch_transmission(I, H, W, p, A, nullptr, t, lam, phi, nullptr, nullptr, s));
+    RUN(launch_transmission(I, H, W, p, A, nullptr, t, lam, phi, nullptr, nullptr, ws + WL.refine, s));
     RUN(launch_phin(phi, H, W, (float2 *)(ws + WL.phin_part), (SolveState *)(ws + WL.state), s));
     char *nws = (char *)net_workspace;
     RUN(net_forward(params, base, I, t, A, phi, 1, H, W, nws, NL, false, s));

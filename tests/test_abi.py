@@ -36,8 +36,8 @@ def test_exports_every_declared_symbol(L):
 
 
 def test_struct_sizes_match_header():
-    # dh_params: 18 4-byte fields; dh_report: 2 ints, 6 floats, long long, 2 floats, int (+pad)
-    assert ctypes.sizeof(N.DhParams) == 72
+    # dh_params: 21 4-byte fields; dh_report: 2 ints, 6 floats, long long, 2 floats, int (+pad)
+    assert ctypes.sizeof(N.DhParams) == 84
     assert ctypes.sizeof(N.DhReport) == 56
 
 
@@ -114,3 +114,18 @@ def test_semi_implicit_arguments_rejected_on_host():
     assert N.dh_semi_implicit(*args, p, 2.0, 16, None, None, fake, b - 1) == N.DH_EWORKSPACE
     assert N.dh_semi_implicit(*args, p, 2.0, 16, None, None, fake + 8, b) == N.DH_EWORKSPACE
     assert N.dh_semi_implicit(None, None, fake, fake, 64, 96, p, 2.0, 16, None, None, fake, b) == N.DH_EINVAL
+
+
+def test_refinement_parameters_validated_on_host():
+    p = N.dh_params_default(N.DH_PRESET_STABLE)
+    fake = 1 << 20  # never dereferenced
+    assert N.dh_workspace_bytes(64, 64, p.replace(dc_scales=2)) == 0
+    assert N.dh_workspace_bytes(64, 64, p.replace(dc_scales=3, patch=17)) == 0
+    assert N.dh_workspace_bytes(64, 64, p.replace(gf_radius=25)) == 0
+    assert N.dh_workspace_bytes(64, 64, p.replace(gf_radius=4, gf_eps=0.0)) == 0
+    plain = N.dh_workspace_bytes(64, 64, p)
+    assert N.dh_workspace_bytes(64, 64, p.replace(dc_scales=3, gf_radius=4)) > plain
+    # the workspace-free call cannot hold the refinements' scratch
+    assert N.dh_transmission(fake, fake, 8, 8, p.replace(gf_radius=4), None, fake, fake, fake) == N.DH_EINVAL
+    assert N.dh_transmission_ws(fake, fake, 8, 8, p.replace(gf_radius=4), None, fake, fake, fake, None, 0) == \
+        N.DH_EWORKSPACE
