@@ -215,7 +215,8 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
                 break;
             }
             // reflect the halo cells that fall outside the image (TMA filled zeros,
-            // which is already the Dirichlet boundary)
+            // which is already the Dirichlet boundary); interior tiles need no
+            // barrier here: the one above already ordered the landed tile
             if (!dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + TH + 2 > H)) {
                 for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
                     const int r = e / SW, q = e - r * SW;
@@ -229,8 +230,8 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
                     }
                 }
                 fence_proxy_async_smem();  // these writes precede the stage's next TMA load
+                __syncthreads();
             }
-            __syncthreads();
 
             T *__restrict__ un = ubase + c * N;
             const int x = x0 + 4 * lane;
@@ -263,7 +264,10 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             };
             walk_rows<R, SW, T, EDGE>(s, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
 
-            const float2 tot = block_pair_sum<NW>(rs, rc, red);  // ends with a barrier
+            // every thread is past its walk once block_pair_sum's barrier is
+            // passed, so the stage can be refilled; red[] is rewritten only after
+            // the next item's wait barrier, which every reader of it reaches first
+            const float2 tot = block_pair_sum<NW>(rs, rc, red);
             if (threadIdx.x == 0) {
                 part[(size_t)c * nblk + tile] = tot;
                 if (j + STAGES < m) {
@@ -271,7 +275,6 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
                     issue(j + STAGES, stage);
                 }
             }
-            __syncthreads();  // red[] reuse
         }
         if (failed) {
             // let every load already issued land (bounded) before going on
@@ -1101,6 +1104,7 @@ static const SweepCfg kVariants[] = {
     {4, 4, 1, 4, true, 0, 1}, {6, 4, 1, 4, true, 0, 1},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+constexpr int kTb2Variant = 31;  // the two-iteration sweep with 120 x 16 tiles
 
 int sweep_variant_count() { return kNumVariants; }
 bool sweep_variant_usable(int v, int W, bool aligned) {
@@ -1148,6 +1152,10 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
     if (v <= 0) {
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) v = tune_get(dev, H, W, p->storage);
+        // tb_depth: iterations per tile load requested by the caller
+        const bool two = v > 0 && v < kNumVariants && kVariants[v].tma == 4;
+        if (p->tb_depth == 2 && !two) v = kTb2Variant;
+        if (p->tb_depth == 1 && two) v = 0;
     }
     if (p->boundary == DH_BOUNDARY_ZERO && v > 0 && v < kNumVariants && kVariants[v].tma == 3) v = 0;
     if (v > 0 && v < kNumVariants && (kVariants[v].tma == 0 || tma_ok)) {

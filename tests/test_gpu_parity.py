@@ -360,3 +360,15 @@ def test_full_size(N, api, orc, H, W, seed):
         rep2 = d2(Id)
         assert rep2.n_iter == rep.n_iter
         assert torch.equal(d2.u, dz.u)
+
+
+def test_transpose_equivariance(N, api):
+    """The scheme is transpose-equivariant (R11: the tangential difference of an
+    x-face is taken at its left cell, of a y-face at its lower cell): dehazing
+    I^T gives u^T, to float32 rounding, on a scene without ties for A."""
+    I = scenes.hazy_scene(4711, 72, 104)["I"]
+    a = api.dehaze(dev(I), api.params("stable", tol=0.0, max_iter=60))
+    b = api.dehaze(dev(np.ascontiguousarray(I.transpose(0, 2, 1))), api.params("stable", tol=0.0, max_iter=60))
+    ua, ub = host(a["u"]), host(b["u"])
+    assert np.array_equal(host(a["A"]), host(b["A"]))
+    assert np.max(np.abs(ua - ub.transpose(0, 2, 1)) / np.maximum(1.0, np.abs(ua))) <= 1e-5

@@ -139,3 +139,15 @@ def test_launch_count(api, orc):
     # two iterations per step while n + 1 < max_iter
     loop_steps = 300 // 2 + 1
     assert rep.launches == 4 + (loop_steps + 63) // 64
+
+
+def test_tb_depth_parameter_selects_the_sweep(api, orc):
+    """tb_depth = 2 asks for two iterations per tile load (the 120 x 16
+    variant), tb_depth = 1 for one (the library default) whatever was tuned."""
+    _, Phi, lam = problem(orc, 8808, 64, 128)
+    two = run(api, Phi, lam, 0, tol=0.0, max_iter=21, tb_depth=2)
+    ref2 = run(api, Phi, lam, TB2[0], tol=0.0, max_iter=21)
+    assert np.array_equal(two[1], ref2[1])
+    one = run(api, Phi, lam, 0, tol=0.0, max_iter=21, tb_depth=1)
+    ref1 = run(api, Phi, lam, 26, tol=0.0, max_iter=21)  # the default variant's configuration
+    assert rel(one[1], ref1[1]) <= 1e-6 and one[0].n_iter == 21
