@@ -997,9 +997,9 @@ static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge, in
 #define DH_STM(r, nw, st, pls, mb) DH_STX(r, nw, st, pls, mb, false)
 #define DH_ST(r, nw, st, pls) DH_STM(r, nw, st, pls, 0)
     DH_ST(8, 4, 1, true)
+    DH_STX(6, 4, 1, true, 5, true)
     if (sizeof(T) == 4) {
         DH_STX(8, 4, 1, true, 0, true)
-        DH_STX(6, 4, 1, true, 5, true)
         DH_STX(4, 4, 1, true, 6, true)
         DH_STX(6, 4, 1, true, 0, true)
         DH_STX(4, 4, 2, true, 0, true)
@@ -1143,8 +1143,9 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
     const bool edge = !(p->variant & DH_VAR_NO_EDGE);
     SweepCfg c = kVariants[0];
     c.edge = edge;
-    if (is16) {  // 16-bit storage: one tiling, single-iteration launches
-        c = SweepCfg{8, 4, 1, tma_ok ? 1 : 0, edge};
+    if (is16) {  // 16-bit storage: the default multi-iteration tiling (variant 1: single-iteration)
+        if (tma_ok && p->sweep_variant != 1) c = SweepCfg{6, 4, 1, 1, edge, 5, 1};
+        else c = SweepCfg{8, 4, 1, tma_ok ? 1 : 0, edge};
         return c;
     }
     if (!tma_ok) c.tma = 0;
