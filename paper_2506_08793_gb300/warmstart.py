@@ -60,26 +60,34 @@ class WarmStartNet:
         return self._ws[key]
 
     def train(self, data: dict, steps: int, batch: int = 8, lr: float = 1e-3, lr_end: float = 1e-4,
-              log_every: int = 50) -> list:
+              log_every: int = 50, total_steps: int | None = None, seed: int = 12345) -> list:
         """Adam on mean((y - y*)^2); learning rate decays geometrically from
-        lr to lr_end.  Batches cycle through the data in a fixed order."""
+        lr to lr_end over total_steps (default: steps).  Batches cycle through
+        the data in a fixed order.  The Adam moments and the step count persist
+        across calls, so a run can go on with new data (chunked training)."""
         n, _, H, W = data["I"].shape
+        total = total_steps or steps
         grads = torch.empty_like(self.params)
-        m = torch.zeros_like(self.params)
-        v = torch.zeros_like(self.params)
+        if not hasattr(self, "_m"):
+            self._m = torch.zeros_like(self.params)
+            self._v = torch.zeros_like(self.params)
+            self._step = 0
         loss = torch.empty(1, device=self.dev)
         ws = self._workspace(batch, H, W, True)
         log = []
-        order = np.random.default_rng(12345).permutation(n)
+        order = np.random.default_rng(seed).permutation(n)
         s = api._stream(None)
-        for step in range(1, steps + 1):
-            idx = torch.from_numpy(order[[(step * batch + k) % n for k in range(batch)]]).to(self.dev)
-            b = {k: data[k].index_select(0, idx).contiguous() for k in ("I", "t", "A", "Phi", "y")}
+        for k in range(1, steps + 1):
+            self._step += 1
+            step = self._step
+            idx = torch.from_numpy(order[[(k * batch + j) % n for j in range(batch)]]).to(self.dev)
+            b = {key: data[key].index_select(0, idx).contiguous() for key in ("I", "t", "A", "Phi", "y")}
             api._check(N.dh_unet_backward(self.params, self.base, b["I"], b["t"], b["A"], b["Phi"], b["y"], batch, H,
                                           W, grads, loss, ws, ws.numel(), s), "dh_unet_backward")
-            rate = lr * (lr_end / lr) ** ((step - 1) / max(1, steps - 1))
-            api._check(N.dh_unet_adam(self.params, grads, m, v, self.n, rate, 0.9, 0.999, 1e-8, step, s), "dh_unet_adam")
-            if step % log_every == 0 or step == 1 or step == steps:
+            rate = lr * (lr_end / lr) ** (min(step - 1, total - 1) / max(1, total - 1))
+            api._check(N.dh_unet_adam(self.params, grads, self._m, self._v, self.n, rate, 0.9, 0.999, 1e-8, step, s),
+                       "dh_unet_adam")
+            if k % log_every == 0 or k == 1 or k == steps:
                 log.append((step, float(loss.item())))
         return log
 
@@ -154,3 +162,48 @@ def evaluate(net: WarmStartNet | None, seeds, H: int, W: int, p=None, repeats: i
             summ[name] = {"mean_iter": float(np.mean([r[name]["n_iter"] for r in rows])),
                           "mean_ms": float(np.mean([r[name]["ms"] for r in rows]))}
     return {"images": rows, "summary": summ}
+
+
+def train_chunked(pairs: int, size: int, chunk: int, epochs: float = 1.0, batch: int = 8, base: int = 32,
+                  lr: float = 1e-3, lr_end: float = 5e-5, seed0: int = 5_000_000, p=None) -> tuple:
+    """Training on `pairs` solver-generated size x size scenes (seeds seed0 + i),
+    generated and consumed `chunk` at a time so the set need not fit in
+    memory; `epochs` passes over each chunk.  Returns (net, log, seconds)."""
+    p = p or api.params("stable")
+    net = WarmStartNet(base, seed=1)
+    steps_per_chunk = max(1, int(round(epochs * chunk / batch)))
+    nchunks = (pairs + chunk - 1) // chunk
+    total = steps_per_chunk * nchunks
+    log = []
+    t0 = time.perf_counter()
+    for c in range(nchunks):
+        m = min(chunk, pairs - c * chunk)
+        data = make_dataset(m, size, size, seed0=seed0 + c * chunk, p=p)
+        log += net.train(data, steps_per_chunk, batch=batch, lr=lr, lr_end=lr_end,
+                         log_every=steps_per_chunk, total_steps=total, seed=12345 + c)
+        del data
+    torch.cuda.synchronize()
+    return net, log, time.perf_counter() - t0
+
+
+def main():
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="chunked training of the warm-start network and its gain")
+    ap.add_argument("--pairs", type=int, default=20000)
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--chunk", type=int, default=1000)
+    ap.add_argument("--epochs", type=float, default=1.0)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--eval", type=int, default=4, help="held-out 1080p scenes (seeds 6e6 + i)")
+    a = ap.parse_args()
+    net, log, secs = train_chunked(a.pairs, a.size, a.chunk, a.epochs, a.batch)
+    ev = evaluate(net, range(6_000_000, 6_000_000 + a.eval), 1080, 1920)
+    print(json.dumps({"pairs": a.pairs, "size": a.size, "chunk": a.chunk, "epochs": a.epochs, "batch": a.batch,
+                      "train_s": secs, "loss_first": log[0][1], "loss_last": log[-1][1],
+                      "eval_1080p": ev["summary"]}))
+
+
+if __name__ == "__main__":
+    main()
