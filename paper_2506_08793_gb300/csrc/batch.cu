@@ -503,7 +503,7 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
     BatchHdr *hdr = (BatchHdr *)(ws + B.hdr);
     int launches = 0;
     if (p->use_graph) {
-        BatchGraph bg;
+        BatchGraph bg{};
         int rc = batch_graph(dev, hdr, grid, edge, smem, &bg);
         if (rc) return rc;
         k_batch_init<<<1, 32, 0, s>>>(hdr, dimgs, n, 1, bg.cond);

@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "common.cuh"
 #include "tma.cuh"
@@ -112,7 +113,6 @@ k_conv3x3_tc(const bf16 *__restrict__ x, int ldx, int C, int Nimg, int H, int W,
     __shared__ __align__(8) uint64_t mma_bar[S];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_fail;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int HW = H * W, M = Nimg * HW;
@@ -128,7 +128,6 @@ k_conv3x3_tc(const bf16 *__restrict__ x, int ldx, int C, int Nimg, int H, int W,
         for (int s = 0; s < S; ++s) mbar_init(&mma_bar[s], 1);
         mbar_init(&done_bar, 1);
         fence_mbar_init();
-        s_fail = 0;
     }
     tc_fence_before();
     __syncthreads();
@@ -235,12 +234,17 @@ template <int NT>
 int launch_tc(const bf16 *x, int ldx, int C, int N, int H, int W, const bf16 *w, const float *b, int Cout, bool relu,
               bf16 *y, int ldy, int *err, cudaStream_t s) {
     using P = TcPlan<NT>;
+    static std::mutex mu;
     static bool attr_set[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return DH_ECUDA;
-    if (!attr_set[dev]) {
-        DH_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM));
-        attr_set[dev] = true;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!attr_set[dev]) {
+            DH_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)P::SMEM));
+            attr_set[dev] = true;
+        }
     }
     const int M = N * H * W;
     dim3 grid((M + kTcBM - 1) / kTcBM, (Cout + NT - 1) / NT);
@@ -414,9 +418,11 @@ template <int C, int CO>
 int launch_halo(const bf16 *x, int ldx, int N, int H, int W, const bf16 *w, const float *b, bool relu, bf16 *y,
                 int ldy, int *err, cudaStream_t s) {
     using P = HaloPlan<C, CO>;
+    static std::mutex mu;
     static int grid_cache[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return DH_ECUDA;
+    std::lock_guard<std::mutex> lk(mu);
     if (!grid_cache[dev]) {
         DH_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3_halo<C, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)P::SMEM));

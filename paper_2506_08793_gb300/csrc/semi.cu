@@ -28,6 +28,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "tma.cuh"
@@ -443,9 +444,11 @@ SiLayout si_layout(int H, int W) {
 }
 
 int si_grid(int E) {
+    static std::mutex mu;
     static int cached = 0, cached_dev = -1;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(mu);
     if (cached_dev != dev) {
         int per_sm = 0, sms = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_semi_implicit, kSiThreads, 0) != cudaSuccess)
