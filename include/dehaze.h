@@ -117,7 +117,8 @@ typedef struct dh_report {
     long long a_index;  /* row-major index of the pixel A was taken from, or -1 */
     float ms;           /* device time of the call (CUDA events on `stream`) */
     float ms_loop;      /* device time of the fixed-point loop alone */
-    int launches;       /* kernels the call ran (each loop iteration counts one) */
+    int launches;       /* kernels the call ran; sweep launches are counted on the device
+                           (a multi-iteration launch runs up to 64 iterations) */
 } dh_report;
 
 /* Fill *p with a preset.  Returns DH_OK or DH_EINVAL (NULL p, unknown preset). */
