@@ -338,6 +338,13 @@ int dh_semi_implicit(float *u, float *u_lo, const float *Phi, const float *lam, 
                      float step, int cg_iters, float *rho_hist, float *J, void *workspace, size_t workspace_bytes,
                      void *stream, dh_report *report);
 
+/* Diagnostic, no counterpart in the paper: runs one wait on a device barrier
+ * that nothing completes, bounded by limit_cycles SM clocks (1 .. 4e9), the
+ * way every wait of the library is bounded.  Returns DH_ETIMEOUT when the
+ * bound is honoured (the expected result), DH_EINVAL for a bad limit,
+ * DH_ECUDA on a CUDA error.  Synchronises the stream. */
+int dh_selftest_bounded_wait(long long limit_cycles, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

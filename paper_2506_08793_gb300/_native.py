@@ -34,7 +34,8 @@ EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes
            "dh_unet_forward", "dh_unet_backward", "dh_unet_adam", "dh_warm_start", "dh_warm_target",
            "dh_conv3x3_forward",
            "dh_conv3x3_backward_weights", "dh_dehaze_warm", "dh_atmospheric_light_noalloc",
-           "dh_semi_implicit_workspace_bytes", "dh_semi_implicit", "dh_transmission_ws")
+           "dh_semi_implicit_workspace_bytes", "dh_semi_implicit", "dh_transmission_ws",
+           "dh_selftest_bounded_wait")
 
 
 class DhParams(ctypes.Structure):
@@ -159,6 +160,7 @@ def lib(build_if_missing: bool = True):
             "dh_dehaze_warm": ([P, I, P, I, I, PP, P, P, P, P, P, S, P, S, P, PR], I),
             "dh_semi_implicit_workspace_bytes": ([I, I], S),
             "dh_transmission_ws": ([P, P, I, I, PP, P, P, P, P, P, S, P], I),
+            "dh_selftest_bounded_wait": ([ctypes.c_longlong, P], I),
             "dh_semi_implicit": ([P, P, P, P, I, I, PP, ctypes.c_float, I, P, P, P, S, P, PR], I),
         }
         for name, (args, res) in sig.items():
@@ -343,3 +345,7 @@ def dh_dehaze_warm(params, base, I, H, W, p: DhParams, J, u, t, A, workspace, wo
     return lib().dh_dehaze_warm(_p(params), base, _p(I), H, W, ctypes.byref(p), _p(J), _p(u), _p(t), _p(A),
                                 _p(workspace), workspace_bytes, _p(net_workspace), net_workspace_bytes,
                                 _stream(stream), _ref(report))
+
+
+def dh_selftest_bounded_wait(limit_cycles: int, stream=None) -> int:
+    return lib().dh_selftest_bounded_wait(int(limit_cycles), _stream(stream))

@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace dh {
 
@@ -62,4 +63,38 @@ extern "C" int dh_atmospheric_light_noalloc(const float *I, const float *dc, int
     // writes every per-block record before reading it.
     return launch_select_A(I, dc, H, W, topk_permille, A_out, index_out, scratch, L,
                            (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- bounded-wait self test
+// A wait on an mbarrier that nothing ever completes, given up after
+// limit_cycles: the same bounded wait every TMA / tensor-core stage uses.
+namespace dh {
+static __device__ int g_selftest_result;
+
+__global__ void k_selftest_wait(int *out, long long limit_cycles) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);  // one arrival expected, none will come
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0, limit_cycles);
+    if (threadIdx.x == 0) *out = ok ? DH_OK : DH_ETIMEOUT;
+}
+}  // namespace dh
+
+extern "C" int dh_selftest_bounded_wait(long long limit_cycles, void *stream) {
+    using namespace dh;
+    if (limit_cycles < 1 || limit_cycles > 4000000000LL) return DH_EINVAL;
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    int *d = nullptr;
+    DH_CUDA_TRY(cudaGetSymbolAddress((void **)&d, g_selftest_result));
+    cudaStream_t s = (cudaStream_t)stream;
+    k_selftest_wait<<<1, 32, 0, s>>>(d, limit_cycles);
+    DH_CUDA_TRY(cudaGetLastError());
+    int h = DH_ECUDA;
+    DH_CUDA_TRY(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DH_CUDA_TRY(cudaStreamSynchronize(s));
+    return h;
 }
