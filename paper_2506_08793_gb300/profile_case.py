@@ -24,10 +24,37 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="sweep variant (0: library default)")
     ap.add_argument("--net", type=int, default=0, help="instead: N images through the warm-start network forward")
     ap.add_argument("--conv", default="", help="instead: one 3x3 convolution 'C,Cout' on 1 x H x W, --repeat times")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead: N images of the mixed photo sizes (seed 3000) in one batched solve")
+    ap.add_argument("--semi", type=int, default=0,
+                    help="instead: the semi-implicit solver with this many CG iterations per outer step "
+                         "(paper preset, --iters outer steps)")
     ap.add_argument("--host-loop", action="store_true",
                     help="queue the sweeps from the host instead of the graph loop (profilers cannot "
                          "see kernels inside a graph with conditional nodes)")
     a = ap.parse_args()
+    if a.batch:
+        sizes = scenes.batch_sizes(3000, a.batch)
+        imgs = [torch.from_numpy(scenes.hazy_scene(3000 + k, H, W)["I"]).cuda() for k, (H, W) in enumerate(sizes)]
+        b = api.BatchDehazer(sizes, api.params(a.preset, tol=a.tol, max_iter=a.iters,
+                                               use_graph=0 if a.host_loop else 1))
+        for _ in range(a.repeat):
+            reps = b(imgs)
+        torch.cuda.synchronize()
+        print(f"batch of {a.batch}: {[r.n_iter for r in reps]} iterations, {reps[0].ms:.3f} ms")
+        return
+    if a.semi:
+        I = torch.from_numpy(scenes.hazy_scene(a.seed, a.H, a.W)["I"]).cuda()
+        p = api.params("paper", tol=a.tol, max_iter=a.iters)
+        dc = api.dark_channel(I, p.patch)
+        A, _, _ = api.atmospheric_light(I, dc, p.topk_permille)
+        _, _, lam, Phi = api.transmission(I, A, p)
+        for _ in range(a.repeat):
+            u = Phi.clone()
+            rep, _ = api.semi_implicit(u, Phi, lam, p, 2.0, a.semi)
+        torch.cuda.synchronize()
+        print(f"semi-implicit {a.H}x{a.W}: {rep.n_iter} outer steps, {rep.ms:.3f} ms, status {rep.status}")
+        return
     if a.conv:
         from . import _native as N
 
