@@ -216,17 +216,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
                 break;
             }
             if (!d->dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + kBTH + 2 > H)) {
-                for (int e = threadIdx.x; e < SH * SW; e += kBNW * 32) {
-                    const int r = e / SW, q = e - r * SW;
-                    const int gy = y0 - 2 + r, gx = x0 - 4 + q;
-                    const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
-                    const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
-                    const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
-                    if ((fy && (inx || fx)) || (fx && iny)) {
-                        const int sy = reflect_idx(gy, H) - (y0 - 2), sx = reflect_idx(gx, W) - (x0 - 4);
-                        s[e] = s[sy * SW + sx];
-                    }
-                }
+                reflect_border(s, SW, SW, SH, x0 - 4, y0 - 2, H, W);
                 fence_proxy_async_smem();
             }
         } else {

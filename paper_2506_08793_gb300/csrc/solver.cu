@@ -218,17 +218,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             // which is already the Dirichlet boundary); interior tiles need no
             // barrier here: the one above already ordered the landed tile
             if (!dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + TH + 2 > H)) {
-                for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
-                    const int r = e / SW, q = e - r * SW;
-                    const int gy = y0 - 2 + r, gx = x0 - HALO + q;
-                    const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
-                    const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
-                    const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
-                    if ((fy && (inx || fx)) || (fx && iny)) {
-                        const int sy = reflect_idx(gy, H) - (y0 - 2), sx = reflect_idx(gx, W) - (x0 - HALO);
-                        s[e] = s[sy * SW + sx];
-                    }
-                }
+                reflect_border(s, SW, SW, SH, x0 - HALO, y0 - 2, H, W);
                 fence_proxy_async_smem();  // these writes precede the stage's next TMA load
                 __syncthreads();
             }
@@ -528,17 +518,7 @@ k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             }
             // the reflecting boundary on the u^n tile (rows / columns 1-2 outside)
             if (!dirichlet && (x0 < 8 || y0 < 4 || x0 + kTW2 + 8 > W || y0 + TH + 4 > H)) {
-                for (int e = threadIdx.x; e < (TH + 8) * SW; e += NW * 32) {
-                    const int r = e / SW, q = e - r * SW;
-                    const int gy = y0 - 4 + r, gx = x0 - 8 + q;
-                    const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
-                    const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
-                    const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
-                    if ((fy && (inx || fx)) || (fx && iny)) {
-                        const int sy = reflect_idx(gy, H) - (y0 - 4), sx = reflect_idx(gx, W) - (x0 - 8);
-                        s0[e] = s0[sy * SW + sx];
-                    }
-                }
+                reflect_border(s0, SW, SW, TH + 8, x0 - 8, y0 - 4, H, W);
                 fence_proxy_async_smem();  // these writes precede the next TMA load into this buffer
             }
             __syncthreads();
@@ -575,22 +555,15 @@ k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             if (two) {
                 __syncthreads();
                 // boundary rule on u^{n+1} (shared rows y0-2.., columns x0-4..)
-                if (dirichlet || x0 < 4 || y0 < 4 || x0 + kTW2 + 4 > W || y0 + TH + 4 > H) {
-                    for (int e = threadIdx.x; e < (TH + 4) * kTW; e += NW * 32) {
-                        const int r = e / kTW, q = e - r * kTW;
-                        const int gy = y0 - 2 + r, gx = x0 - 4 + q;
-                        const bool iny = gy >= 0 && gy < H, inx = gx >= 0 && gx < W;
-                        if (iny && inx) continue;
-                        if (dirichlet) {
-                            s1[r * SW + q] = 0.f;
-                        } else {
-                            const bool fy = gy == -2 || gy == -1 || gy == H || gy == H + 1;
-                            const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
-                            if ((fy && (inx || fx)) || (fx && iny)) {
-                                const int sy = reflect_idx(gy, H) - (y0 - 2), sx = reflect_idx(gx, W) - (x0 - 4);
-                                s1[r * SW + q] = s1[sy * SW + sx];
-                            }
+                if (x0 < 4 || y0 < 4 || x0 + kTW2 + 4 > W || y0 + TH + 4 > H) {
+                    if (dirichlet) {
+                        for (int e = threadIdx.x; e < (TH + 4) * kTW; e += NW * 32) {
+                            const int r = e / kTW, q = e - r * kTW;
+                            const int gy = y0 - 2 + r, gx = x0 - 4 + q;
+                            if (gy < 0 || gy >= H || gx < 0 || gx >= W) s1[r * SW + q] = 0.f;
                         }
+                    } else {
+                        reflect_border(s1, SW, kTW, TH + 4, x0 - 4, y0 - 2, H, W);
                     }
                     __syncthreads();
                 }

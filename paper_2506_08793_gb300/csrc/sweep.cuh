@@ -377,6 +377,48 @@ __device__ __forceinline__ void walk_rows(const T *__restrict__ s, int r0, int l
 }
 
 
+// Reflecting boundary on a staged tile: the cells one or two rows / columns
+// outside the image (zero-filled by TMA) take the value of their half-sample
+// reflection, which always lies inside the image and inside the tile.  Only
+// the (at most four) border rows and columns of the tile are visited: rows with
+// gy in {-2, -1, H, H+1} over all columns whose gx is inside the image or is
+// itself such a border column (corners), then border columns over the rows
+// inside the image.  Tile row r is image row ry0 + r, column q image column
+// cx0 + q.  The sources are never written, so one pass in any order suffices.
+template <class T>
+__device__ __forceinline__ void reflect_border(T *s, int stride, int ncols, int nrows, int cx0, int ry0, int H,
+                                               int W) {
+    int rows[4], nr = 0, cols[4], nc = 0;
+    for (int g : {-2, -1, H, H + 1}) {
+        const int r = g - ry0;
+        if (r >= 0 && r < nrows && (g < 0 || g >= H)) rows[nr++] = r;
+    }
+    for (int g : {-2, -1, W, W + 1}) {
+        const int q = g - cx0;
+        if (q >= 0 && q < ncols && (g < 0 || g >= W)) cols[nc++] = q;
+    }
+    const int nrow_cells = nr * ncols, total = nrow_cells + nc * nrows;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        int r, q;
+        if (e < nrow_cells) {
+            const int k = e / ncols;
+            r = rows[k];
+            q = e - k * ncols;
+            const int gx = cx0 + q;
+            const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
+            if (!(fx || (gx >= 0 && gx < W))) continue;
+        } else {
+            const int e2 = e - nrow_cells, k = e2 / nrows;
+            q = cols[k];
+            r = e2 - k * nrows;
+            const int gy = ry0 + r;
+            if (gy < 0 || gy >= H) continue;  // rows outside were done above (corners included)
+        }
+        const int sy = reflect_idx(ry0 + r, H) - ry0, sx = reflect_idx(cx0 + q, W) - cx0;
+        s[r * stride + q] = s[sy * stride + sx];
+    }
+}
+
 // Shared-memory plan of the TMA sweep: per stage the u^n tile with its halo,
 // the Phi tile and the lambda tile, each 1024-byte aligned.
 template <int TH, bool PL_SMEM, class T>
