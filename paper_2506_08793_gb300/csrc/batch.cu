@@ -194,6 +194,19 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
     };
     if (threadIdx.x == 0 && m > 0) issue(item_at(0));
 
+    // An image whose last item of this iteration a CTA has just finished is
+    // finished (residual, stop rule) by that CTA at its next barrier, so the
+    // arrival atomic's round trip overlaps the next tile's load.
+    if (threadIdx.x == 0) s_img_last = -1;
+    auto finish_pending = [&]() {  // all threads, right after a barrier
+        const int fin = s_img_last;
+        if (fin >= 0) {
+            finish_iteration(&imgs[fin].d, imgs[fin].d.st);
+            __syncthreads();
+            if (threadIdx.x == 0) s_img_last = -1;
+        }
+    };
+
     int kt = 0;  // TMA items waited for so far (barrier phase)
     bool failed = false;
     for (int j = 0; j < m; ++j) {
@@ -215,11 +228,14 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
                 failed = true;
                 break;
             }
+            finish_pending();
             if (!d->dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + kBTH + 2 > H)) {
                 reflect_border(s, SW, SW, SH, x0 - 4, y0 - 2, H, W);
                 fence_proxy_async_smem();
             }
         } else {
+            __syncthreads();
+            finish_pending();
             // gather the tile with the reflecting boundary (W % 4 != 0 or unaligned image)
             const float *u = static_cast<const float *>(d->u[cur]) + c * N;
             for (int e = threadIdx.x; e < SH * SW; e += kBNW * 32) {
@@ -279,12 +295,11 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
             d->part[(size_t)c * d->nblk + tile] = tot;
             __threadfence();
             const unsigned prev = atomicAdd(&st->arrive, 1u);
-            s_img_last = prev == (unsigned)im->items - 1u;
+            if (prev == (unsigned)im->items - 1u) s_img_last = img;  // read after the next barrier
         }
-        __syncthreads();
-        if (s_img_last) finish_iteration(d, st);  // this image's iteration is complete
-        __syncthreads();
     }
+    __syncthreads();
+    finish_pending();
     if (failed) {
         if (threadIdx.x == 0) {
             mbar_wait_bounded(&bar, kt & 1, kWaitLimitCycles);  // the load already issued
