@@ -46,7 +46,8 @@ def measured_peaks():
         return None
 
 
-SWEEP_SOURCES = ("paper_2506_08793_gb300/csrc/sweep.cuh", "paper_2506_08793_gb300/csrc/solver.cu")
+SWEEP_SOURCES = ("paper_2506_08793_gb300/csrc/sweep.cuh", "paper_2506_08793_gb300/csrc/sweep_kernels.cuh",
+                 "paper_2506_08793_gb300/csrc/solver.cu")
 
 
 def sweep_source_hash() -> str:

@@ -11,854 +11,9 @@
 #include <cstdlib>
 #include <cstring>
 
-#include "sweep.cuh"
+#include "sweep_kernels.cuh"
 
 namespace dh {
-
-// Generic sweep (any W, any alignment): one CTA per (tile, channel), tile of
-// u^n gathered with the reflecting boundary by plain loads.
-template <int R, int NW, class T, bool EDGE>
-__global__ void __launch_bounds__(NW * 32)
-k_sweep(const SolveDesc *__restrict__ d) {
-    constexpr int TH = R * NW;
-    constexpr int SW = kTW + 8;
-    constexpr int SH = TH + 4;
-    __shared__ __align__(16) float s[SH * SW];
-    __shared__ float2 red[NW];
-    __shared__ int s_last;
-
-    SolveState *st = d->st;
-    clear_condition(d);
-    if (__ldcg(&st->done)) return;
-    const int H = d->H, W = d->W;
-    const int c = blockIdx.z;
-    const int x0 = blockIdx.x * kTW, y0 = blockIdx.y * TH;
-    const int cur = __ldcg(&st->cur);
-    const size_t N = (size_t)H * W;
-    const T *__restrict__ u = static_cast<const T *>(d->u[cur]) + c * N;
-    T *__restrict__ un = static_cast<T *>(d->u[cur ^ 1]) + c * N;
-    const float *__restrict__ phi = d->phi + c * N;
-    const float *__restrict__ lam = d->lam;
-
-    const bool dirichlet = d->dirichlet != 0;
-    for (int e = threadIdx.x; e < SH * SW; e += NW * 32) {
-        const int r = e / SW, q = e - r * SW;
-        const int yy = y0 - 2 + r, xx = x0 - 4 + q;
-        if (dirichlet) {
-            s[e] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? Store<T>::get(u + (size_t)yy * W + xx) : 0.f;
-        } else {
-            s[e] = Store<T>::get(u + (size_t)reflect_idx(yy, H) * W + reflect_idx(xx, W));
-        }
-    }
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int x = x0 + 4 * lane;
-    const bool vec = d->vec != 0;
-    float rs = 0.f, rc = 0.f;
-    auto pl = [&](int ty, float *ph, float *la) {
-        const int y = y0 + ty;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) ph[j] = la[j] = 0.f;
-        if (y >= H) return;
-        const size_t ro = (size_t)y * W;
-        if (vec) {
-            if (x < W) {
-                const float4 p4 = __ldg(reinterpret_cast<const float4 *>(phi + ro + x));
-                const float4 l4 = __ldg(reinterpret_cast<const float4 *>(lam + ro + x));
-                ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
-                la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (x + j < W) { ph[j] = __ldg(phi + ro + x + j); la[j] = __ldg(lam + ro + x + j); }
-        }
-    };
-    auto sink = [&](int ty, const float *nu, const float *F) {
-        const int y = y0 + ty;
-        if (y >= H) return;
-        const size_t ro = (size_t)y * W;
-        float q = 0.f;
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (x + j < W) q = fmaf(F[j], F[j], q);
-        neumaier_add(rs, rc, q);
-        if (vec) {
-            if (x < W) Store<T>::write4(un + ro + x, nu[0], nu[1], nu[2], nu[3]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (x + j < W) Store<T>::put(un + ro + x + j, nu[j]);
-        }
-    };
-    walk_rows<R, SW, float, EDGE>(s, w * R, lane, d->eps, d->tau, d->wg0, d->wg1, d->wg2, pl, sink);
-
-    const float2 tot = block_pair_sum<NW>(rs, rc, red);
-    if (threadIdx.x == 0)
-        d->part[(size_t)c * d->nblk + blockIdx.y * gridDim.x + blockIdx.x] = tot;
-    arrive_and_finish(d, st, &s_last);
-}
-
-// TMA sweep (W % 4 == 0, 16-byte aligned planes): persistent CTAs walk the
-// (tile, channel) items; one thread streams each item's u^n tile (with halo)
-// into shared memory by TMA, STAGES items ahead, together with the Phi and
-// lambda tiles when PL_SMEM (otherwise the walk reads those with vector
-// loads); the border halo is reflected in shared memory afterwards.  Each
-// item's tiles are first pulled into L2 one item before their load is issued.
-// Odd iterations walk a CTA's items in reverse order, so that an iteration
-// starts on the tiles the previous one touched last (still in L2).
-//
-// MULTI: a cooperative launch runs up to d->depth iterations.  Between two
-// iterations the CTAs meet at a grid barrier whose last arrival reduces the
-// residual and decides (finish_iteration), then bumps st->gen; the others
-// wait for the bump (bounded, DH_ETIMEOUT).  The u^{n+1} tiles that the next
-// iteration loads by TMA were written by generic stores of other CTAs: the
-// writers fence them to the async proxy before arriving and the issuing
-// thread fences again after the barrier.
-template <int R, int NW, int STAGES, bool PL_SMEM, class T, bool EDGE, int MINB = 0, bool MULTI = false>
-__global__ void __launch_bounds__(NW * 32, MINB > 0 ? MINB : 16 / NW)
-k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
-            const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
-            const SolveDesc *__restrict__ d) {
-    constexpr int TH = R * NW;
-    constexpr int HALO = Store<T>::HALO;
-    using P = TmaPlan<TH, PL_SMEM, T>;
-    constexpr int SW = P::SW, SH = P::SH;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte aligned base (the launch adds 1 KiB of slack)
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bar[STAGES];
-    __shared__ float2 red[NW];
-    __shared__ int s_last, s_timeout;
-
-    SolveState *st = d->st;
-    clear_condition(d);
-    if (__ldcg(&st->done)) return;
-    unsigned gen = 0;
-    if (MULTI) gen = ld_acquire_gpu(&st->gen);  // before this CTA can arrive anywhere
-    const int H = d->H, W = d->W;
-    const size_t N = (size_t)H * W;
-    const int ntx = (W + kTW - 1) / kTW, nty = (H + TH - 1) / TH;
-    const int ntiles = ntx * nty, nitems = 3 * ntiles;
-    const int G = gridDim.x;
-    const int m = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;  // items of this CTA
-
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < STAGES; ++k) mbar_init(&bar[k], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
-    const bool dirichlet = d->dirichlet != 0;
-    const float *__restrict__ phi_all = d->phi;
-    const float *__restrict__ glam = d->lam;
-    float2 *__restrict__ part = d->part;
-    const int nblk = d->nblk;
-    const int iters = MULTI ? d->depth : 1;
-    int k = 0;  // items this CTA has started in the launch (stage and parity)
-    bool failed = false;
-    for (int it = 0; it < iters; ++it) {
-        const int cur = __ldcg(&st->cur);
-        const bool rev = (__ldcg(&st->n) & 1) != 0;
-        const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
-        T *__restrict__ ubase = static_cast<T *>(d->u[cur ^ 1]);
-        auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
-        auto tile_xy = [&](int item, int &c, int &x0, int &y0) {
-            const int tile = item / 3;
-            c = item - 3 * tile;
-            x0 = (tile % ntx) * kTW;
-            y0 = (tile / ntx) * TH;
-            return tile;
-        };
-        auto issue = [&](int j, int stage) {
-            int c, x0, y0;
-            tile_xy(item_at(j), c, x0, y0);
-            unsigned char *sb = smem + stage * P::STAGE;
-            mbar_arrive_expect_tx(&bar[stage], P::TX);
-            tma_load_3d(sb + P::U_OFF, tm_u, &bar[stage], x0 - HALO, y0 - 2, c);
-            if (PL_SMEM) {
-                tma_load_3d(sb + P::PHI_OFF, &tm_phi, &bar[stage], x0, y0, c);
-                tma_load_2d(sb + P::LAM_OFF, &tm_lam, &bar[stage], x0, y0);
-            }
-        };
-        auto prefetch = [&](int j) {
-            int c, x0, y0;
-            tile_xy(item_at(j), c, x0, y0);
-            tma_prefetch_3d(tm_u, x0 - HALO, y0 - 2, c);
-            if (PL_SMEM) {
-                tma_prefetch_3d(&tm_phi, x0, y0, c);
-                tma_prefetch_2d(&tm_lam, x0, y0);
-            }
-        };
-        if (threadIdx.x == 0) {
-            if (MULTI && it > 0) fence_proxy_async_global();
-            for (int j = 0; j < STAGES && j < m; ++j) issue(j, (k + j) % STAGES);
-        }
-        int j = 0;
-        for (; j < m; ++j, ++k) {
-            const int stage = k % STAGES;
-            const uint32_t parity = (k / STAGES) & 1;
-            int c, x0, y0;
-            const int tile = tile_xy(item_at(j), c, x0, y0);
-            unsigned char *sb = smem + stage * P::STAGE;
-            T *s = reinterpret_cast<T *>(sb + P::U_OFF);
-            const float *sphi = reinterpret_cast<const float *>(sb + P::PHI_OFF);
-            const float *slam = reinterpret_cast<const float *>(sb + P::LAM_OFF);
-            if (threadIdx.x == 0 && j + STAGES < m) prefetch(j + STAGES);
-
-            const bool ok = mbar_wait_bounded(&bar[stage], parity, kWaitLimitCycles);
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-            // reflect the halo cells that fall outside the image (TMA filled zeros,
-            // which is already the Dirichlet boundary); interior tiles need no
-            // barrier here: the one above already ordered the landed tile
-            if (!dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + TH + 2 > H)) {
-                reflect_border(s, SW, SW, SH, x0 - HALO, y0 - 2, H, W);
-                fence_proxy_async_smem();  // these writes precede the stage's next TMA load
-                __syncthreads();
-            }
-
-            T *__restrict__ un = ubase + c * N;
-            const int x = x0 + 4 * lane;
-            float rs = 0.f, rc = 0.f;
-            const float *__restrict__ gphi = phi_all + c * N;
-            auto pl = [&](int ty, float *ph, float *la) {
-                float4 p4, l4;
-                if (PL_SMEM) {
-                    p4 = *reinterpret_cast<const float4 *>(sphi + ty * kTW + 4 * lane);
-                    l4 = *reinterpret_cast<const float4 *>(slam + ty * kTW + 4 * lane);
-                } else {
-                    const int y = y0 + ty;
-                    p4 = l4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (y < H && x < W) {
-                        p4 = __ldg(reinterpret_cast<const float4 *>(gphi + (size_t)y * W + x));
-                        l4 = __ldg(reinterpret_cast<const float4 *>(glam + (size_t)y * W + x));
-                    }
-                }
-                ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
-                la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
-            };
-            auto sink = [&](int ty, const float *nu, const float *F) {
-                const int y = y0 + ty;
-                if (y >= H || x >= W) return;  // W % 4 == 0: x < W covers all 4 columns
-                float q = 0.f;
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) q = fmaf(F[jj], F[jj], q);
-                neumaier_add(rs, rc, q);
-                Store<T>::write4(un + (size_t)y * W + x, nu[0], nu[1], nu[2], nu[3]);
-            };
-            walk_rows<R, SW, T, EDGE>(s, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
-
-            // every thread is past its walk once block_pair_sum's barrier is
-            // passed, so the stage can be refilled; red[] is rewritten only after
-            // the next item's wait barrier, which every reader of it reaches first
-            const float2 tot = block_pair_sum<NW>(rs, rc, red);
-            if (threadIdx.x == 0) {
-                part[(size_t)c * nblk + tile] = tot;
-                if (j + STAGES < m) {
-                    fence_proxy_async_smem();
-                    issue(j + STAGES, stage);
-                }
-            }
-        }
-        if (failed) {
-            // let every load already issued land (bounded) before going on
-            for (int q = 0; q < STAGES && j + q < m; ++q) {
-                const int kk = k + q;
-                mbar_wait_bounded(&bar[kk % STAGES], (kk / STAGES) & 1, kWaitLimitCycles);
-            }
-            if (threadIdx.x == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
-        }
-        if (!MULTI) break;
-
-        // grid barrier; the last CTA to arrive finishes the iteration
-        fence_proxy_async_global();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(&st->arrive, 1u);
-            s_last = prev == (unsigned)G - 1u;
-            s_timeout = 0;
-        }
-        __syncthreads();
-        if (s_last) {
-            finish_iteration(d, st);
-            if (threadIdx.x == 0) {
-                __threadfence();
-                st_release_gpu(&st->gen, gen + 1u);
-            }
-        } else if (threadIdx.x == 0) {
-            const long long t0 = clock64();
-            while (ld_acquire_gpu(&st->gen) == gen) {
-                if (clock64() - t0 > kWaitLimitCycles) {
-                    s_timeout = 1;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        ++gen;
-        __syncthreads();
-        if (s_timeout) {  // another CTA never arrived: give up, report
-            if (threadIdx.x == 0) {
-                atomicCAS(&st->err, 0, DH_ETIMEOUT);
-                st->status = DH_ETIMEOUT;
-                st->done = 1;
-            }
-            return;
-        }
-        if (__ldcg(&st->done) || failed) return;
-    }
-    if (!MULTI) arrive_and_finish(d, st, &s_last);
-}
-
-// ---------------------------------------------------------------- two iterations per tile load
-// Temporally blocked sweep (float iterates, W % 4 == 0, 16-byte aligned
-// planes).  An item is a 120 x TH output tile of one channel.  TMA loads u^n
-// on the output tile plus a 4-cell ring (136 x (TH+8)), Phi and lambda on the
-// tile plus a (2-row, 4-column) ring (128 x (TH+4)).  Step 1 walks the 128 x
-// (TH+4) region around the tile and keeps u^{n+1} in shared memory; after the
-// border ring is reflected, step 2 walks the tile from it and writes u^{n+2}.
-// The residual of step 1 over the tile is F(u^n) and that of step 2 is
-// F(u^{n+1}), the same quantities one iteration at a time would give.  The
-// last CTA at the grid barrier decides with both (finish_tb2): stop at n, or
-// advance by two, or - when u^{n+1} is the iterate to return (its residual
-// meets tol, or n+1 = max_iter) - switch the rest of the solve to one
-// iteration per load (step 1 writing the tile to global memory), which
-// recomputes u^{n+1} and stops there.
-template <int R2, int NW>
-struct Tb2Plan {
-    static constexpr int TH = R2 * NW;
-    static constexpr int R1 = R2 + 4 / NW;        // rows per warp in step 1 (TH + 4 rows)
-    static constexpr int SW = kTW + 8;            // 136 floats per shared row
-    static constexpr uint32_t U0_BYTES = (TH + 8) * SW * 4;
-    static constexpr uint32_t PL_BYTES = (TH + 4) * kTW * 4;
-    static constexpr uint32_t U1_BYTES = (TH + 4) * SW * 4;
-    static constexpr uint32_t U0_OFF = 0;
-    static constexpr uint32_t PHI_OFF = (U0_BYTES + 1023) / 1024 * 1024;
-    static constexpr uint32_t LAM_OFF = PHI_OFF + PL_BYTES;
-    static constexpr uint32_t U1_OFF = (LAM_OFF + PL_BYTES + 1023) / 1024 * 1024;
-    static constexpr uint32_t SMEM = U1_OFF + U1_BYTES + 1024;  // + alignment slack
-    static constexpr uint32_t TX = U0_BYTES + 2 * PL_BYTES;
-    static_assert(4 % NW == 0, "the TH + 4 step-1 rows must split evenly over the warps");
-};
-
-// Last CTA of a two-iteration sweep: residuals of both levels, decision.
-static __device__ void finish_tb2(const SolveDesc *d, SolveState *st) {
-    constexpr int U = 4;
-    __shared__ float2 wsum[6][32];
-    __shared__ float sq[6];
-    const int tid = threadIdx.x, nt = blockDim.x, w = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    __threadfence();
-    const int nblk = d->nblk;
-    const float2 *part = d->part;
-    float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, cc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    for (int b0 = tid; b0 < nblk; b0 += U * nt) {
-        float2 pv[6][U];
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-#pragma unroll
-            for (int j = 0; j < U; ++j) {
-                const int b = b0 + j * nt;
-                pv[k][j] = b < nblk ? __ldcg(part + (size_t)k * nblk + b) : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-        for (int k = 0; k < 6; ++k)
-#pragma unroll
-            for (int j = 0; j < U; ++j) neumaier_merge(s[k], cc[k], pv[k][j].x, pv[k][j].y);
-    }
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        for (int off = 16; off; off >>= 1) {
-            const float s2 = __shfl_down_sync(0xffffffffu, s[k], off);
-            const float c2 = __shfl_down_sync(0xffffffffu, cc[k], off);
-            neumaier_merge(s[k], cc[k], s2, c2);
-        }
-        if (lane == 0) wsum[k][w] = make_float2(s[k], cc[k]);
-    }
-    __syncthreads();
-    if (tid < 6) {
-        float a = wsum[tid][0].x, b = wsum[tid][0].y;
-        for (int k = 1; k < nw; ++k) neumaier_merge(a, b, wsum[tid][k].x, wsum[tid][k].y);
-        sq[tid] = a + b;
-    }
-    __syncthreads();
-    if (tid != 0) return;
-    const int n = st->n, two = st->tb2;
-    auto rho_of = [&](int lv, float *rho, float &worst) {
-        bool finite = true;
-        worst = 0.f;
-        for (int c = 0; c < 3; ++c) {
-            const float pn = st->phin2[c], q = sq[3 * lv + c];
-            rho[c] = pn > 0.f ? sqrtf(q / pn) : sqrtf(q);
-            if (!isfinite(rho[c])) finite = false;
-            else worst = fmaxf(worst, rho[c]);
-        }
-        return finite;
-    };
-    float rho0[3], w0;
-    const bool fin0 = rho_of(0, rho0, w0);
-    if (d->rho_hist)
-        for (int c = 0; c < 3; ++c) d->rho_hist[3 * n + c] = rho0[c];
-    const int err = __ldcg(&st->err);
-    const bool conv = fin0 && w0 <= d->tol;
-    unsigned cont = 1;
-    if (err || conv || !fin0 || n >= d->max_iter) {
-        st->done = 1;
-        st->n_final = n;
-        st->status = err ? err : (!fin0 ? DH_ENONFINITE : (conv ? DH_OK : DH_WNOCONV));
-        for (int c = 0; c < 3; ++c) st->rho[c] = rho0[c];
-        cont = 0;
-    } else if (!two) {
-        st->n = n + 1;
-        st->cur ^= 1;
-    } else {
-        float rho1[3], w1;
-        const bool fin1 = rho_of(1, rho1, w1);
-        if (!fin1 || w1 <= d->tol || n + 1 >= d->max_iter) {
-            st->tb2 = 0;  // u^{n+1} may be the answer: redo it one iteration at a time
-        } else {
-            if (d->rho_hist)
-                for (int c = 0; c < 3; ++c) d->rho_hist[3 * (n + 1) + c] = rho1[c];
-            st->n = n + 2;
-            st->cur ^= 1;
-        }
-    }
-    st->arrive = 0;
-    __threadfence();
-    if (d->use_cond) cudaGraphSetConditional(d->cond, cont);
-}
-
-template <int R2, int NW, bool EDGE, int MINB>
-__global__ void __launch_bounds__(NW * 32, MINB)
-k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
-            const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
-            const SolveDesc *__restrict__ d) {
-    using P = Tb2Plan<R2, NW>;
-    constexpr int TH = P::TH, R1 = P::R1, SW = P::SW;
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ float2 red[2][NW];
-    __shared__ int s_last, s_timeout;
-    float *s0 = reinterpret_cast<float *>(smem + P::U0_OFF);
-    const float *sphi = reinterpret_cast<const float *>(smem + P::PHI_OFF);
-    const float *slam = reinterpret_cast<const float *>(smem + P::LAM_OFF);
-    float *s1 = reinterpret_cast<float *>(smem + P::U1_OFF);
-
-    SolveState *st = d->st;
-    clear_condition(d);
-    if (__ldcg(&st->done)) return;
-    unsigned gen = ld_acquire_gpu(&st->gen);
-    const int H = d->H, W = d->W;
-    const size_t N = (size_t)H * W;
-    const int ntx = (W + kTW2 - 1) / kTW2, nty = (H + TH - 1) / TH;
-    const int nitems = 3 * ntx * nty;
-    const int G = gridDim.x;
-    const int m = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
-    const bool dirichlet = d->dirichlet != 0;
-    float2 *__restrict__ part = d->part;
-    const int nblk = d->nblk;
-    int k = 0;
-    bool failed = false;
-    for (int it = 0; it < d->depth; ++it) {
-        const int cur = __ldcg(&st->cur);
-        const bool rev = (__ldcg(&st->n) & 1) != 0;
-        const bool two = __ldcg(&st->tb2) != 0;
-        const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
-        float *__restrict__ uout = static_cast<float *>(d->u[cur ^ 1]);
-        auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
-        auto tile_xy = [&](int item, int &c, int &x0, int &y0) {
-            const int tile = item / 3;
-            c = item - 3 * tile;
-            x0 = (tile % ntx) * kTW2;
-            y0 = (tile / ntx) * TH;
-            return tile;
-        };
-        auto issue = [&](int j) {
-            int c, x0, y0;
-            tile_xy(item_at(j), c, x0, y0);
-            mbar_arrive_expect_tx(&bar, P::TX);
-            tma_load_3d(smem + P::U0_OFF, tm_u, &bar, x0 - 8, y0 - 4, c);
-            tma_load_3d(smem + P::PHI_OFF, &tm_phi, &bar, x0 - 4, y0 - 2, c);
-            tma_load_2d(smem + P::LAM_OFF, &tm_lam, &bar, x0 - 4, y0 - 2);
-        };
-        auto prefetch = [&](int j) {
-            int c, x0, y0;
-            tile_xy(item_at(j), c, x0, y0);
-            tma_prefetch_3d(tm_u, x0 - 8, y0 - 4, c);
-            tma_prefetch_3d(&tm_phi, x0 - 4, y0 - 2, c);
-            tma_prefetch_2d(&tm_lam, x0 - 4, y0 - 2);
-        };
-        if (threadIdx.x == 0) {
-            if (it > 0) fence_proxy_async_global();
-            if (m > 0) issue(0);
-        }
-        int j = 0;
-        for (; j < m; ++j, ++k) {
-            int c, x0, y0;
-            const int tile = tile_xy(item_at(j), c, x0, y0);
-            if (threadIdx.x == 0 && j + 1 < m) prefetch(j + 1);
-            const bool ok = mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-            // the reflecting boundary on the u^n tile (rows / columns 1-2 outside)
-            if (!dirichlet && (x0 < 8 || y0 < 4 || x0 + kTW2 + 8 > W || y0 + TH + 4 > H)) {
-                reflect_border(s0, SW, SW, TH + 8, x0 - 8, y0 - 4, H, W);
-                fence_proxy_async_smem();  // these writes precede the next TMA load into this buffer
-            }
-            __syncthreads();
-
-            // step 1: region rows y0-2 .. y0+TH+1, columns x0-4 .. x0+123 (frame row t, column 4*lane + j)
-            float rs0 = 0.f, rc0 = 0.f, rs1 = 0.f, rc1 = 0.f;
-            {
-                const int xo = x0 - 4 + 4 * lane;  // output column of this lane's first pixel
-                const bool colin = lane >= 1 && lane <= 30 && xo < W;
-                float *__restrict__ gout = uout + c * N;
-                auto pl = [&](int t, float *ph, float *la) {
-                    const float4 p4 = *reinterpret_cast<const float4 *>(sphi + t * kTW + 4 * lane);
-                    const float4 l4 = *reinterpret_cast<const float4 *>(slam + t * kTW + 4 * lane);
-                    ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
-                    la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
-                };
-                auto sink = [&](int t, const float *nu, const float *F) {
-                    const int yo = y0 - 2 + t;
-                    const bool in = colin && t >= 2 && t < TH + 2 && yo < H;
-                    if (in) {
-                        float q = 0.f;
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) q = fmaf(F[jj], F[jj], q);
-                        neumaier_add(rs0, rc0, q);
-                    }
-                    if (two) {
-                        *reinterpret_cast<float4 *>(s1 + t * SW + 4 * lane) = make_float4(nu[0], nu[1], nu[2], nu[3]);
-                    } else if (in) {
-                        *reinterpret_cast<float4 *>(gout + (size_t)yo * W + xo) = make_float4(nu[0], nu[1], nu[2], nu[3]);
-                    }
-                };
-                walk_rows<R1, SW, float, EDGE>(s0 + 0 * SW, w * R1, lane, eps, tau, wg0, wg1, wg2, pl, sink);
-            }
-            if (two) {
-                __syncthreads();
-                // boundary rule on u^{n+1} (shared rows y0-2.., columns x0-4..)
-                if (x0 < 4 || y0 < 4 || x0 + kTW2 + 4 > W || y0 + TH + 4 > H) {
-                    if (dirichlet) {
-                        for (int e = threadIdx.x; e < (TH + 4) * kTW; e += NW * 32) {
-                            const int r = e / kTW, q = e - r * kTW;
-                            const int gy = y0 - 2 + r, gx = x0 - 4 + q;
-                            if (gy < 0 || gy >= H || gx < 0 || gx >= W) s1[r * SW + q] = 0.f;
-                        }
-                    } else {
-                        reflect_border(s1, SW, kTW, TH + 4, x0 - 4, y0 - 2, H, W);
-                    }
-                    __syncthreads();
-                }
-                // step 2: the tile (frame row t = output row y0 + t, column x0 + 4*lane + j)
-                const int xo = x0 + 4 * lane;
-                const bool colin = lane < 30 && xo < W;
-                float *__restrict__ gout = uout + c * N;
-                auto pl = [&](int t, float *ph, float *la) {
-                    const float4 p4 = *reinterpret_cast<const float4 *>(sphi + (t + 2) * kTW + 4 + 4 * lane);
-                    const float4 l4 = *reinterpret_cast<const float4 *>(slam + (t + 2) * kTW + 4 + 4 * lane);
-                    ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
-                    la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
-                };
-                auto sink = [&](int t, const float *nu, const float *F) {
-                    const int yo = y0 + t;
-                    if (!colin || yo >= H) return;
-                    float q = 0.f;
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) q = fmaf(F[jj], F[jj], q);
-                    neumaier_add(rs1, rc1, q);
-                    *reinterpret_cast<float4 *>(gout + (size_t)yo * W + xo) = make_float4(nu[0], nu[1], nu[2], nu[3]);
-                };
-                walk_rows<R2, SW, float, EDGE>(s1, w * R2, lane, eps, tau, wg0, wg1, wg2, pl, sink);
-            }
-            const float2 t0 = block_pair_sum<NW>(rs0, rc0, red[0]);  // ends with a barrier
-            const float2 t1 = block_pair_sum<NW>(rs1, rc1, red[1]);
-            if (threadIdx.x == 0) {
-                part[(size_t)c * nblk + tile] = t0;
-                part[(size_t)(3 + c) * nblk + tile] = t1;
-                if (j + 1 < m) {
-                    fence_proxy_async_smem();
-                    issue(j + 1);
-                }
-            }
-            __syncthreads();
-        }
-        if (failed) {
-            if (j < m) mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);  // the load in flight
-            if (threadIdx.x == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
-        }
-        // grid barrier; the last CTA to arrive decides
-        fence_proxy_async_global();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            s_last = atomicAdd(&st->arrive, 1u) == (unsigned)G - 1u;
-            s_timeout = 0;
-        }
-        __syncthreads();
-        if (s_last) {
-            finish_tb2(d, st);
-            if (threadIdx.x == 0) {
-                __threadfence();
-                st_release_gpu(&st->gen, gen + 1u);
-            }
-        } else if (threadIdx.x == 0) {
-            const long long t0 = clock64();
-            while (ld_acquire_gpu(&st->gen) == gen) {
-                if (clock64() - t0 > kWaitLimitCycles) {
-                    s_timeout = 1;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        ++gen;
-        __syncthreads();
-        if (s_timeout) {
-            if (threadIdx.x == 0) {
-                atomicCAS(&st->err, 0, DH_ETIMEOUT);
-                st->status = DH_ETIMEOUT;
-                st->done = 1;
-            }
-            return;
-        }
-        if (__ldcg(&st->done) || failed) return;
-    }
-}
-
-// Streaming sweep (W % 4 == 0, 16-byte aligned planes).  Each warp owns
-// segments of a 128-column strip of one channel (tasks) and walks their rows
-// top to bottom.  Lane 0 streams rows into a per-warp ring of NSLOT row slots
-// (u with a 4-column halo, Phi, lambda), one TMA load per array and row, one
-// mbarrier per slot, refilling a slot as soon as the walk has consumed it.
-// The vertical reflecting boundary is applied by loading the reflected row,
-// the horizontal one by substituting the reflected columns in registers.
-// Rows are unrolled in blocks of 20 (the period of the 4- and 5-row register
-// rings), so a segment is a multiple of 20 rows.
-constexpr int kStreamUnroll = 20;
-constexpr uint32_t kRowU = (kTW + 8) * 4;     // 544 bytes
-constexpr uint32_t kRowPhiOff = 640;          // 128-byte aligned offsets in a slot
-constexpr uint32_t kRowLamOff = 1152;
-constexpr uint32_t kRowBytes = 1664;
-
-template <int NW, int NSLOT, bool EDGE>
-__global__ void __launch_bounds__(NW * 32)
-k_sweep_stream(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
-               const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
-               const SolveDesc *__restrict__ d, int seg) {
-    static_assert(NSLOT >= 4 && (NSLOT & (NSLOT - 1)) == 0, "NSLOT: power of two >= 4");
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t bars[NW][NSLOT];
-    __shared__ int s_last;
-
-    SolveState *st = d->st;
-    clear_condition(d);
-    if (__ldcg(&st->done)) return;
-    const int H = d->H, W = d->W;
-    const int cur = __ldcg(&st->cur);
-    const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
-    float *__restrict__ ubase = static_cast<float *>(d->u[cur ^ 1]);
-    const size_t N = (size_t)H * W;
-    const int ntx = (W + kTW - 1) / kTW;
-    const int nseg = (H + seg - 1) / seg;
-    const int ntasks = 3 * ntx * nseg;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int gw = blockIdx.x * NW + w, GW = gridDim.x * NW;
-    const int mytasks = gw < ntasks ? (ntasks - 1 - gw) / GW + 1 : 0;
-    const int P = seg + 4;  // stream positions per task: u rows y0-2 .. y0+seg+1
-    const int total = mytasks * P;
-    unsigned char *ring = smem + (size_t)w * NSLOT * kRowBytes;
-    uint64_t *bar = bars[w];
-    const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
-    float2 *__restrict__ part = d->part;
-    const int nblk = d->nblk;
-
-    if (lane == 0) {
-        for (int k = 0; k < NSLOT; ++k) mbar_init(&bar[k], 1);
-        fence_mbar_init();
-    }
-    __syncwarp();
-
-    // task k of this warp -> (channel, strip, segment)
-    auto task_of = [&](int k, int &c, int &x0, int &y0, int &tile) {
-        const int t = gw + k * GW;
-        c = t % 3;
-        const int r = t / 3;
-        tile = r;
-        x0 = (r % ntx) * kTW;
-        y0 = (r / ntx) * seg;
-    };
-    // Lane 0's issue cursor: positions are issued strictly in order, one per
-    // released slot, so the (task, row) of the next position is advanced
-    // incrementally.
-    int iss_pos = 0, iss_k = 0, iss_o = 0, iss_c = 0, iss_x0 = 0, iss_y0 = 0, iss_tile = 0;
-    if (mytasks > 0) task_of(0, iss_c, iss_x0, iss_y0, iss_tile);
-    auto issue_next = [&]() {  // lane 0 only
-        if (iss_pos >= total) return;
-        const int Y = reflect_idx(iss_y0 - 2 + iss_o, H);
-        const bool pl = iss_o >= 2 && iss_o < seg + 2;
-        const int slot = iss_pos & (NSLOT - 1);
-        unsigned char *sb = ring + slot * kRowBytes;
-        mbar_arrive_expect_tx(&bar[slot], kRowU + (pl ? 2 * kTW * 4 : 0));
-        tma_load_3d(sb, tm_u, &bar[slot], iss_x0 - 4, Y, iss_c);
-        if (pl) {
-            tma_load_3d(sb + kRowPhiOff, &tm_phi, &bar[slot], iss_x0, Y, iss_c);
-            tma_load_2d(sb + kRowLamOff, &tm_lam, &bar[slot], iss_x0, Y);
-        }
-        ++iss_pos;
-        if (++iss_o == P) {
-            iss_o = 0;
-            if (++iss_k < mytasks) task_of(iss_k, iss_c, iss_x0, iss_y0, iss_tile);
-        }
-    };
-    if (lane == 0)
-        for (int k = 0; k < NSLOT; ++k) issue_next();
-
-    bool failed = false;
-    int waited = 0;  // positions [0, waited) have been waited for
-    auto wait_pos = [&](int pos) -> const unsigned char * {
-        const int slot = pos & (NSLOT - 1);
-        const uint32_t parity = (uint32_t)((pos / NSLOT) & 1);
-        const bool ok = mbar_wait_bounded(&bar[slot], parity, kWaitLimitCycles);
-        if (__any_sync(0xffffffffu, !ok)) failed = true;
-        waited = pos + 1;
-        return ring + slot * kRowBytes;
-    };
-    // The walk is done with the oldest slot in use: refill it with the next position.
-    auto release = [&]() {
-        __syncwarp();
-        if (lane == 0) {
-            fence_proxy_async_smem();
-            issue_next();
-        }
-    };
-
-    const float2 W0 = make_float2(wg0, wg0), W1 = make_float2(wg1, wg1), W2 = make_float2(wg2, wg2);
-    const float2 E2 = make_float2(eps, eps), HALF = make_float2(0.5f, 0.5f), TAU = make_float2(tau, tau);
-    const float2 MONE = make_float2(-1.f, -1.f);
-    auto gauss = [&](float2 m2, float2 m1, float2 c0, float2 p1, float2 p2) {
-        return fma2(W2, add2(m2, p2), fma2(W1, add2(m1, p1), mul2(W0, c0)));
-    };
-
-    for (int k = 0; k < mytasks && !failed; ++k) {
-        int c, x0, y0, tile;
-        task_of(k, c, x0, y0, tile);
-        const int p0 = k * P;
-        const int x = x0 + 4 * lane;
-        const bool left = x == 0, right = x + 4 == W;
-        auto load_row = [&](const unsigned char *sb, RowU &u, float2 *g) {
-            const float *row = reinterpret_cast<const float *>(sb) + 4 * lane;
-            float4 L = *reinterpret_cast<const float4 *>(row);
-            const float4 C = *reinterpret_cast<const float4 *>(row + 4);
-            float4 Rr = *reinterpret_cast<const float4 *>(row + 8);
-            if (left) { L.z = C.y; L.w = C.x; }     // u(-2) = u(1), u(-1) = u(0)
-            if (right) { Rr.x = C.w; Rr.y = C.z; }  // u(W) = u(W-1), u(W+1) = u(W-2)
-            const float2 e0 = make_float2(L.z, L.w), e3 = make_float2(Rr.x, Rr.y);
-            u.o0 = make_float2(L.w, C.x);
-            u.e1 = make_float2(C.x, C.y);
-            u.o1 = make_float2(C.y, C.z);
-            u.e2 = make_float2(C.z, C.w);
-            u.o2 = make_float2(C.w, Rr.x);
-            g[0] = gauss(e0, u.o0, u.e1, u.o1, u.e2);
-            g[1] = gauss(u.e1, u.o1, u.e2, u.o2, e3);
-        };
-        auto yfaces = [&](const RowU &a, const RowU &b, float2 *f) {
-            f[0] = face_flux2<EDGE>(sub2(b.e1, a.e1), mul2(HALF, sub2(a.o1, a.o0)), E2);
-            f[1] = face_flux2<EDGE>(sub2(b.e2, a.e2), mul2(HALF, sub2(a.o2, a.o1)), E2);
-        };
-        RowU uu[4];
-        float2 gh[5][2];
-        float2 fyu[2];
-        {
-            RowU dummy;
-            load_row(wait_pos(p0 + 0), dummy, gh[0]);
-            load_row(wait_pos(p0 + 1), uu[0], gh[1]);
-            load_row(wait_pos(p0 + 2), uu[1], gh[2]);
-            load_row(wait_pos(p0 + 3), uu[2], gh[3]);
-            yfaces(uu[0], uu[1], fyu);
-            release();  // rows y0-2, y0-1 carry no Phi/lambda: done with them
-            release();
-        }
-        if (failed) break;
-        float rs = 0.f, rc = 0.f;
-        float *__restrict__ un = ubase + c * N;
-        for (int m = 0; m < seg; m += kStreamUnroll) {
-#pragma unroll
-            for (int j = 0; j < kStreamUnroll; ++j) {
-                const int i = m + j;
-                const RowU &um = uu[(j + 0) & 3];
-                const RowU &u0 = uu[(j + 1) & 3];
-                const RowU &up = uu[(j + 2) & 3];
-                load_row(wait_pos(p0 + 4 + i), uu[(j + 3) & 3], gh[(j + 4) % 5]);
-                const unsigned char *sbo = ring + ((p0 + 2 + i) & (NSLOT - 1)) * kRowBytes;
-                const float4 p4 = *reinterpret_cast<const float4 *>(sbo + kRowPhiOff + 16 * lane);
-                const float4 l4 = *reinterpret_cast<const float4 *>(sbo + kRowLamOff + 16 * lane);
-                const float2 *g_m2 = gh[(j + 0) % 5], *g_m1 = gh[(j + 1) % 5], *g_0 = gh[(j + 2) % 5];
-                const float2 *g_p1 = gh[(j + 3) % 5], *g_p2 = gh[(j + 4) % 5];
-                const float2 fxA = face_flux2<EDGE>(sub2(u0.e1, u0.o0), mul2(HALF, sub2(up.o0, um.o0)), E2);
-                const float2 fxB = face_flux2<EDGE>(sub2(u0.e2, u0.o1), mul2(HALF, sub2(up.o1, um.o1)), E2);
-                const float fx4 = face_flux<EDGE>(__fsub_rn(u0.o2.y, u0.o2.x), half_diff(up.o2.x, um.o2.x), eps);
-                float2 fyd[2];
-                yfaces(u0, up, fyd);
-                const float2 dxA = make_float2(__fsub_rn(fxA.y, fxA.x), __fsub_rn(fxB.x, fxA.y));
-                const float2 dxB = make_float2(__fsub_rn(fxB.y, fxB.x), __fsub_rn(fx4, fxB.y));
-                const float2 dvA = add2(dxA, sub2(fyd[0], fyu[0]));
-                const float2 dvB = add2(dxB, sub2(fyd[1], fyu[1]));
-                const float2 GA = gauss(g_m2[0], g_m1[0], g_0[0], g_p1[0], g_p2[0]);
-                const float2 GB = gauss(g_m2[1], g_m1[1], g_0[1], g_p1[1], g_p2[1]);
-                const float2 FA = add2(fma2(mul2(MONE, make_float2(l4.x, l4.y)), GA, dvA), make_float2(p4.x, p4.y));
-                const float2 FB = add2(fma2(mul2(MONE, make_float2(l4.z, l4.w)), GB, dvB), make_float2(p4.z, p4.w));
-                const float2 nA = fma2(TAU, FA, u0.e1);
-                const float2 nB = fma2(TAU, FB, u0.e2);
-                fyu[0] = fyd[0];
-                fyu[1] = fyd[1];
-                const int y = y0 + i;
-                if (y < H && x < W) {
-                    const float2 q2 = fma2(FB, FB, mul2(FA, FA));
-                    neumaier_add(rs, rc, __fadd_rn(q2.x, q2.y));
-                    *reinterpret_cast<float4 *>(un + (size_t)y * W + x) = make_float4(nA.x, nA.y, nB.x, nB.y);
-                }
-                release();
-            }
-            if (failed) break;
-        }
-        if (failed) break;
-        release();  // look-ahead rows of the segment's end
-        release();
-        for (int off = 16; off; off >>= 1) {
-            const float s2 = __shfl_down_sync(0xffffffffu, rs, off);
-            const float c2 = __shfl_down_sync(0xffffffffu, rc, off);
-            neumaier_merge(rs, rc, s2, c2);
-        }
-        if (lane == 0) part[(size_t)c * nblk + tile] = make_float2(rs, rc);
-    }
-    if (failed) {
-        // let the loads this warp still has in flight land (bounded), then report
-        const int issued = __shfl_sync(0xffffffffu, iss_pos, 0);
-        for (int pos = waited; pos < issued; ++pos)
-            mbar_wait_bounded(&bar[pos & (NSLOT - 1)], (uint32_t)((pos / NSLOT) & 1), kWaitLimitCycles);
-        if (lane == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
-    }
-    arrive_and_finish(d, st, &s_last);
-}
 
 // ------------------------------------------------------------ small kernels
 
@@ -945,89 +100,17 @@ constexpr int kMinTileH = 16;  // smallest tile height any variant uses
 int sweep_depth(const dh_params *) { return 2; }  // residual levels per tile (two-iteration sweep)
 int sweep_tile_h(int) { return kMinTileH; }
 
-typedef void (*SweepFn)(const SolveDesc *);
-typedef void (*SweepTmaFn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const SolveDesc *);
-
+template <class T>
+constexpr int storage_kind() {
+    return sizeof(T) == 4 ? 0 : (Store<T>::TMA_TYPE == CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 ? 1 : 2);
+}
 template <class T>
 static SweepFn sweep_fn(int R, int NW, bool edge) {
-#define DH_SW(r, nw) \
-    if (R == r && NW == nw) return edge ? k_sweep<r, nw, T, true> : k_sweep<r, nw, T, false>;
-    DH_SW(8, 4)
-    if (sizeof(T) == 4) {
-        DH_SW(16, 4)
-        DH_SW(8, 8)
-    }
-#undef DH_SW
-    return nullptr;
+    return sweep_generic_fn(storage_kind<T>(), R, NW, edge);
 }
-
 template <class T>
 static SweepTmaFn sweep_tma_fn(int R, int NW, int stages, int tma, bool edge, int minb, int multi) {
-#define DH_STX(r, nw, st, pls, mb, mu)                                                              \
-    if (R == r && NW == nw && stages == st && tma == (pls ? 1 : 2) && minb == mb && multi == mu)     \
-        return edge ? (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, true, mb, mu>                      \
-                    : (SweepTmaFn)k_sweep_tma<r, nw, st, pls, T, false, mb, mu>;
-#define DH_STM(r, nw, st, pls, mb) DH_STX(r, nw, st, pls, mb, false)
-#define DH_ST(r, nw, st, pls) DH_STM(r, nw, st, pls, 0)
-    DH_ST(8, 4, 1, true)
-    DH_STX(6, 4, 1, true, 5, true)
-    if (sizeof(T) == 4) {
-        DH_STX(8, 4, 1, true, 0, true)
-        DH_STX(4, 4, 1, true, 6, true)
-        DH_STX(6, 4, 1, true, 0, true)
-        DH_STX(4, 4, 2, true, 0, true)
-        DH_ST(4, 4, 2, true)
-        DH_ST(6, 4, 1, true)
-        DH_ST(4, 4, 1, true)
-        DH_ST(16, 2, 1, true)
-        DH_ST(12, 2, 1, true)
-        DH_STM(8, 4, 1, true, 5)
-        DH_STM(6, 4, 1, true, 5)
-        DH_STM(4, 4, 1, true, 6)
-        DH_ST(8, 4, 2, true)
-        DH_ST(4, 8, 2, true)
-        DH_ST(4, 8, 1, true)
-        DH_ST(8, 4, 1, false)
-        DH_ST(8, 4, 2, false)
-        DH_ST(4, 8, 1, false)
-        DH_ST(4, 8, 2, false)
-        DH_ST(16, 4, 1, false)
-        DH_ST(8, 8, 1, false)
-        DH_ST(16, 2, 2, false)
-    }
-#undef DH_ST
-#undef DH_STM
-#undef DH_STX
-    return nullptr;
-}
-
-static SweepTmaFn sweep_tb2_fn(int R, int NW, bool edge) {
-#define DH_TB(r, nw, mb) \
-    if (R == r && NW == nw) return edge ? (SweepTmaFn)k_sweep_tb2<r, nw, true, mb> : (SweepTmaFn)k_sweep_tb2<r, nw, false, mb>;
-    DH_TB(4, 4, 4)
-    DH_TB(6, 4, 3)
-#undef DH_TB
-    return nullptr;
-}
-
-static uint32_t tb2_smem_bytes(int R, int NW) {
-    if (R == 4 && NW == 4) return Tb2Plan<4, 4>::SMEM;
-    if (R == 6 && NW == 4) return Tb2Plan<6, 4>::SMEM;
-    return 0;
-}
-
-typedef void (*SweepStreamFn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const SolveDesc *, int);
-
-static SweepStreamFn sweep_stream_fn(int NW, int NSLOT, bool edge) {
-#define DH_SS(nw, ns) \
-    if (NW == nw && NSLOT == ns) return edge ? k_sweep_stream<nw, ns, true> : k_sweep_stream<nw, ns, false>;
-    DH_SS(4, 8)
-    DH_SS(8, 8)
-    DH_SS(4, 16)
-    DH_SS(2, 8)
-    DH_SS(8, 4)
-#undef DH_SS
-    return nullptr;
+    return sweep_tma_fn_kind(storage_kind<T>(), R, NW, stages, tma, edge, minb, multi);
 }
 
 // Segment height (a multiple of the 20-row unroll) that minimises the waves of
