@@ -164,33 +164,55 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         tile = j / 3;
         c = j - 3 * tile;
     };
-    // this CTA's items: blockIdx.x + j*G; odd loop iterations take them in
-    // reverse, starting on the tiles the previous iteration touched last
-    const int m = (int)blockIdx.x < total ? (total - 1 - (int)blockIdx.x) / G + 1 : 0;
+    // this CTA's items: the contiguous run [lo, hi) of the active item list, so
+    // that consecutive items mostly belong to one image (one tensor-map acquire
+    // and one arrival atomic per image, not per item); odd loop iterations walk
+    // the run in reverse, starting on the tiles this CTA touched last
+    const int lo = (int)((long long)blockIdx.x * total / G), hi = (int)((long long)(blockIdx.x + 1) * total / G);
+    const int m = hi - lo;
     const bool rev = (__ldcg(&hb->iter) & 1) != 0;
-    auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
-    // thread 0, TMA images only: load an item's tiles.  The maps were written
-    // on the device (k_batch_put): acquire them for the tensor-map proxy when
-    // the image changes from the previous load of this CTA.
-    int acq_img = -1;
-    auto issue = [&](int item) {
-        int slot, img, tile, c;
+    const int base = rev ? hi - 1 : lo, step = rev ? -1 : 1;
+    auto item_at = [&](int j) { return base + step * j; };
+    // thread 0, TMA images only: load an item's tiles (or pull them into L2).
+    // The maps were written on the device (k_batch_put): acquire them for the
+    // tensor-map proxy when the image changes from the previous use by this CTA.
+    __shared__ int s_acq_img, s_arr_cnt;  // thread 0's state, kept out of the walk's registers
+    if (threadIdx.x == 0) {
+        s_acq_img = -1;
+        s_arr_cnt = 0;  // finished items of the current image not yet counted
+    }
+    auto maps = [&](int item, int &img, int &slot, int &tile, int &c, int &x0, int &y0) -> const BImg * {
         locate(item, slot, img, tile, c);
-        BImg *im = imgs + img;
-        if (!im->tma) return;
+        const BImg *im = imgs + img;
+        if (!im->tma) return nullptr;
         const int ntx = im->ntx;
-        const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * kBTH;
-        const CUtensorMap *tu = &im->tm[s_cur[slot]];
-        if (img != acq_img) {
-            tensormap_acquire(tu);
+        x0 = (tile % ntx) * kTW;
+        y0 = (tile / ntx) * kBTH;
+        if (img != s_acq_img) {
+            tensormap_acquire(&im->tm[s_cur[slot]]);
             tensormap_acquire(&im->tm[2]);
             tensormap_acquire(&im->tm[3]);
-            acq_img = img;
+            s_acq_img = img;
         }
+        return im;
+    };
+    auto issue = [&](int item) {  // returns the item's image
+        int img, slot, tile, c, x0 = 0, y0 = 0;
+        const BImg *im = maps(item, img, slot, tile, c, x0, y0);
+        if (!im) return img;
         mbar_arrive_expect_tx(&bar, P::TX);
-        tma_load_3d(sb + P::U_OFF, tu, &bar, x0 - 4, y0 - 2, c);
+        tma_load_3d(sb + P::U_OFF, &im->tm[s_cur[slot]], &bar, x0 - 4, y0 - 2, c);
         tma_load_3d(sb + P::PHI_OFF, &im->tm[2], &bar, x0, y0, c);
         tma_load_2d(sb + P::LAM_OFF, &im->tm[3], &bar, x0, y0);
+        return img;
+    };
+    auto prefetch = [&](int item) {
+        int img, slot, tile, c, x0 = 0, y0 = 0;
+        const BImg *im = maps(item, img, slot, tile, c, x0, y0);
+        if (!im) return;
+        tma_prefetch_3d(&im->tm[s_cur[slot]], x0 - 4, y0 - 2, c);
+        tma_prefetch_3d(&im->tm[2], x0, y0, c);
+        tma_prefetch_2d(&im->tm[3], x0, y0);
     };
     if (threadIdx.x == 0 && m > 0) issue(item_at(0));
 
@@ -221,6 +243,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         const int ntx = im->ntx;
         const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * kBTH;
         const int cur = s_cur[slot];
+        if (threadIdx.x == 0 && j + 1 < m) prefetch(item_at(j + 1));
         if (im->tma) {
             const bool ok = mbar_wait_bounded(&bar, kt & 1, kWaitLimitCycles);
             ++kt;
@@ -288,14 +311,19 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
 
         const float2 tot = block_pair_sum<kBNW>(rs, rc, red);  // every thread is past its walk
         if (threadIdx.x == 0) {
+            int next_img = -1;
             if (j + 1 < m) {  // the stage is free: start the next load first
                 fence_proxy_async_smem();
-                issue(item_at(j + 1));
+                next_img = issue(item_at(j + 1));
             }
             d->part[(size_t)c * d->nblk + tile] = tot;
-            __threadfence();
-            const unsigned prev = atomicAdd(&st->arrive, 1u);
-            if (prev == (unsigned)im->items - 1u) s_img_last = img;  // read after the next barrier
+            const unsigned cnt = (unsigned)++s_arr_cnt;
+            if (next_img != img) {  // the run leaves this image: count its items
+                __threadfence();
+                const unsigned prev = atomicAdd(&st->arrive, cnt);
+                if (prev + cnt == (unsigned)im->items) s_img_last = img;  // read after the next barrier
+                s_arr_cnt = 0;
+            }
         }
     }
     __syncthreads();
