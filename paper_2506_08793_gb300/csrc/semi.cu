@@ -54,11 +54,12 @@ struct SiDesc {
     float *xlo;                // its trailing part (u = x + xlo, a double-float pair)
     const float *phi, *lam;
     float *r, *z, *p[2], *q, *dg;
-    float *fx, *fy;            // faces: 3 x H x (W+1), 3 x (H+1) x W
+    float *fx, *fy;            // faces: 3 x H x wf (W+1 used), 3 x (H+1) x W
     float2 *part;              // [6][grid] per-CTA (sum, compensation)
     SiState *st;
     float *rho_hist;
-    int H, W, max_iter, cg_iters, dirichlet, no_edge, zero_lo;
+    int H, W, wf, max_iter, cg_iters, dirichlet, no_edge, zero_lo;
+    int vec;                   // W % 4 == 0, 16-byte aligned planes: the CG passes take 4 pixels a thread
     float tol, inv_s, eps, wg0, wg1, wg2;
 };
 
@@ -95,6 +96,28 @@ __device__ __forceinline__ float coef(float a, float b, float eps, bool no_edge)
     return no_edge ? 1.f : 1.f / (sqrtf(fmaf(a, a, b * b)) + eps);
 }
 
+__device__ __forceinline__ float4 ldca4(const float *p) { return __ldca(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ float4 ldcg4(const float *p) { return __ldcg(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ void st4(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void unpack(const float4 a, float (&v)[4]) {
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+__device__ __forceinline__ float pick3(const float (&v)[3], int ch) { return ch == 0 ? v[0] : (ch == 1 ? v[1] : v[2]); }
+// Neumaier-accumulate x into running sum k (no dynamic register indexing).
+template <int K>
+__device__ __forceinline__ void add_ch(float (&s)[K], float (&c)[K], int k, float x) {
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+        if (q == k) neumaier_add(s[q], c[q], x);
+}
+// One face term of (A v)_i: a coupling face (inside) adds D (v - nb); a border
+// face adds D v under Dirichlet (ghost 0) and drops out under reflection.
+__device__ __forceinline__ float face_term(float a, float D, float v, float nb, bool inside, bool dir) {
+    return inside ? fmaf(D, v - nb, a) : (dir ? fmaf(D, v, a) : a);
+}
+
 // (A v)_i = v_i/s + sum_f D_f (v_i - v_nb); `get(i, j)` reads v inside the image.
 template <class Get>
 __device__ __forceinline__ float apply_A(const SiDesc &d, const float *fxc, const float *fyc, int x, int y,
@@ -102,7 +125,7 @@ __device__ __forceinline__ float apply_A(const SiDesc &d, const float *fxc, cons
     const int H = d.H, W = d.W;
     const bool dir = d.dirichlet != 0;
     float a = d.inv_s * v0, dg = d.inv_s;
-    const float Dl = __ldca(fxc + (size_t)y * (W + 1) + x), Dr = __ldca(fxc + (size_t)y * (W + 1) + x + 1);
+    const float Dl = __ldca(fxc + (size_t)y * d.wf + x), Dr = __ldca(fxc + (size_t)y * d.wf + x + 1);
     const float Du = __ldca(fyc + (size_t)y * W + x), Dd = __ldca(fyc + (size_t)(y + 1) * W + x);
     if (x > 0) { a = fmaf(Dl, v0 - get(x - 1, y), a); dg += Dl; } else if (dir) { a = fmaf(Dl, v0, a); dg += Dl; }
     if (x < W - 1) { a = fmaf(Dr, v0 - get(x + 1, y), a); dg += Dr; } else if (dir) { a = fmaf(Dr, v0, a); dg += Dr; }
@@ -208,7 +231,7 @@ __device__ bool grid_barrier(SiState *st, unsigned &gen, Fin fin) {
     return true;
 }
 
-__global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_constant__ SiDesc d) {
+__global__ void __launch_bounds__(kSiThreads, 3) k_semi_implicit(const __grid_constant__ SiDesc d) {
     SiState *st = d.st;
     const int H = d.H, W = d.W;
     const int N = H * W, E = 3 * N;
@@ -224,7 +247,7 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
         for (int e = e0; e < E; e += T) {
             const int ch = e / N;
             const float v = __ldg(d.phi + e);
-            neumaier_add(s[ch], c[ch], v * v);
+            add_ch(s, c, ch, v * v);
             if (d.zero_lo) d.xlo[e] = 0.f;
         }
         cta_partials<3>(s, c, d.part);
@@ -240,18 +263,18 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
         for (int e = e0; e < E; e += T) {
             const int ch = e / N, pix = e - ch * N, y = pix / W, x = pix - y * W;
             const float *xc = d.x + (size_t)ch * N, *lc = d.xlo + (size_t)ch * N;
-            float *fxc = d.fx + (size_t)ch * H * (W + 1), *fyc = d.fy + (size_t)ch * (H + 1) * W;
+            float *fxc = d.fx + (size_t)ch * H * d.wf, *fyc = d.fy + (size_t)ch * (H + 1) * W;
             auto U = [&](int i, int j) { return ext2(xc, lc, H, W, i, j, dir); };
             const Pair u0 = U(x, y);
             {  // x-face (x+1/2, y), tangential difference at cell x
                 const float a = pdiff(U(x + 1, y), u0);
                 const float b = 0.5f * pdiff(U(x, y + 1), U(x, y - 1));
-                fxc[(size_t)y * (W + 1) + x + 1] = coef(a, b, d.eps, ne);
+                fxc[(size_t)y * d.wf + x + 1] = coef(a, b, d.eps, ne);
             }
             if (x == 0) {  // x-face (-1/2, y): tangential difference at the ghost cell
                 const float a = pdiff(u0, U(-1, y));
                 const float b = 0.5f * pdiff(U(-1, y + 1), U(-1, y - 1));
-                fxc[(size_t)y * (W + 1)] = coef(a, b, d.eps, ne);
+                fxc[(size_t)y * d.wf] = coef(a, b, d.eps, ne);
             }
             {  // y-face (x, y+1/2)
                 const float a = pdiff(U(x, y + 1), u0);
@@ -273,7 +296,7 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
             for (int e = e0; e < E; e += T) {
                 const int ch = e / N, pix = e - ch * N, y = pix / W, x = pix - y * W;
                 const float *xc = d.x + (size_t)ch * N, *lc = d.xlo + (size_t)ch * N;
-                const float *fxc = d.fx + (size_t)ch * H * (W + 1), *fyc = d.fy + (size_t)ch * (H + 1) * W;
+                const float *fxc = d.fx + (size_t)ch * H * d.wf, *fyc = d.fy + (size_t)ch * (H + 1) * W;
                 float g = 0.f;
                 for (int b = -2; b <= 2; ++b) {
                     float h = 0.f;
@@ -283,7 +306,7 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
                 // L_n u^n = sum_f D_f (u_i - u_nb) with pair differences;
                 // diag = 1/s + the faces that couple (all four under Dirichlet)
                 const Pair u0 = ext2(xc, lc, H, W, x, y, dir);
-                const float Dl = __ldca(fxc + (size_t)y * (W + 1) + x), Dr = __ldca(fxc + (size_t)y * (W + 1) + x + 1);
+                const float Dl = __ldca(fxc + (size_t)y * d.wf + x), Dr = __ldca(fxc + (size_t)y * d.wf + x + 1);
                 const float Du = __ldca(fyc + (size_t)y * W + x), Dd = __ldca(fyc + (size_t)(y + 1) * W + x);
                 float Lu = 0.f, dg = d.inv_s;
                 if (x > 0 || dir) { Lu = fmaf(Dl, pdiff(u0, ext2(xc, lc, H, W, x - 1, y, dir)), Lu); dg += Dl; }
@@ -296,8 +319,8 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
                 d.z[e] = z;
                 d.p[0][e] = z;
                 d.dg[e] = dg;
-                neumaier_add(s[ch], c[ch], r * r);
-                neumaier_add(s[3 + ch], c[3 + ch], r * z);
+                add_ch(s, c, ch, r * r);
+                add_ch(s, c, 3 + ch, r * z);
             }
             cta_partials<6>(s, c, d.part);
         }
@@ -335,9 +358,67 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
                 float beta[3];
                 for (int ch = 0; ch < 3; ++ch) beta[ch] = __ldcg(&st->beta[ch]);
                 float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
-                for (int e = e0; e < E; e += T) {
+                // four pixels of a row a thread (W % 4 == 0): 16-byte loads of p
+                // (or z and p_old) on the quad and the rows above and below, single
+                // loads for the left and right neighbours, faces from 16-byte rows;
+                // per pixel the same operations in the same order as apply_A
+                const int Q = W >> 2, HQ = H * Q, NQ = d.vec ? 3 * HQ : 0;
+                for (int g = e0; g < NQ; g += T) {
+                    const int ch = g / HQ, rem = g - ch * HQ, y = rem / Q, x0 = (rem - y * Q) << 2;
+                    const size_t o = (size_t)ch * N + (size_t)y * W + x0;
+                    const bool hu = y > 0, hd = y < H - 1, hl = x0 > 0, hr = x0 + 4 < W;
+                    float v[4], vu[4] = {0.f, 0.f, 0.f, 0.f}, vd[4] = {0.f, 0.f, 0.f, 0.f}, vl = 0.f, vr = 0.f;
+                    if (k == 0) {
+                        unpack(ldca4(pcur + o), v);
+                        if (hu) unpack(ldca4(pcur + o - W), vu);
+                        if (hd) unpack(ldca4(pcur + o + W), vd);
+                        if (hl) vl = __ldca(pcur + o - 1);
+                        if (hr) vr = __ldca(pcur + o + 4);
+                    } else {
+                        const float bt = pick3(beta, ch);
+                        auto p4 = [&](size_t q, float (&out)[4]) {
+                            float a[4], z[4];
+                            unpack(ldca4(pold + q), a);
+                            unpack(ldca4(d.z + q), z);
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) out[i] = fmaf(bt, a[i], z[i]);
+                        };
+                        auto p1 = [&](size_t q) { return fmaf(bt, __ldca(pold + q), __ldca(d.z + q)); };
+                        p4(o, v);
+                        if (hu) p4(o - W, vu);
+                        if (hd) p4(o + W, vd);
+                        if (hl) vl = p1(o - 1);
+                        if (hr) vr = p1(o + 4);
+                        st4(pcur + o, v);
+                    }
+                    const float *fxr = d.fx + (size_t)ch * H * d.wf + (size_t)y * d.wf + x0;
+                    const float *fyr = d.fy + (size_t)ch * (H + 1) * W + (size_t)y * W + x0;
+                    float Dx[5], Du[4], Dd[4];  // Dx[i]: face x0 + i - 1/2
+                    {
+                        float t[4];
+                        unpack(ldca4(fxr), t);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) Dx[i] = t[i];
+                        Dx[4] = __ldca(fxr + 4);
+                    }
+                    unpack(ldca4(fyr), Du);
+                    unpack(ldca4(fyr + W), Dd);
+                    float qv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float a = d.inv_s * v[i];
+                        a = face_term(a, Dx[i], v[i], i > 0 ? v[i - 1] : vl, i > 0 || hl, dir);
+                        a = face_term(a, Dx[i + 1], v[i], i < 3 ? v[i + 1] : vr, i < 3 || hr, dir);
+                        a = face_term(a, Du[i], v[i], vu[i], hu, dir);
+                        a = face_term(a, Dd[i], v[i], vd[i], hd, dir);
+                        qv[i] = a;
+                        add_ch(s, c, ch, v[i] * a);
+                    }
+                    st4(d.q + o, qv);
+                }
+                for (int e = d.vec ? E : e0; e < E; e += T) {
                     const int ch = e / N, pix = e - ch * N, y = pix / W, x = pix - y * W;
-                    const float *fxc = d.fx + (size_t)ch * H * (W + 1), *fyc = d.fy + (size_t)ch * (H + 1) * W;
+                    const float *fxc = d.fx + (size_t)ch * H * d.wf, *fyc = d.fy + (size_t)ch * (H + 1) * W;
                     const size_t base = (size_t)ch * N;
                     float pv, qv;
                     if (k == 0) {
@@ -347,7 +428,7 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
                                      [&](int i, int j) { return __ldca(pc + (size_t)j * W + i); }, nullptr);
                     } else {
                         const float *zc = d.z + base, *oc = pold + base;
-                        const float bt = beta[ch];
+                        const float bt = pick3(beta, ch);
                         auto get = [&](int i, int j) {
                             const size_t o = (size_t)j * W + i;
                             return fmaf(bt, __ldca(oc + o), __ldca(zc + o));
@@ -357,7 +438,7 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
                         qv = apply_A(d, fxc, fyc, x, y, pv, get, nullptr);
                     }
                     d.q[e] = qv;
-                    neumaier_add(s[ch], c[ch], pv * qv);
+                    add_ch(s, c, ch, pv * qv);
                 }
                 cta_partials<3>(s, c, d.part);
             }
@@ -375,9 +456,40 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
                 float alpha[3];
                 for (int ch = 0; ch < 3; ++ch) alpha[ch] = __ldcg(&st->alpha[ch]);
                 float s[3] = {0.f, 0.f, 0.f}, c[3] = {0.f, 0.f, 0.f};
-                for (int e = e0; e < E; e += T) {
+                // four consecutive elements a thread (one channel: N % 4 == 0)
+                const int NQ = d.vec ? E >> 2 : 0;
+                for (int g = e0; g < NQ; g += T) {
+                    const int e = g << 2, ch = e / N;
+                    const float al = pick3(alpha, ch);
+                    float hi[4], lo[4], pv[4], qv[4], rv[4], dg[4];
+                    unpack(ldcg4(d.x + e), hi);
+                    unpack(ldcg4(d.xlo + e), lo);
+                    unpack(ldcg4(pcur + e), pv);
+                    unpack(ldcg4(d.q + e), qv);
+                    unpack(ldcg4(d.r + e), rv);
+                    unpack(ldcg4(d.dg + e), dg);
+                    float zv[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {  // (hi, lo) += alpha p: two-sum, then renormalise
+                        const float dlt = al * pv[i];
+                        const float s1 = hi[i] + dlt, bb = s1 - hi[i];
+                        const float err = (hi[i] - (s1 - bb)) + (dlt - bb);
+                        const float l2 = lo[i] + err;
+                        const float h2 = s1 + l2;
+                        hi[i] = h2;
+                        lo[i] = l2 - (h2 - s1);
+                        rv[i] = fmaf(-al, qv[i], rv[i]);
+                        zv[i] = rv[i] / dg[i];
+                        add_ch(s, c, ch, rv[i] * zv[i]);
+                    }
+                    st4(d.x + e, hi);
+                    st4(d.xlo + e, lo);
+                    st4(d.r + e, rv);
+                    st4(d.z + e, zv);
+                }
+                for (int e = d.vec ? E : e0; e < E; e += T) {
                     const int ch = e / N;
-                    const float al = alpha[ch];
+                    const float al = pick3(alpha, ch);
                     {  // (hi, lo) += alpha p: two-sum, then renormalise
                         const float hi = __ldcg(d.x + e), dlt = al * __ldcg(pcur + e);
                         const float s1 = hi + dlt, bb = s1 - hi;
@@ -391,7 +503,7 @@ __global__ void __launch_bounds__(kSiThreads) k_semi_implicit(const __grid_const
                     const float z = r / __ldcg(d.dg + e);
                     d.r[e] = r;
                     d.z[e] = z;
-                    neumaier_add(s[ch], c[ch], r * z);
+                    add_ch(s, c, ch, r * z);
                 }
                 cta_partials<3>(s, c, d.part);
             }
@@ -426,6 +538,10 @@ __global__ void k_si_reset(SiState *st) {
     st->err = 0;
 }
 
+// Row stride of the x-face planes (W + 1 faces a row), a multiple of 4 so
+// that every row starts on a 16-byte boundary.
+int face_stride(int W) { return (W + 1 + 3) & ~3; }
+
 struct SiLayout {
     size_t state, part, planes, fx, fy, total;
 };
@@ -437,7 +553,7 @@ SiLayout si_layout(int H, int W) {
     L.state = o; o = align_up(o + sizeof(SiState));
     L.part = o; o = align_up(o + (size_t)6 * kSiMaxGrid * sizeof(float2));
     L.planes = o; o = align_up(o + (size_t)7 * 3 * N * sizeof(float));  // r, z, p0, p1, q, diag, u's low part
-    L.fx = o; o = align_up(o + (size_t)3 * H * (W + 1) * sizeof(float));
+    L.fx = o; o = align_up(o + (size_t)3 * H * face_stride(W) * sizeof(float));
     L.fy = o; o = align_up(o + (size_t)3 * (H + 1) * W * sizeof(float));
     L.total = o;
     return L;
@@ -493,6 +609,11 @@ int run_semi_implicit(float *u, float *u_lo, const float *Phi, const float *lam,
     d.rho_hist = rho_hist;
     d.H = H;
     d.W = W;
+    d.wf = face_stride(W);
+    {
+        auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+        d.vec = W % 4 == 0 && a16(d.x) && a16(d.xlo);
+    }
     d.max_iter = p->max_iter;
     d.cg_iters = cg_iters;
     d.dirichlet = p->boundary == DH_BOUNDARY_ZERO;

@@ -128,3 +128,26 @@ def test_whole_method(api, orc):
     # u alone is the float32 rounding of the double-float fixed point: its
     # residual carries the float32 floor ulp(u)/eps, not the solver's 1e-4
     assert rel_res(orc, u, Phi, lam, op) <= 2e-3
+
+
+def test_vector_and_scalar_passes_agree(api, orc):
+    """W % 4 == 0 with 16-byte aligned planes takes the four-pixels-a-thread
+    conjugate-gradient passes; the same problem with u one float off that
+    alignment takes the one-pixel-a-thread passes.  Same arithmetic per pixel,
+    different summation order of the dot products."""
+    _, _, Phi, lam = problem(orc, 937, 36, 92, "stable")
+    p = api.params("stable", tol=0.0, max_iter=3)
+
+    def run(offset):
+        buf = torch.zeros(Phi.size + offset, device="cuda")
+        u = buf[offset:].view(Phi.shape)
+        u.copy_(dev(Phi))
+        lo = torch.zeros_like(u)
+        rep, hist = api.semi_implicit(u, dev(Phi), dev(lam), p, 2.0, 16, history=True, u_lo=lo)
+        return rep, host(u).astype(np.float64) + host(lo), host(hist)
+
+    a, b, a2 = run(0), run(1), run(0)
+    assert a[0].n_iter == b[0].n_iter == 3
+    assert np.array_equal(a[1], a2[1])  # the vector passes are deterministic too
+    assert np.max(np.abs(a[1] - b[1])) <= 1e-5 * max(1.0, np.max(np.abs(a[1])))
+    assert np.max(np.abs(a[2][:4] - b[2][:4])) <= 1e-5
