@@ -197,7 +197,7 @@ typedef struct dh_tune_result {
     int best;               /* fastest usable variant */
     int count;              /* entries below */
     int variant[32];        /* variant ids timed */
-    float us_per_iter[32];  /* device time per iteration (graph loop) */
+    float us_per_iter[32];  /* device time per iteration (graph loop, faster of two rounds) */
 } dh_tune_result;
 
 /* Number of sweep variants (valid ids are 1 .. count-1). */
@@ -206,8 +206,8 @@ int dh_sweep_variants(void);
 /* Autotuner (not in the paper): times every sweep variant usable for an HxW
  * image under *p (float32 storage) on the caller's Phi, lambda (as for
  * dh_fixed_point) for `iters` fixed-point iterations each, in the graph loop,
- * with CUDA events on `stream`; u_scratch (3xHxW) is overwritten.  The fastest
- * is recorded for (current device, H, W) and used by later calls with
+ * with CUDA events on `stream`, in two rounds over all variants (each keeps its
+ * faster time); u_scratch (3xHxW) is overwritten.  The fastest is recorded for (current device, H, W) and used by later calls with
  * sweep_variant = 0.  Waits for the stream.  out may be NULL. */
 int dh_tune(const float *Phi, const float *lam, float *u_scratch, int H, int W, const dh_params *p,
             int iters, void *workspace, size_t workspace_bytes, void *stream, dh_tune_result *out);

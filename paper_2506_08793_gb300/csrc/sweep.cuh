@@ -388,28 +388,35 @@ __device__ __forceinline__ void walk_rows(const T *__restrict__ s, int r0, int l
 template <class T>
 __device__ __forceinline__ void reflect_border(T *s, int stride, int ncols, int nrows, int cx0, int ry0, int H,
                                                int W) {
-    int rows[4], nr = 0, cols[4], nc = 0;
-    for (int g : {-2, -1, H, H + 1}) {
+    // the border rows / columns, one byte each (tiles are under 256 cells a
+    // side), packed in a register rather than a local-memory array
+    unsigned rows = 0, cols = 0;
+    int nr = 0, nc = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int g = k < 2 ? k - 2 : H + k - 2;
         const int r = g - ry0;
-        if (r >= 0 && r < nrows && (g < 0 || g >= H)) rows[nr++] = r;
+        if (r >= 0 && r < nrows && (g < 0 || g >= H)) rows |= (unsigned)r << (8 * nr++);
     }
-    for (int g : {-2, -1, W, W + 1}) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int g = k < 2 ? k - 2 : W + k - 2;
         const int q = g - cx0;
-        if (q >= 0 && q < ncols && (g < 0 || g >= W)) cols[nc++] = q;
+        if (q >= 0 && q < ncols && (g < 0 || g >= W)) cols |= (unsigned)q << (8 * nc++);
     }
     const int nrow_cells = nr * ncols, total = nrow_cells + nc * nrows;
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         int r, q;
         if (e < nrow_cells) {
             const int k = e / ncols;
-            r = rows[k];
+            r = (int)((rows >> (8 * k)) & 0xffu);
             q = e - k * ncols;
             const int gx = cx0 + q;
             const bool fx = gx == -2 || gx == -1 || gx == W || gx == W + 1;
             if (!(fx || (gx >= 0 && gx < W))) continue;
         } else {
             const int e2 = e - nrow_cells, k = e2 / nrows;
-            q = cols[k];
+            q = (int)((cols >> (8 * k)) & 0xffu);
             r = e2 - k * nrows;
             const int gy = ry0 + r;
             if (gy < 0 || gy >= H) continue;  // rows outside were done above (corners included)
