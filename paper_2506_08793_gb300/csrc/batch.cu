@@ -164,14 +164,17 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         tile = j / 3;
         c = j - 3 * tile;
     };
-    // this CTA's items: the contiguous run [lo, hi) of the active item list, so
-    // that consecutive items mostly belong to one image (one tensor-map acquire
-    // and one arrival atomic per image, not per item); odd loop iterations walk
-    // the run in reverse, starting on the tiles this CTA touched last
-    const int lo = (int)((long long)blockIdx.x * total / G), hi = (int)((long long)(blockIdx.x + 1) * total / G);
+    // this CTA's items: one channel of a contiguous run [lo, hi) of the active
+    // tile list (G is a multiple of 3; CTAs 3k, 3k+1, 3k+2 take channels 0, 1, 2
+    // of run k, so the lambda tile the three share is loaded while it is in
+    // L2).  Consecutive items mostly belong to one image: one tensor-map acquire
+    // and one arrival atomic per image, not per item.  Odd loop iterations walk
+    // the run in reverse, starting on the tiles this CTA touched last.
+    const int runs = G / 3, run = (int)blockIdx.x / 3, ch = (int)blockIdx.x - 3 * run, ntiles = total / 3;
+    const int lo = (int)((long long)run * ntiles / runs), hi = (int)((long long)(run + 1) * ntiles / runs);
     const int m = hi - lo;
     const bool rev = (__ldcg(&hb->iter) & 1) != 0;
-    const int base = rev ? hi - 1 : lo, step = rev ? -1 : 1;
+    const int base = 3 * (rev ? hi - 1 : lo) + ch, step = rev ? -3 : 3;
     auto item_at = [&](int j) { return base + step * j; };
     // thread 0, TMA images only: load an item's tiles (or pull them into L2).
     // The maps were written on the device (k_batch_put): acquire them for the
@@ -532,7 +535,9 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
     DH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBNW * 32, smem));
     DH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int grid = total_items < per_sm * sms ? total_items : per_sm * sms;
+    // a multiple of 3 (one CTA per channel of each run of tiles)
+    int grid = total_items < per_sm * sms ? total_items : per_sm * sms;
+    grid = grid < 3 ? 3 : grid - grid % 3;
     BatchHdr *hdr = (BatchHdr *)(ws + B.hdr);
     int launches = 0;
     if (p->use_graph) {
