@@ -19,6 +19,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 
 #include "common.cuh"
@@ -257,26 +258,38 @@ int launch_tc(const bf16 *x, int ldx, int C, int N, int H, int W, const bf16 *w,
 // Layers with few channels (C <= 96 in, <= 96 out) are bound by reading their
 // input, which the general kernel above stages once per tap.  Here a tile is
 // a 128-pixel segment of one image row; its three input rows with a one-pixel
-// margin (3 x 130 pixels x C) are staged once, and each of the nine taps is
-// the same staging viewed through a shifted descriptor.  That needs the
-// non-swizzled K-major layout ("core matrices" of 8 rows x 16 bytes): channel
-// chunk q (8 channels) of pixel p of halo row r at ((r*QC + q)*130 + p)*16
-// bytes, so that for any start pixel the M = 128 rows of a tap are core
-// matrices 128 bytes apart (stride byte offset) and the two 8-channel chunks
-// of a K = 16 step are 130*16 bytes apart (leading byte offset).  All the
-// weights stay in shared memory for the CTA's lifetime, in the same layout
-// ([tap][chunk][cout] rows).  CTAs are persistent over the tiles; the next
-// tile's input is staged while the current tile's MMAs and epilogue run.
+// margin (3 x 130 pixels x C) are loaded once by TMA, one 8-channel chunk at a
+// time (box: 8 channels x 130 pixels x 3 rows = 6240 bytes, zero filled outside
+// the image, each chunk at a 128-byte aligned 6272-byte slot), so that chunk q
+// of pixel p of halo row r sits at q*6272 + (r*130 + p)*16 bytes: the
+// non-swizzled K-major layout ("core matrices" of 8 rows x 16 bytes).  Each of
+// the nine taps is the same staging viewed through a shifted descriptor: for
+// any start pixel the M = 128 rows of a tap are core matrices 128 bytes apart
+// (stride byte offset) and the two chunks of a K = 16 step are 6272 bytes
+// apart (leading byte offset).  With 64 or more input channels, or 96 output
+// channels (one or two CTAs per SM), the halo is instead staged by all threads
+// with 16-byte cp.async copies, consecutive threads on consecutive chunks of a
+// pixel (measured faster there: 96 -> 32 at 1080p 446 vs 578 us; TMA faster
+// for 16 and 32 input channels: 32 -> 32 125 vs 142 us).  All the weights stay in shared memory for the
+// CTA's lifetime ([tap][chunk][cout] 16-byte rows).  CTAs are persistent over
+// the tiles with two halo stages and two TMEM accumulators: while the warps run
+// the epilogue of tile i, the MMAs of tile i+1 run and the loads of tile i+2
+// are in flight.
 template <int C, int CO>
 struct HaloPlan {
     static constexpr int QC = C / 8;                         // 8-channel chunks
     static constexpr uint32_t W_BYTES = 9u * QC * CO * 16;
-    static constexpr uint32_t HALO_BYTES = 3u * QC * 130 * 16;
+    static constexpr uint32_t BOX_BYTES = 3u * 130 * 16;     // one chunk of the three rows
+    static constexpr uint32_t CHUNK_BYTES = (BOX_BYTES + 127) / 128 * 128;  // its slot (TMA: 128-byte aligned)
+    static constexpr uint32_t TX_BYTES = QC * BOX_BYTES;     // bytes a tile's loads deliver
+    static constexpr uint32_t HALO_BYTES = QC * CHUNK_BYTES;
     static constexpr uint32_t W_OFF = 0;
     static constexpr uint32_t H_OFF = (W_BYTES + 1023) / 1024 * 1024;
     static constexpr uint32_t H_STRIDE = (HALO_BYTES + 1023) / 1024 * 1024;
     static constexpr uint32_t SMEM = H_OFF + 2 * H_STRIDE + 1024;
-    static constexpr uint32_t TMEM_COLS = CO <= 32 ? 32 : CO <= 64 ? 64 : 128;
+    static constexpr uint32_t ACC_COLS = CO <= 32 ? 32 : CO <= 64 ? 64 : 128;  // one accumulator
+    static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+    static constexpr bool CP_ASYNC = C >= 64 || CO >= 96;    // staging by cp.async instead of TMA
     static_assert(C % 16 == 0 && CO % 16 == 0 && CO <= 128, "channel counts");
 };
 
@@ -292,17 +305,21 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t lbo, ui
 
 template <int C, int CO>
 __global__ void __launch_bounds__(128)
-k_conv3x3_halo(const bf16 *__restrict__ x, int ldx, int Nimg, int H, int W, const bf16 *__restrict__ w,
-               const float *__restrict__ bias, int relu, bf16 *__restrict__ y, int ldy, int *err) {
+k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__ x, int ldx, int Nimg, int H, int W,
+               const bf16 *__restrict__ w, const float *__restrict__ bias, int relu, bf16 *__restrict__ y, int ldy,
+               int *err) {
     using P = HaloPlan<C, CO>;
     constexpr int QC = P::QC;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ __align__(8) uint64_t tma_bar[2], mma_bar[2];
     __shared__ uint32_t tmem_slot;
+    __shared__ float s_bias[CO];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int segs = (W + 127) / 128;
     const int T = Nimg * H * segs;
+    const int G = gridDim.x;
+    const int nt = (int)blockIdx.x < T ? (T - 1 - (int)blockIdx.x) / G + 1 : 0;  // tiles blockIdx.x + i*G
     const uint32_t sbase = smem_addr(smem);
 
     if (warp == 0) {
@@ -312,84 +329,142 @@ k_conv3x3_halo(const bf16 *__restrict__ x, int ldx, int Nimg, int H, int W, cons
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(&mma_bar, 1);
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&tma_bar[k], 1);
+            mbar_init(&mma_bar[k], 1);
+        }
         fence_mbar_init();
     }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_slot;
-
+    for (int c = tid; c < CO; c += 128) s_bias[c] = bias ? __ldg(bias + c) : 0.f;
     // weights [co][tap][ci] -> shared [tap][chunk][co] 16-byte rows
     for (int e = tid; e < 9 * QC * CO; e += 128) {
         const int co = e % CO, rest = e / CO, q = rest % QC, tap = rest / QC;
         cp_async_16(sbase + P::W_OFF + (uint32_t)e * 16, w + ((size_t)co * 9 + tap) * C + 8 * q, 16u);
     }
-    // thread tid stages halo pixel tid (and tids 0, 1 also pixels 128, 129):
-    // all C channels of it in the three rows
-    auto stage_halo = [&](int t, int stg) {
+    cp_async_commit();
+    cp_async_wait<0>();
+    fence_proxy_async_smem();  // the weights, written by cp.async, are read by the MMAs
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    // thread 0 alone issues the loads and the MMAs and counts them, so that a
+    // CTA that gives up can still let everything in flight finish
+    int n_load = 0, n_load_done = 0, n_mma = 0;
+    auto issue = [&](int i) {  // the halo of tile i into stage i & 1
+        const int t = (int)blockIdx.x + i * G;
         const int seg = t % segs, row = t / segs, n = row / H, yy = row - n * H;
-        const int x0 = seg * 128;
-        const uint32_t hb = sbase + P::H_OFF + stg * P::H_STRIDE;
-        for (int pp = 0; pp < 2; ++pp) {
-            const int p = tid + 128 * pp;
-            if (p >= 130) break;
-            const int gx = x0 + p - 1;
-            const bool colok = gx >= 0 && gx < W;
+        const uint32_t hb = sbase + P::H_OFF + (uint32_t)(i & 1) * P::H_STRIDE;
+        mbar_arrive_expect_tx(&tma_bar[i & 1], P::TX_BYTES);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const int gy = yy + r - 1;
-                const bool ok = colok && gy >= 0 && gy < H;
-                const bf16 *src = ok ? x + ((size_t)(n * H + gy) * W + gx) * ldx : x;
-                const uint32_t dst = hb + (uint32_t)((r * QC * 130 + p) * 16);
-#pragma unroll
-                for (int q = 0; q < QC; ++q)
-                    cp_async_16(dst + (uint32_t)(q * 130 * 16), ok ? src + 8 * q : x, ok ? 16u : 0u);
+        for (int q = 0; q < QC; ++q)
+            tma_load_4d(hb + (uint32_t)q * P::CHUNK_BYTES, &tmx, &tma_bar[i & 1], 8 * q, seg * 128 - 1, yy - 1, n);
+        ++n_load;
+    };
+    constexpr uint32_t IDESC = f16_idesc(kTcBM, CO);
+    auto mmas = [&](int i) {  // the nine taps of tile i into accumulator i & 1
+        const uint32_t hb = sbase + P::H_OFF + (uint32_t)(i & 1) * P::H_STRIDE;
+        const uint32_t acc = tmem + (uint32_t)(i & 1) * P::ACC_COLS;
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;  // halo row, start pixel
+            for (int kk = 0; kk < QC / 2; ++kk) {
+                const uint32_t a = hb + (uint32_t)(2 * kk) * P::CHUNK_BYTES + (uint32_t)((dy * 130 + dx) * 16);
+                const uint32_t b = sbase + P::W_OFF + (uint32_t)((tap * QC + 2 * kk) * CO * 16);
+                tc_mma(acc, kmajor_desc(a, P::CHUNK_BYTES, 128), kmajor_desc(b, CO * 16, 128), IDESC,
+                       (tap > 0 || kk > 0) ? 1u : 0u);
             }
         }
+        tc_commit(&mma_bar[i & 1]);
+        ++n_mma;
     };
-    const int G = gridDim.x;
-    int t = blockIdx.x;
-    if (t < T) stage_halo(t, 0);
-    cp_async_commit();
-    constexpr uint32_t IDESC = f16_idesc(kTcBM, CO);
-    bool failed = false;
-    for (int i = 0; t < T; ++i, t += G) {
-        const int stg = i & 1;
-        if (t + G < T) stage_halo(t + G, stg ^ 1);  // that stage's MMAs finished last iteration
+    // all threads: the halo of tile i into stage i & 1 by cp.async (zero fill
+    // outside the image), one commit group per tile
+    auto stage = [&](int i) {
+        const int t = (int)blockIdx.x + i * G;
+        const int seg = t % segs, row = t / segs, n = row / H, yy = row - n * H;
+        const uint32_t hb = sbase + P::H_OFF + (uint32_t)(i & 1) * P::H_STRIDE;
+        for (int e = tid; e < 390 * QC; e += 128) {
+            const int q = e % QC, rp = e / QC, r = rp / 130, p = rp - r * 130;
+            const int gx = seg * 128 + p - 1, gy = yy + r - 1;
+            const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
+            const bf16 *src = ok ? x + ((size_t)(n * H + gy) * W + gx) * ldx + 8 * q : x;
+            cp_async_16(hb + (uint32_t)q * P::CHUNK_BYTES + (uint32_t)rp * 16, src, ok ? 16u : 0u);
+        }
         cp_async_commit();
-        cp_async_wait<1>();
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
+    };
+    // tile i's halo has landed (thread 0)
+    auto landed = [&](int i) {
+        const bool ok = mbar_wait_bounded(&tma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles);
+        if (ok) ++n_load_done;
+        return ok;
+    };
+
+    bool failed = false;
+    if constexpr (P::CP_ASYNC) {
+        if (nt > 0) stage(0);
+        if (nt > 1) stage(1);
+        if (nt > 0) {
+            cp_async_wait<1>();
+            fence_proxy_async_smem();  // generic-proxy copies, read by the MMAs
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                mmas(0);
+            }
+        }
+    } else if (tid == 0 && nt > 0) {
+        issue(0);
+        if (nt > 1) issue(1);
+        if (landed(0)) {
             tc_fence_after();
-            const uint32_t hb = sbase + P::H_OFF + stg * P::H_STRIDE;
-            for (int tap = 0; tap < 9; ++tap) {
-                const int dy = tap / 3, dx = tap % 3;  // halo row, start pixel
-                for (int kk = 0; kk < QC / 2; ++kk) {
-                    const uint32_t a = hb + (uint32_t)(((dy * QC + 2 * kk) * 130 + dx) * 16);
-                    const uint32_t b = sbase + P::W_OFF + (uint32_t)((tap * QC + 2 * kk) * CO * 16);
-                    tc_mma(tmem, kmajor_desc(a, 130 * 16, 128), kmajor_desc(b, CO * 16, 128), IDESC,
-                           (tap > 0 || kk > 0) ? 1u : 0u);
+            mmas(0);
+        } else {
+            failed = true;
+        }
+    }
+    for (int i = 0; i < nt; ++i) {
+        // the next tile's MMAs run while this tile's epilogue does
+        if constexpr (P::CP_ASYNC) {
+            if (i + 1 < nt) {
+                cp_async_wait<0>();
+                fence_proxy_async_smem();
+                __syncthreads();
+                if (tid == 0 && !failed) {
+                    tc_fence_after();
+                    mmas(i + 1);
                 }
             }
-            tc_commit(&mma_bar);
+        } else if (tid == 0 && !failed && i + 1 < nt) {
+            if (landed(i + 1)) {
+                tc_fence_after();
+                mmas(i + 1);
+            } else {
+                failed = true;
+            }
         }
-        if (!mbar_wait_bounded(&mma_bar, i & 1, kTcWaitCycles)) failed = true;
+        // tile i's MMAs are done: its accumulator is ready and its stage is free
+        if (!failed && !mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles)) failed = true;
         tc_fence_after();
+        if (!failed && i + 2 < nt) {
+            if constexpr (P::CP_ASYNC) stage(i + 2);
+            else if (tid == 0) issue(i + 2);
+        }
         // epilogue: TMEM lane = pixel of the segment
+        const int t = (int)blockIdx.x + i * G;
         const int seg = t % segs, row = t / segs;
         const int px = seg * 128 + warp * 32 + lane;
+        const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(i & 1) * P::ACC_COLS;
 #pragma unroll
         for (int c = 0; c < CO; c += 16) {
             uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+            tmem_ld16(acc + (uint32_t)c, r);
             if (px < W && !failed) {
                 uint32_t packed[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    float v0 = __uint_as_float(r[2 * j]) + (bias ? __ldg(bias + c + 2 * j) : 0.f);
-                    float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? __ldg(bias + c + 2 * j + 1) : 0.f);
+                    float v0 = __uint_as_float(r[2 * j]) + s_bias[c + 2 * j];
+                    float v1 = __uint_as_float(r[2 * j + 1]) + s_bias[c + 2 * j + 1];
                     if (relu) {
                         v0 = fmaxf(v0, 0.f);
                         v1 = fmaxf(v1, 0.f);
@@ -403,10 +478,22 @@ k_conv3x3_halo(const bf16 *__restrict__ x, int ldx, int Nimg, int H, int W, cons
             }
         }
         tc_fence_before();
-        if (__syncthreads_or(failed)) break;  // TMEM and the stage are free for the next tile
+        if (__syncthreads_or(failed)) {  // accumulator i & 1 is free for tile i+2 once all pass here
+            failed = true;
+            break;
+        }
     }
     cp_async_wait<0>();
-    if (failed && err) atomicExch(err, DH_ETIMEOUT);
+    if (failed) {
+        // let every load and MMA thread 0 issued finish (bounded) before the
+        // shared and tensor memory go away
+        if (tid == 0) {
+            for (int k = n_load_done; k < n_load; ++k)
+                mbar_wait_bounded(&tma_bar[k & 1], (uint32_t)(k >> 1) & 1u, kTcWaitCycles);
+            if (n_mma > 0) mbar_wait_bounded(&mma_bar[(n_mma - 1) & 1], (uint32_t)((n_mma - 1) >> 1) & 1u, kTcWaitCycles);
+            if (err) atomicExch(err, DH_ETIMEOUT);
+        }
+    }
     tc_fence_before();
     __syncthreads();
     if (warp == 0)
@@ -414,10 +501,45 @@ k_conv3x3_halo(const bf16 *__restrict__ x, int ldx, int Nimg, int H, int W, cons
                      : "memory");
 }
 
+// The halo kernel's input map: bf16 NHWC activations with a pixel pitch of
+// ldx elements (C of them used), as a 4D tensor (channel, x, y, image) whose
+// box is 8 channels x 130 pixels x 3 rows of one image.
+static int encode_halo_map(CUtensorMap *m, const bf16 *x, int ldx, int C, int N, int H, int W) {
+    static std::mutex mu;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!encode) {
+            void *fn = nullptr;
+            cudaDriverEntryPointQueryResult q;
+            const cudaError_t e =
+                cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+            if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return DH_ECUDA;
+            encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        }
+    }
+    const cuuint64_t pitch = (cuuint64_t)ldx * sizeof(bf16);
+    cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    cuuint64_t strides[3] = {pitch, pitch * (cuuint64_t)W, pitch * (cuuint64_t)W * (cuuint64_t)H};
+    cuuint32_t box[4] = {8, 130, 3, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(x), dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? DH_OK : DH_EINVAL;
+}
+
 template <int C, int CO>
 int launch_halo(const bf16 *x, int ldx, int N, int H, int W, const bf16 *w, const float *b, bool relu, bf16 *y,
                 int ldy, int *err, cudaStream_t s) {
     using P = HaloPlan<C, CO>;
+    if ((uintptr_t)x % 16) return DH_EINVAL;  // TMA and cp.async need a 16-byte aligned base
+    CUtensorMap map;
+    std::memset(&map, 0, sizeof(map));
+    if (!P::CP_ASYNC) {
+        const int rc = encode_halo_map(&map, x, ldx, C, N, H, W);
+        if (rc) return rc;
+    }
     static std::mutex mu;
     static int grid_cache[64] = {};
     int dev = 0;
@@ -439,7 +561,7 @@ int launch_halo(const bf16 *x, int ldx, int N, int H, int W, const bf16 *w, cons
     }
     const long long T = (long long)N * H * ((W + 127) / 128);
     const int grid = (int)(T < grid_cache[dev] ? T : grid_cache[dev]);
-    k_conv3x3_halo<C, CO><<<grid, 128, P::SMEM, s>>>(x, ldx, N, H, W, w, b, relu ? 1 : 0, y, ldy, err);
+    k_conv3x3_halo<C, CO><<<grid, 128, P::SMEM, s>>>(map, x, ldx, N, H, W, w, b, relu ? 1 : 0, y, ldy, err);
     DH_CUDA_TRY(cudaGetLastError());
     return DH_OK;
 }
