@@ -258,66 +258,114 @@ k_bias_grad(const bf16 *__restrict__ dy, int lddy, int Cout, int M, int split_px
 }
 
 // ------------------------------------------------------------ elementwise layers
+// Every activation of the network is bf16 NHWC with channel counts, pitches
+// and channel offsets that are multiples of 8 (16 bytes) and H, W multiples of
+// 8 with N*H*W <= 2^26 (unet_shape_ok): a thread moves 8 channels as one 16-byte
+// vector and the unit indices fit in 32 bits.  Per element the arithmetic (and
+// its order) is that of the plain definitions.
 
-__global__ void k_relu_bwd(bf16 *g, int ldg, const bf16 *__restrict__ y, int ldy, int C, size_t M) {
-    const size_t n = M * C;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t p = i / C;
-        const int c = (int)(i - p * C);
-        if (!(__bfloat162float(y[p * ldy + c]) > 0.f)) g[p * ldg + c] = __float2bfloat16(0.f);
+__device__ __forceinline__ uint4 ld8(const bf16 *p) { return __ldg(reinterpret_cast<const uint4 *>(p)); }
+__device__ __forceinline__ void st8(bf16 *p, uint4 v) { *reinterpret_cast<uint4 *>(p) = v; }
+__device__ __forceinline__ void unpack8(uint4 v, float (&f)[8]) {
+    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 t = __bfloat1622float2(h[j]);
+        f[2 * j] = t.x;
+        f[2 * j + 1] = t.y;
+    }
+}
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+    uint4 v;
+    __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+    return v;
+}
+#define DH_GRID_STRIDE(u, n) for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < (n); u += gridDim.x * blockDim.x)
+
+// ReLU backward: g = 0 where the layer's output y is not positive (M pixels x C)
+__global__ void k_relu_bwd(bf16 *g, int ldg, const bf16 *__restrict__ y, int ldy, int C, int M) {
+    const int G = C / 8;
+    DH_GRID_STRIDE(u, M * G) {
+        const int p = u / G, c = 8 * (u - p * G);
+        bf16 *gp = g + (size_t)p * ldg + c;
+        float gv[8], yv[8];
+        unpack8(*reinterpret_cast<const uint4 *>(gp), gv);
+        unpack8(ld8(y + (size_t)p * ldy + c), yv);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (!(yv[j] > 0.f)) gv[j] = 0.f;
+        st8(gp, pack8(gv));
     }
 }
 
 // 2x2 average pooling: out (H/2 x W/2) from in (H x W)
 __global__ void k_avgpool(const bf16 *__restrict__ in, int ldi, int C, int Nimg, int H, int W, bf16 *out, int ldo) {
-    const int Ho = H / 2, Wo = W / 2;
-    const size_t n = (size_t)Nimg * Ho * Wo * C;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const size_t q = i / C;
-        const int xo = (int)(q % Wo), yo = (int)((q / Wo) % Ho), nn = (int)(q / ((size_t)Wo * Ho));
-        const size_t b = ((size_t)(nn * H + 2 * yo) * W + 2 * xo);
-        const float s = __bfloat162float(in[b * ldi + c]) + __bfloat162float(in[(b + 1) * ldi + c]) +
-                        __bfloat162float(in[(b + W) * ldi + c]) + __bfloat162float(in[(b + W + 1) * ldi + c]);
-        out[q * ldo + c] = __float2bfloat16(0.25f * s);
+    const int Ho = H / 2, Wo = W / 2, G = C / 8;
+    DH_GRID_STRIDE(u, Nimg * Ho * Wo * G) {
+        const int q = u / G, c = 8 * (u - q * G);
+        const int xo = q % Wo, r = q / Wo, yo = r % Ho, nn = r / Ho;
+        const size_t b = (size_t)(nn * H + 2 * yo) * W + 2 * xo;
+        float a[8], e[8], f[8], h[8], o[8];
+        unpack8(ld8(in + b * ldi + c), a);
+        unpack8(ld8(in + (b + 1) * ldi + c), e);
+        unpack8(ld8(in + (b + W) * ldi + c), f);
+        unpack8(ld8(in + (b + W + 1) * ldi + c), h);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = 0.25f * (a[j] + e[j] + f[j] + h[j]);
+        st8(out + (size_t)q * ldo + c, pack8(o));
     }
 }
 
 // d_in (H x W) += d_out (H/2 x W/2) / 4 at each of the four positions
 __global__ void k_avgpool_bwd_add(const bf16 *__restrict__ gout, int ldo, int C, int Nimg, int H, int W, bf16 *gin, int ldi) {
-    const size_t n = (size_t)Nimg * H * W * C;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const size_t p = i / C;
-        const int xx = (int)(p % W), yy = (int)((p / W) % H), nn = (int)(p / ((size_t)W * H));
-        const size_t q = ((size_t)(nn * (H / 2) + yy / 2) * (W / 2) + xx / 2);
-        const float g = __bfloat162float(gin[p * ldi + c]) + 0.25f * __bfloat162float(gout[q * ldo + c]);
-        gin[p * ldi + c] = __float2bfloat16(g);
+    const int G = C / 8;
+    DH_GRID_STRIDE(u, Nimg * H * W * G) {
+        const int p = u / G, c = 8 * (u - p * G);
+        const int xx = p % W, r = p / W, yy = r % H, nn = r / H;
+        const size_t q = (size_t)(nn * (H / 2) + yy / 2) * (W / 2) + xx / 2;
+        bf16 *gp = gin + (size_t)p * ldi + c;
+        float gi[8], go[8];
+        unpack8(*reinterpret_cast<const uint4 *>(gp), gi);
+        unpack8(ld8(gout + q * ldo + c), go);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) gi[j] = gi[j] + 0.25f * go[j];
+        st8(gp, pack8(gi));
     }
 }
 
-// nearest 2x upsampling: out (2H x 2W) from in (H x W)
+// nearest 2x upsampling: out (2H x 2W) from in (H x W); a thread reads one
+// input vector and writes its 2x2 block
 __global__ void k_upsample(const bf16 *__restrict__ in, int ldi, int C, int Nimg, int H, int W, bf16 *out, int ldo) {
-    const size_t n = (size_t)Nimg * 4 * H * W * C;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const size_t p = i / C;
-        const int xx = (int)(p % (2 * W)), yy = (int)((p / (2 * W)) % (2 * H)), nn = (int)(p / ((size_t)4 * W * H));
-        out[p * ldo + c] = in[((size_t)(nn * H + yy / 2) * W + xx / 2) * ldi + c];
+    const int G = C / 8;
+    DH_GRID_STRIDE(u, Nimg * H * W * G) {
+        const int p = u / G, c = 8 * (u - p * G);
+        const int xx = p % W, r = p / W, yy = r % H, nn = r / H;
+        const uint4 v = ld8(in + (size_t)p * ldi + c);
+        const size_t b = (size_t)(nn * 2 * H + 2 * yy) * (2 * W) + 2 * xx;
+        st8(out + b * ldo + c, v);
+        st8(out + (b + 1) * ldo + c, v);
+        st8(out + (b + 2 * W) * ldo + c, v);
+        st8(out + (b + 2 * W + 1) * ldo + c, v);
     }
 }
 
 // d_in (H x W) = sum of the four d_out (2H x 2W) it was copied to
 __global__ void k_upsample_bwd(const bf16 *__restrict__ gout, int ldo, int C, int Nimg, int H, int W, bf16 *gin, int ldi) {
-    const size_t n = (size_t)Nimg * H * W * C;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const size_t p = i / C;
-        const int xx = (int)(p % W), yy = (int)((p / W) % H), nn = (int)(p / ((size_t)W * H));
-        const size_t b = ((size_t)(nn * 2 * H + 2 * yy) * 2 * W + 2 * xx);
-        const float s = __bfloat162float(gout[b * ldo + c]) + __bfloat162float(gout[(b + 1) * ldo + c]) +
-                        __bfloat162float(gout[(b + 2 * W) * ldo + c]) + __bfloat162float(gout[(b + 2 * W + 1) * ldo + c]);
-        gin[p * ldi + c] = __float2bfloat16(s);
+    const int G = C / 8;
+    DH_GRID_STRIDE(u, Nimg * H * W * G) {
+        const int p = u / G, c = 8 * (u - p * G);
+        const int xx = p % W, r = p / W, yy = r % H, nn = r / H;
+        const size_t b = (size_t)(nn * 2 * H + 2 * yy) * (2 * W) + 2 * xx;
+        float a[8], e[8], f[8], h[8], o[8];
+        unpack8(ld8(gout + b * ldo + c), a);
+        unpack8(ld8(gout + (b + 1) * ldo + c), e);
+        unpack8(ld8(gout + (b + 2 * W) * ldo + c), f);
+        unpack8(ld8(gout + (b + 2 * W + 1) * ldo + c), h);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = a[j] + e[j] + f[j] + h[j];
+        st8(gin + (size_t)p * ldi + c, pack8(o));
     }
 }
 
@@ -325,17 +373,23 @@ __global__ void k_upsample_bwd(const bf16 *__restrict__ gout, int ldo, int C, in
 // Phi^B, 0 ...) padded to 16
 __global__ void k_pack_input(const float *__restrict__ I, const float *__restrict__ t, const float *__restrict__ A,
                              const float *__restrict__ Phi, int Nimg, int H, int W, bf16 *x) {
-    const size_t HW = (size_t)H * W, n = (size_t)Nimg * HW;
-    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
-        const size_t nn = p / HW, q = p - nn * HW;
+    const int HW = H * W;
+    DH_GRID_STRIDE(p, Nimg * HW) {
+        const int nn = p / HW, q = p - nn * HW;
+        const size_t o = (size_t)nn * 3 * HW + q;
         float v[16];
-        for (int c = 0; c < 3; ++c) v[c] = I[(nn * 3 + c) * HW + q];
-        v[3] = t[nn * HW + q];
-        for (int c = 0; c < 3; ++c) v[4 + c] = A[nn * 3 + c];
-        for (int c = 0; c < 3; ++c) v[7 + c] = Phi[(nn * 3 + c) * HW + q];
+        for (int c = 0; c < 3; ++c) v[c] = __ldg(I + o + (size_t)c * HW);
+        v[3] = __ldg(t + (size_t)nn * HW + q);
+        for (int c = 0; c < 3; ++c) v[4 + c] = __ldg(A + nn * 3 + c);
+        for (int c = 0; c < 3; ++c) v[7 + c] = __ldg(Phi + o + (size_t)c * HW);
         for (int c = 10; c < 16; ++c) v[c] = 0.f;
-        __nv_bfloat162 *d = reinterpret_cast<__nv_bfloat162 *>(x + p * 16);
-        for (int c = 0; c < 8; ++c) d[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+        float lo[8], hi[8];
+        for (int c = 0; c < 8; ++c) {
+            lo[c] = v[c];
+            hi[c] = v[8 + c];
+        }
+        st8(x + (size_t)p * 16, pack8(lo));
+        st8(x + (size_t)p * 16 + 8, pack8(hi));
     }
 }
 
@@ -343,15 +397,19 @@ __global__ void k_pack_input(const float *__restrict__ I, const float *__restric
 // sum_c hw[o][c] x[p][c] (fp32 out, planar)
 __global__ void k_head(const bf16 *__restrict__ x, int ldx, int C, const float *__restrict__ hw, const float *__restrict__ hb,
                        const float *__restrict__ Phi, int Nimg, int H, int W, float *y) {
-    const size_t HW = (size_t)H * W, n = (size_t)Nimg * HW;
-    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (size_t)gridDim.x * blockDim.x) {
-        const size_t nn = p / HW, q = p - nn * HW;
-        float s[3] = {hb[0] + Phi[(nn * 3) * HW + q], hb[1] + Phi[(nn * 3 + 1) * HW + q], hb[2] + Phi[(nn * 3 + 2) * HW + q]};
-        for (int c = 0; c < C; ++c) {
-            const float v = __bfloat162float(x[p * ldx + c]);
-            for (int o = 0; o < 3; ++o) s[o] = fmaf(hw[o * C + c], v, s[o]);
+    const int HW = H * W;
+    DH_GRID_STRIDE(p, Nimg * HW) {
+        const int nn = p / HW, q = p - nn * HW;
+        const size_t o = (size_t)nn * 3 * HW + q;
+        float s[3] = {__ldg(hb) + __ldg(Phi + o), __ldg(hb + 1) + __ldg(Phi + o + HW), __ldg(hb + 2) + __ldg(Phi + o + 2 * (size_t)HW)};
+        for (int c0 = 0; c0 < C; c0 += 8) {
+            float v[8];
+            unpack8(ld8(x + (size_t)p * ldx + c0), v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                for (int k = 0; k < 3; ++k) s[k] = fmaf(__ldg(hw + k * C + c0 + j), v[j], s[k]);
         }
-        for (int o = 0; o < 3; ++o) y[(nn * 3 + o) * HW + q] = s[o];
+        for (int k = 0; k < 3; ++k) y[o + (size_t)k * HW] = s[k];
     }
 }
 
@@ -742,8 +800,8 @@ static int net_backward(const float *params, int b, const float *target, int N, 
         k_head_bwd<16><<<hb, 256, 0, s>>>(BF(L.d1.off), b, params + P.hw, gy, N, H, W, BF(L.g_d1.off), b, hpart);
     k_sum_splits<<<1, 256, 0, s>>>(hpart, hb, (size_t)(3 * b + 3), grads + P.hw, 0);
     auto relu_b = [&](bf16 *g, int ldg, const bf16 *yv, int ldy, int C, int lvl) {
-        const size_t M = (size_t)N * (H >> lvl) * (W >> lvl);
-        k_relu_bwd<<<gs(M * C), 256, 0, s>>>(g, ldg, yv, ldy, C, M);
+        const int M = N * (H >> lvl) * (W >> lvl);
+        k_relu_bwd<<<gs((size_t)M * C / 8), 256, 0, s>>>(g, ldg, yv, ldy, C, M);
     };
     // conv k: y = conv_k(x); dy given -> dw, db, and (if gx) gx = dgrad
     auto conv_b = [&](int k, const bf16 *x, int ldx, const bf16 *dy, int lddy, int lvl, bf16 *gx, int ldgx) {
