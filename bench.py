@@ -16,6 +16,7 @@ import argparse
 import hashlib
 import json
 import os
+import math
 import statistics
 import subprocess
 import sys
@@ -153,6 +154,53 @@ def batch_extra(api, p, n=64, reps=3):
     return {"images": n, "sizes": "uniform over 480x640, 720x1280, 1080x1920, 1200x1600 (seed 3000)",
             "images_per_s": n / t, "value": units / t, "unit": UNIT, "ms": 1e3 * t,
             "all_converged": all(x.status == 0 for x in r)}
+
+
+def storage16_extra(api, p, n=64):
+    """The uneven 64-image batch with 16-bit iterate storage: pure bf16 / fp16
+    (which stall above 1e-4; run to the float32 batch's largest n) and the
+    switched forms (16-bit until an image's residual stalls, then float32 to
+    1e-4).  Per image: max-abs of u and PSNR of J against the float32 batch on
+    the same images (the float32 path itself agrees with the FP64 oracle to
+    about 1e-5 in the parity tests)."""
+    import torch
+
+    from paper_2506_08793_gb300 import scenes
+
+    sizes = scenes.batch_sizes(3000, n)
+    imgs = [torch.from_numpy(scenes.hazy_scene(3000 + k, H, W)["I"]).cuda() for k, (H, W) in enumerate(sizes)]
+    ref = api.BatchDehazer(sizes, p)
+    ref(imgs)
+    r32 = ref(imgs)
+    u32 = [o["u"].clone() for o in ref.out]
+    j32 = [o["J"].clone() for o in ref.out]
+    nmax = max(x.n_iter for x in r32)
+    out = {"images": n, "reference": "float32 batch of the same images",
+           "float32": {"ms": r32[0].ms, "images_per_s": n / (r32[0].ms / 1e3)}}
+    del ref
+    for name, st in (("bf16", 1), ("fp16", 2), ("bf16_f32", 3), ("fp16_f32", 4)):
+        pure = st in (1, 2)
+        q = p.replace(storage=st, max_iter=nmax) if pure else p.replace(storage=st)
+        b = api.BatchDehazer(sizes, q)
+        b(imgs)  # warm-up (graph build)
+        rep = b(imgs)
+        maxabs, psnr = [], []
+        for o, u, J in zip(b.out, u32, j32):
+            maxabs.append(float((o["u"] - u).abs().max()))
+            mse = float(((o["J"] - J) ** 2).mean())
+            psnr.append(None if mse == 0 else 10 * math.log10(1.0 / mse))
+        finite = [x for x in psnr if x is not None]
+        out[name] = {"ms": rep[0].ms, "images_per_s": n / (rep[0].ms / 1e3),
+                     "max_iter": nmax if pure else q.max_iter,
+                     "converged_to_tol": sum(x.status == 0 for x in rep),
+                     "iterations": {"min": min(x.n_iter for x in rep), "max": max(x.n_iter for x in rep)},
+                     "max_abs_u": {"max": max(maxabs), "median": statistics.median(maxabs)},
+                     "psnr_J_db": {"min": min(finite) if finite else None,
+                                   "median": statistics.median(finite) if finite else None,
+                                   "identical_images": len(psnr) - len(finite)}}
+        del b
+        torch.cuda.empty_cache()
+    return out
 
 
 def semi_extra(api, im, step=2.0, cg_iters=32):
@@ -395,6 +443,7 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_extras:
         line["batch"] = batch_extra(api, p)
+        line["batch_16bit_storage"] = storage16_extra(api, p)
         line["warm_start"] = warm_extra(api, p, imgs[0])
         line["semi_implicit"] = semi_extra(api, imgs[0])
         line["refinements"] = refine_extra(api, imgs[0])

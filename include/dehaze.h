@@ -229,12 +229,14 @@ typedef struct dh_image {
 /* Workspace bytes dh_dehaze_batch needs for these images (0 if invalid). */
 size_t dh_batch_workspace_bytes(int n, const dh_image *imgs, const dh_params *p);
 
-/* The whole method on n <= 256 images of any sizes (float32 storage).  The
- * front end (Sec. II-D, II-A) runs per image; the fixed-point loops (App. A-A)
- * of all images run in one CUDA graph while loop whose body is ONE persistent
- * sweep launch over the (128x32 tile, channel) items of every image still
- * iterating; each image stops on its own residual or max_iter, exactly as in
- * dh_dehaze, and leaves the batch's work list.  reports: host array of n or
+/* The whole method on n <= 256 images of any sizes.  The front end (Sec.
+ * II-D, II-A) runs per image; the fixed-point loops (App. A-A) of all images
+ * run in one CUDA graph while loop whose body is ONE persistent sweep launch
+ * over the (128x24 tile, channel) items of every image still iterating; each
+ * image stops on its own residual or max_iter, exactly as in dh_dehaze, and
+ * leaves the batch's work list.  p->storage may be any DH_STORE_*: with the
+ * switched forms every image runs 16-bit until its own residual stalls, then
+ * all such images continue in float32 from their n in a second loop.  reports: host array of n or
  * NULL; with reports the call waits and reports[i].ms is the batch's time.
  * Returns the first error, else the first warning, else DH_OK. */
 int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *workspace,

@@ -20,6 +20,8 @@ int launch_select_A(const float *I, const float *dc, int H, int W, int permille,
                     long long *index_out, char *ws, const WsLayout &L, cudaStream_t s);
 int launch_output_f32(const SolveDesc *desc_dev, float *J, float *u, size_t n3, cudaStream_t s);
 int encode_f32_map(CUtensorMap *m, const void *base, int rank, int W, int H, int C, int boxW, int boxH);
+int encode_tiled(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *base, const cuuint64_t *dims,
+                 const cuuint64_t *strides, const cuuint32_t *box);
 int sweep_tile_h(int depth);
 
 constexpr int kMaxBatch = 256;
@@ -74,7 +76,7 @@ struct PutChunk {
     BImg rec[kPutChunk];
 };
 
-__global__ void k_batch_put(BImg *dst, const __grid_constant__ PutChunk ch, int count) {
+__global__ void k_batch_put(BImg *dst, const __grid_constant__ PutChunk ch, int count, int reset) {
     const int words = (int)(sizeof(BImg) / 4);
     for (int r = 0; r < count; ++r) {
         const unsigned *src = reinterpret_cast<const unsigned *>(&ch.rec[r]);
@@ -82,7 +84,7 @@ __global__ void k_batch_put(BImg *dst, const __grid_constant__ PutChunk ch, int 
         for (int k = threadIdx.x; k < words; k += blockDim.x) d[k] = src[k];
     }
     __syncthreads();
-    if (threadIdx.x < count) {
+    if (reset && threadIdx.x < count) {
         SolveState *st = ch.rec[threadIdx.x].d.st;
         st->arrive = 0;
         st->n = 0;
@@ -106,20 +108,58 @@ __global__ void k_batch_init(BatchHdr *h, BImg *imgs, int n, int use_cond, unsig
     h->arrive = 0;
     h->use_cond = use_cond;
     h->cond = cond;
-    int acc = 0;
+    int acc = 0, k = 0;
     for (int i = 0; i < n; ++i) {
-        h->active[i] = i;
-        h->prefix[i] = acc;
+        if (__ldcg(&imgs[i].d.st->done)) continue;  // finished in an earlier precision phase
+        h->active[k] = i;
+        h->prefix[k] = acc;
         acc += imgs[i].items;
+        ++k;
     }
-    h->prefix[n] = acc;
+    h->prefix[k] = acc;
+    h->nactive = k;
 }
 
-template <bool EDGE>
+// 16-bit iterate storage: u0 (float32) into the first iterate buffer
+template <class T>
+__global__ void k_b_to16(const float *__restrict__ src, T *__restrict__ dst, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        Store<T>::put(dst + i, src[i]);
+}
+
+// End of an image's 16-bit loop: u^n (in d->u[cur]) as float32 into u_out and,
+// when J is given, J = clamp(u^n, 0, 1).
+template <class T>
+__global__ void k_b_from16(const SolveDesc *__restrict__ d, float *u_out, float *J) {
+    const int cur = __ldcg(&d->st->cur);
+    const size_t n3 = (size_t)3 * d->H * d->W;
+    const T *src = static_cast<const T *>(d->u[cur]);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+        const float v = Store<T>::get(src + i);
+        u_out[i] = v;
+        if (J) J[i] = fminf(fmaxf(v, 0.f), 1.f);
+    }
+}
+
+// Hands an image to the float32 phase: its iterate now sits in buffer 0; a
+// stalled 16-bit phase continues from the same n, any other outcome is final.
+__global__ void k_b_handoff(SolveState *st) {
+    st->cur = 0;
+    st->arrive = 0;
+    if (st->status == kStatusSwitch) {
+        st->done = 0;
+        st->status = 0;
+        st->phase_start = st->n;
+    }
+}
+
+
+// T: storage of the iterates (float, or bf16 / fp16 with float arithmetic)
+template <bool EDGE, class T>
 __global__ void __launch_bounds__(kBNW * 32, 5)
 k_sweep_batch(BatchHdr *__restrict__ hb) {
-    using P = TmaPlan<kBTH, true, float>;
-    constexpr int SW = P::SW, SH = P::SH;
+    using P = TmaPlan<kBTH, true, T>;
+    constexpr int SW = P::SW, SH = P::SH, HALO = Store<T>::HALO;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *sb = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t bar;
@@ -146,7 +186,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
     const int total = s_prefix[nact];
     BImg *imgs = hb->imgs;
     const int G = gridDim.x;
-    float *s = reinterpret_cast<float *>(sb + P::U_OFF);
+    T *s = reinterpret_cast<T *>(sb + P::U_OFF);
     float *sphi = reinterpret_cast<float *>(sb + P::PHI_OFF);
     float *slam = reinterpret_cast<float *>(sb + P::LAM_OFF);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -204,7 +244,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         const BImg *im = maps(item, img, slot, tile, c, x0, y0);
         if (!im) return img;
         mbar_arrive_expect_tx(&bar, P::TX);
-        tma_load_3d(sb + P::U_OFF, &im->tm[s_cur[slot]], &bar, x0 - 4, y0 - 2, c);
+        tma_load_3d(sb + P::U_OFF, &im->tm[s_cur[slot]], &bar, x0 - HALO, y0 - 2, c);
         tma_load_3d(sb + P::PHI_OFF, &im->tm[2], &bar, x0, y0, c);
         tma_load_2d(sb + P::LAM_OFF, &im->tm[3], &bar, x0, y0);
         return img;
@@ -213,7 +253,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         int img, slot, tile, c, x0 = 0, y0 = 0;
         const BImg *im = maps(item, img, slot, tile, c, x0, y0);
         if (!im) return;
-        tma_prefetch_3d(&im->tm[s_cur[slot]], x0 - 4, y0 - 2, c);
+        tma_prefetch_3d(&im->tm[s_cur[slot]], x0 - HALO, y0 - 2, c);
         tma_prefetch_3d(&im->tm[2], x0, y0, c);
         tma_prefetch_2d(&im->tm[3], x0, y0);
     };
@@ -256,21 +296,23 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
             }
             finish_pending();
             if (!d->dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + kBTH + 2 > H)) {
-                reflect_border(s, SW, SW, SH, x0 - 4, y0 - 2, H, W);
+                reflect_border(s, SW, SW, SH, x0 - HALO, y0 - 2, H, W);
                 fence_proxy_async_smem();
             }
         } else {
             __syncthreads();
             finish_pending();
             // gather the tile with the reflecting boundary (W % 4 != 0 or unaligned image)
-            const float *u = static_cast<const float *>(d->u[cur]) + c * N;
+            const T *u = static_cast<const T *>(d->u[cur]) + c * N;
             for (int e = threadIdx.x; e < SH * SW; e += kBNW * 32) {
                 const int r = e / SW, q = e - r * SW;
-                const int yy = y0 - 2 + r, xx = x0 - 4 + q;
-                if (d->dirichlet)
-                    s[e] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? u[(size_t)yy * W + xx] : 0.f;
-                else
+                const int yy = y0 - 2 + r, xx = x0 - HALO + q;
+                if (!d->dirichlet)
                     s[e] = u[(size_t)reflect_idx(yy, H) * W + reflect_idx(xx, W)];
+                else if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                    s[e] = u[(size_t)yy * W + xx];
+                else
+                    Store<T>::put(s + e, 0.f);
             }
             for (int e = threadIdx.x; e < kBTH * kTW; e += kBNW * 32) {
                 const int r = e / kTW, q = e - r * kTW;
@@ -283,9 +325,9 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         }
         __syncthreads();
 
-        float *__restrict__ un = static_cast<float *>(d->u[cur ^ 1]) + c * N;
+        T *__restrict__ un = static_cast<T *>(d->u[cur ^ 1]) + c * N;
         const int x = x0 + 4 * lane;
-        const bool vec = im->tma != 0;  // aligned planes, W % 4 == 0
+        const bool vec = im->tma != 0;  // aligned planes, W % 4 == 0 (W % 8 == 0 for 16-bit storage)
         float rs = 0.f, rc = 0.f;
         auto pl = [&](int ty, float *ph, float *la) {
             const float4 p4 = *reinterpret_cast<const float4 *>(sphi + ty * kTW + 4 * lane);
@@ -303,14 +345,14 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
                 if (x + j < W) q = fmaf(F[j], F[j], q);
             neumaier_add(rs, rc, q);
             if (vec) {
-                *reinterpret_cast<float4 *>(un + ro + x) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+                Store<T>::write4(un + ro + x, nu[0], nu[1], nu[2], nu[3]);
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
-                    if (x + j < W) un[ro + x + j] = nu[j];
+                    if (x + j < W) Store<T>::put(un + ro + x + j, nu[j]);
             }
         };
-        walk_rows<kBR, SW, float, EDGE>(s, w * kBR, lane, d->eps, d->tau, d->wg0, d->wg1, d->wg2, pl, sink);
+        walk_rows<kBR, SW, T, EDGE>(s, w * kBR, lane, d->eps, d->tau, d->wg0, d->wg1, d->wg2, pl, sink);
 
         const float2 tot = block_pair_sum<kBNW>(rs, rc, red);  // every thread is past its walk
         if (threadIdx.x == 0) {
@@ -374,21 +416,33 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
 
 // ------------------------------------------------------------ host
 
+// storage kind: 0 float32, 1 bf16, 2 fp16
+static void *batch_fn(bool edge, int kind) {
+    if (kind == 1) return edge ? (void *)k_sweep_batch<true, __nv_bfloat16> : (void *)k_sweep_batch<false, __nv_bfloat16>;
+    if (kind == 2) return edge ? (void *)k_sweep_batch<true, __half> : (void *)k_sweep_batch<false, __half>;
+    return edge ? (void *)k_sweep_batch<true, float> : (void *)k_sweep_batch<false, float>;
+}
+static unsigned batch_smem(int kind) {
+    return (kind ? TmaPlan<kBTH, true, __half>::STAGE : TmaPlan<kBTH, true, float>::STAGE) + 1024;
+}
+
+
 struct BatchGraph {
     int dev;
     const void *hdr;
     int grid;
     int edge;
+    int kind;
     cudaGraphExec_t exec;
     cudaGraphConditionalHandle cond;
 };
 static std::mutex g_bmu;
 static std::vector<BatchGraph> g_bcache;
 
-static int batch_graph(int dev, BatchHdr *hdr, int grid, bool edge, unsigned smem, BatchGraph *out) {
+static int batch_graph(int dev, BatchHdr *hdr, int grid, bool edge, int kind, unsigned smem, BatchGraph *out) {
     std::lock_guard<std::mutex> lk(g_bmu);
     for (auto &e : g_bcache)
-        if (e.dev == dev && e.hdr == hdr && e.grid == grid && e.edge == (edge ? 1 : 0)) {
+        if (e.dev == dev && e.hdr == hdr && e.grid == grid && e.edge == (edge ? 1 : 0) && e.kind == kind) {
             *out = e;
             return DH_OK;
         }
@@ -408,7 +462,7 @@ static int batch_graph(int dev, BatchHdr *hdr, int grid, bool edge, unsigned sme
     if (err == cudaSuccess) {
         cudaKernelNodeParams kp = {};
         void *args[] = {(void *)&hdr};
-        kp.func = edge ? (void *)k_sweep_batch<true> : (void *)k_sweep_batch<false>;
+        kp.func = batch_fn(edge, kind);
         kp.gridDim = dim3(grid);
         kp.blockDim = dim3(kBNW * 32);
         kp.sharedMemBytes = smem;
@@ -424,7 +478,7 @@ static int batch_graph(int dev, BatchHdr *hdr, int grid, bool edge, unsigned sme
         cudaGraphExecDestroy(g_bcache.front().exec);
         g_bcache.erase(g_bcache.begin());
     }
-    BatchGraph e{dev, hdr, grid, edge ? 1 : 0, exec, h};
+    BatchGraph e{dev, hdr, grid, edge ? 1 : 0, kind, exec, h};
     g_bcache.push_back(e);
     *out = e;
     return DH_OK;
@@ -451,7 +505,7 @@ size_t dh_batch_workspace_bytes(int n, const dh_image *imgs, const dh_params *p)
 int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *workspace, size_t workspace_bytes,
                     void *stream, dh_report *reports) {
     if (n < 1 || n > kMaxBatch || !imgs || !p) return DH_EINVAL;
-    if (dh_workspace_bytes(1, 1, p) == 0 || p->storage != DH_STORE_F32) return DH_EINVAL;
+    if (dh_workspace_bytes(1, 1, p) == 0) return DH_EINVAL;
     for (int i = 0; i < n; ++i)
         if (!image_ok(imgs[i])) return DH_EINVAL;
     const BatchLayout B = batch_layout(n, imgs, p);
@@ -464,8 +518,49 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
         cudaEventCreate(&e1);
         cudaEventRecord(e0, s);
     }
-    // front end per image (Sec. II-D, II-A)
+    // iterate storage: float32, 16-bit (bf16 / fp16), or 16-bit until the
+    // residual stalls and float32 from the same n (as in the single-image path)
+    const int storage = p->storage;
+    const bool bf = storage == DH_STORE_BF16 || storage == DH_STORE_BF16_F32;
+    const bool switched = storage == DH_STORE_BF16_F32 || storage == DH_STORE_F16_F32;
+    const int kind1 = storage == DH_STORE_F32 ? 0 : (bf ? 1 : 2);
+    auto grid_for_n = [](size_t m) { return (int)((m + 255) / 256 < 4096 ? (m + 255) / 256 : 4096); };
     std::vector<BImg> recs(n);
+    // the two iterate buffers of image i for storage `kind`, and their tensor maps
+    auto set_iterates = [&](BImg &r, int i, int kind) -> int {
+        const dh_image &m = imgs[i];
+        char *iw = ws + B.off[i];
+        const WsLayout L = img_layout(m.H, m.W, p);
+        const size_t n3 = (size_t)3 * m.H * m.W;
+        SolveDesc &d = r.d;
+        if (kind == 0) {
+            d.u[0] = m.u;
+            d.u[1] = iw + L.ub;
+        } else {
+            d.u[0] = iw + L.ub;
+            d.u[1] = iw + L.ub + align_up(n3 * 2);
+        }
+        auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
+        // TMA rows start on 16-byte boundaries: W % 4 == 0 for float32, W % 8 == 0 for 16 bits
+        r.tma = (m.W % (kind ? 8 : 4) == 0) && a16(d.u[0]) && a16(d.u[1]) && a16(d.phi) && a16(d.lam);
+        if (!r.tma) return DH_OK;
+        int e = DH_OK;
+        if (kind == 0) {
+            e = encode_f32_map(&r.tm[0], d.u[0], 3, m.W, m.H, 3, kTW + 8, kBTH + 4);
+            if (!e) e = encode_f32_map(&r.tm[1], d.u[1], 3, m.W, m.H, 3, kTW + 8, kBTH + 4);
+        } else {
+            const cuuint64_t dims[3] = {(cuuint64_t)m.W, (cuuint64_t)m.H, 3};
+            const cuuint64_t strides[2] = {(cuuint64_t)m.W * 2, (cuuint64_t)m.W * m.H * 2};
+            const cuuint32_t box[3] = {kTW + 16, kBTH + 4, 1};
+            const CUtensorMapDataType dt = kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+            e = encode_tiled(&r.tm[0], dt, 3, d.u[0], dims, strides, box);
+            if (!e) e = encode_tiled(&r.tm[1], dt, 3, d.u[1], dims, strides, box);
+        }
+        if (!e) e = encode_f32_map(&r.tm[2], d.phi, 3, m.W, m.H, 3, kTW, kBTH);
+        if (!e) e = encode_f32_map(&r.tm[3], d.lam, 2, m.W, m.H, 1, kTW, kBTH);
+        return e;
+    };
+    // front end per image (Sec. II-D, II-A)
     int total_items = 0;
     for (int i = 0; i < n; ++i) {
         const dh_image &m = imgs[i];
@@ -484,8 +579,6 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
         BImg &r = recs[i];
         std::memset(&r, 0, sizeof(r));
         SolveDesc &d = r.d;
-        d.u[0] = m.u;
-        d.u[1] = iw + L.ub;
         d.phi = phi;
         d.lam = lam;
         d.part = (float2 *)(iw + L.part);
@@ -508,53 +601,88 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
         d.nblk = r.ntx * ((m.H + kBTH - 1) / kBTH);
         r.items = 3 * d.nblk;
         total_items += r.items;
-        auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
-        r.tma = (m.W % 4 == 0) && a16(d.u[0]) && a16(d.u[1]) && a16(phi) && a16(lam);
-        if (r.tma) {
-            int e = encode_f32_map(&r.tm[0], d.u[0], 3, m.W, m.H, 3, kTW + 8, kBTH + 4);
-            if (!e) e = encode_f32_map(&r.tm[1], d.u[1], 3, m.W, m.H, 3, kTW + 8, kBTH + 4);
-            if (!e) e = encode_f32_map(&r.tm[2], phi, 3, m.W, m.H, 3, kTW, kBTH);
-            if (!e) e = encode_f32_map(&r.tm[3], lam, 2, m.W, m.H, 1, kTW, kBTH);
-            if (e) return e;
+        d.phase_stop = switched ? 1 : 0;
+        const int rc2 = set_iterates(r, i, kind1);
+        if (rc2) return rc2;
+        if (kind1) {  // u0 (float32 in m.u) into the first 16-bit buffer
+            const size_t n3 = (size_t)3 * m.H * m.W;
+            if (kind1 == 1)
+                k_b_to16<__nv_bfloat16><<<grid_for_n(n3), 256, 0, s>>>(m.u, (__nv_bfloat16 *)d.u[0], n3);
+            else
+                k_b_to16<__half><<<grid_for_n(n3), 256, 0, s>>>(m.u, (__half *)d.u[0], n3);
         }
     }
     BImg *dimgs = (BImg *)(ws + B.imgs);
-    for (int i = 0; i < n; i += kPutChunk) {
-        PutChunk ch;
-        const int cnt = n - i < kPutChunk ? n - i : kPutChunk;
-        for (int k = 0; k < cnt; ++k) ch.rec[k] = recs[i + k];
-        k_batch_put<<<1, 128, 0, s>>>(dimgs + i, ch, cnt);
-    }
+    auto put = [&](int reset) {
+        for (int i = 0; i < n; i += kPutChunk) {
+            PutChunk ch;
+            const int cnt = n - i < kPutChunk ? n - i : kPutChunk;
+            for (int k = 0; k < cnt; ++k) ch.rec[k] = recs[i + k];
+            k_batch_put<<<1, 128, 0, s>>>(dimgs + i, ch, cnt, reset);
+        }
+    };
+    put(1);
     DH_CUDA_TRY(cudaGetLastError());
-    // the batched loop
+    // the batched loop over the images still iterating, for storage `kind`
     const bool edge = !(p->variant & DH_VAR_NO_EDGE);
-    const unsigned smem = TmaPlan<kBTH, true, float>::STAGE + 1024;
-    void *fn = edge ? (void *)k_sweep_batch<true> : (void *)k_sweep_batch<false>;
-    int dev = 0, per_sm = 0, sms = 0;
-    DH_CUDA_TRY(cudaGetDevice(&dev));
-    DH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBNW * 32, smem));
-    DH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // a multiple of 3 (one CTA per channel of each run of tiles)
-    int grid = total_items < per_sm * sms ? total_items : per_sm * sms;
-    grid = grid < 3 ? 3 : grid - grid % 3;
     BatchHdr *hdr = (BatchHdr *)(ws + B.hdr);
-    int launches = 0;
-    if (p->use_graph) {
-        BatchGraph bg{};
-        int rc = batch_graph(dev, hdr, grid, edge, smem, &bg);
+    int dev = 0, sms = 0, launches = 0;
+    DH_CUDA_TRY(cudaGetDevice(&dev));
+    DH_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    auto run_loop = [&](int kind) -> int {
+        const unsigned smem = batch_smem(kind);
+        void *fn = batch_fn(edge, kind);
+        int per_sm = 0;
+        DH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBNW * 32, smem));
+        // a multiple of 3 (one CTA per channel of each run of tiles)
+        int grid = total_items < per_sm * sms ? total_items : per_sm * sms;
+        grid = grid < 3 ? 3 : grid - grid % 3;
+        if (p->use_graph) {
+            BatchGraph bg{};
+            const int rc = batch_graph(dev, hdr, grid, edge, kind, smem, &bg);
+            if (rc) return rc;
+            k_batch_init<<<1, 32, 0, s>>>(hdr, dimgs, n, 1, bg.cond);
+            DH_CUDA_TRY(cudaGraphLaunch(bg.exec, s));
+        } else {
+            k_batch_init<<<1, 32, 0, s>>>(hdr, dimgs, n, 0, 0);
+            void *args[] = {(void *)&hdr};
+            for (int it = 0; it <= p->max_iter; ++it)
+                DH_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kBNW * 32), args, smem, s));
+            launches += p->max_iter + 1;
+        }
+        return DH_OK;
+    };
+    int rc = run_loop(kind1);
+    if (rc) return rc;
+    if (kind1 && switched) {
+        // each image's 16-bit iterate becomes float32 in its u; the stalled ones
+        // continue in float32 from the same n, the others are final
+        for (int i = 0; i < n; ++i) {
+            if (kind1 == 1)
+                k_b_from16<__nv_bfloat16><<<grid_for_n((size_t)3 * imgs[i].H * imgs[i].W), 256, 0, s>>>(&dimgs[i].d, imgs[i].u, nullptr);
+            else
+                k_b_from16<__half><<<grid_for_n((size_t)3 * imgs[i].H * imgs[i].W), 256, 0, s>>>(&dimgs[i].d, imgs[i].u, nullptr);
+            k_b_handoff<<<1, 1, 0, s>>>(recs[i].d.st);
+            recs[i].d.phase_stop = 0;
+            rc = set_iterates(recs[i], i, 0);
+            if (rc) return rc;
+        }
+        put(0);
+        rc = run_loop(0);
         if (rc) return rc;
-        k_batch_init<<<1, 32, 0, s>>>(hdr, dimgs, n, 1, bg.cond);
-        DH_CUDA_TRY(cudaGraphLaunch(bg.exec, s));
-    } else {
-        k_batch_init<<<1, 32, 0, s>>>(hdr, dimgs, n, 0, 0);
-        void *args[] = {(void *)&hdr};
-        for (int it = 0; it <= p->max_iter; ++it) DH_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kBNW * 32), args, smem, s));
-        launches += p->max_iter + 1;
     }
     for (int i = 0; i < n; ++i) {
-        int rc = launch_output_f32(&dimgs[i].d, imgs[i].J, imgs[i].u, (size_t)3 * imgs[i].H * imgs[i].W, s);
-        if (rc) return rc;
+        const size_t n3 = (size_t)3 * imgs[i].H * imgs[i].W;
+        if (kind1 && !switched) {
+            if (kind1 == 1)
+                k_b_from16<__nv_bfloat16><<<grid_for_n(n3), 256, 0, s>>>(&dimgs[i].d, imgs[i].u, imgs[i].J);
+            else
+                k_b_from16<__half><<<grid_for_n(n3), 256, 0, s>>>(&dimgs[i].d, imgs[i].u, imgs[i].J);
+        } else {
+            rc = launch_output_f32(&dimgs[i].d, imgs[i].J, imgs[i].u, n3, s);
+            if (rc) return rc;
+        }
     }
     DH_CUDA_TRY(cudaGetLastError());
     if (!reports) return DH_OK;

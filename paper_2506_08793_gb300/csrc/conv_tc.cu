@@ -27,6 +27,9 @@
 
 namespace dh {
 
+int encode_tiled(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *base, const cuuint64_t *dims,
+                 const cuuint64_t *strides, const cuuint32_t *box);
+
 namespace {
 
 typedef __nv_bfloat16 bf16;
@@ -505,28 +508,11 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
 // ldx elements (C of them used), as a 4D tensor (channel, x, y, image) whose
 // box is 8 channels x 130 pixels x 3 rows of one image.
 static int encode_halo_map(CUtensorMap *m, const bf16 *x, int ldx, int C, int N, int H, int W) {
-    static std::mutex mu;
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        if (!encode) {
-            void *fn = nullptr;
-            cudaDriverEntryPointQueryResult q;
-            const cudaError_t e =
-                cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-            if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return DH_ECUDA;
-            encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-        }
-    }
     const cuuint64_t pitch = (cuuint64_t)ldx * sizeof(bf16);
-    cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
-    cuuint64_t strides[3] = {pitch, pitch * (cuuint64_t)W, pitch * (cuuint64_t)W * (cuuint64_t)H};
-    cuuint32_t box[4] = {8, 130, 3, 1};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(x), dims, strides, box, estr,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? DH_OK : DH_EINVAL;
+    const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t strides[3] = {pitch, pitch * (cuuint64_t)W, pitch * (cuuint64_t)W * (cuuint64_t)H};
+    const cuuint32_t box[4] = {8, 130, 3, 1};
+    return encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, x, dims, strides, box);
 }
 
 template <int C, int CO>

@@ -92,7 +92,7 @@ def test_invalid_arguments_rejected_on_host():
     assert N.dh_batch_workspace_bytes(1, [N.dh_image(fake, 0, 8, None, fake, fake, fake, fake)], p) == 0
     assert N.dh_dehaze_batch(1, [img], p, None, 0) == N.DH_EWORKSPACE
     assert N.dh_dehaze_batch(1, [N.dh_image(None, 8, 8, None, fake, fake, fake, fake)], p, fake, 1 << 30) == N.DH_EINVAL
-    assert N.dh_dehaze_batch(1, [img], p.replace(storage=1), fake, 1 << 30) == N.DH_EINVAL
+    assert N.dh_dehaze_batch(1, [img], p.replace(storage=9), fake, 1 << 30) == N.DH_EINVAL
     assert N.dh_sweep_variants() >= 2
     assert N.dh_workspace_bytes(4, 4, p.replace(sweep_variant=N.dh_sweep_variants())) == 0
     assert N.dh_tune(fake, fake, fake, 8, 8, p, 0, fake, 1 << 30) == N.DH_EINVAL

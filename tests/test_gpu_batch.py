@@ -81,3 +81,42 @@ def test_batch_uneven_full_sizes(api):
         assert abs(one["report"].n_iter - o["report"].n_iter) <= 1
         if one["report"].n_iter == o["report"].n_iter:
             assert torch.allclose(one["u"], o["u"], rtol=1e-6, atol=1e-6)
+
+
+@pytest.mark.parametrize("storage", [1, 2])  # DH_STORE_BF16, DH_STORE_F16
+def test_batch_pure_16bit_equals_single_image_path(api, storage):
+    """Pure 16-bit iterate storage in the batched loop: the same per-pixel
+    arithmetic and rounding as the single-image path, so a fixed number of
+    iterations gives the same iterate (TMA and gathered tiles alike)."""
+    shapes = [(64, 128), (61, 83), (96, 40), (48, 136), (30, 8)]
+    imgs = [torch.from_numpy(scenes.hazy_scene(700 + k, H, W)["I"]).cuda() for k, (H, W) in enumerate(shapes)]
+    p = api.params("stable", storage=storage, tol=0.0, max_iter=150)
+    outs = api.dehaze_batch(imgs, p)
+    for k, (I, o) in enumerate(zip(imgs, outs)):
+        one = api.dehaze(I, p)
+        assert o["report"].n_iter == one["report"].n_iter == 150, k
+        assert o["report"].status == one["report"].status == 2, k
+        d = np.abs(host(o["u"]) - host(one["u"]))
+        assert np.max(d / np.maximum(1.0, np.abs(host(one["u"])))) <= 1e-6, k
+        assert torch.equal(torch.clamp(o["u"], 0, 1), o["J"])
+
+
+@pytest.mark.parametrize("storage", [3, 4])  # DH_STORE_BF16_F32, DH_STORE_F16_F32
+def test_batch_switched_storage_reaches_tolerance(api, orc, storage):
+    """16-bit storage until an image's residual stalls, then float32 from the
+    same n, per image: every image reaches 1e-4 and is as close to the FP64
+    fixed point as the float32 batch."""
+    shapes = [(64, 128), (61, 83), (48, 136)]
+    Is = [scenes.hazy_scene(800 + k, H, W)["I"] for k, (H, W) in enumerate(shapes)]
+    imgs = [torch.from_numpy(I).cuda() for I in Is]
+    o32 = api.dehaze_batch(imgs, api.params("stable"))
+    o16 = api.dehaze_batch(imgs, api.params("stable", storage=storage))
+    op = orc.params(**orc.STABLE)
+    for k, I in enumerate(Is):
+        r16 = o16[k]["report"]
+        assert r16.status == 0 and max(r16.rho) <= 1e-4, k
+        ustar = orc.dehaze(I, op, 20000, 1e-9)["u"]
+        e32 = np.max(np.abs(host(o32[k]["u"]) - ustar))
+        e16 = np.max(np.abs(host(o16[k]["u"]) - ustar))
+        assert e16 <= 2 * e32 + 2e-4, (k, e16, e32)
+        assert torch.equal(torch.clamp(o16[k]["u"], 0, 1), o16[k]["J"])
