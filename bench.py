@@ -134,6 +134,33 @@ def cpu_sample(I, H, W, iters, n_gpu_iters):
     return (t1 - t0) + per_iter * n_gpu_iters, oracle.num_threads(), (t1 - t0), per_iter
 
 
+def cpu_single_thread(seed, H, W, iters, n_gpu_iters):
+    """The same oracle sample on one thread (OMP_NUM_THREADS=1, in a child
+    process so that the parent's OpenMP pool is untouched); returns (seconds
+    extrapolated to n_gpu_iters iterations, front end s, s per iteration)."""
+    code = (
+        "import json, time, oracle\n"
+        "from paper_2506_08793_gb300 import scenes\n"
+        f"I = scenes.hazy_scene({seed}, {H}, {W})['I']\n"
+        "op = oracle.params(**oracle.STABLE)\n"
+        "t0 = time.perf_counter()\n"
+        "dc = oracle.dark_channel(I, op.patch, None)\n"
+        "A, _, _ = oracle.atmospheric_light(I, dc, op.topk_permille)\n"
+        "td = oracle.dark_channel(I, op.patch, A)\n"
+        "_, lam, Phi = oracle.transmission(I, A, td, op)\n"
+        "t1 = time.perf_counter()\n"
+        f"oracle.solve(Phi, Phi, lam, op, {iters} - 1, 0.0)\n"
+        "t2 = time.perf_counter()\n"
+        f"print(json.dumps([t1 - t0, (t2 - t1) / {iters}, oracle.num_threads()]))\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600,
+                       cwd=os.path.dirname(os.path.abspath(__file__)))
+    if r.returncode != 0:
+        return None
+    fe, per_iter, threads = json.loads(r.stdout.strip().splitlines()[-1])
+    return fe + per_iter * n_gpu_iters, fe, per_iter, threads
+
+
 def batch_extra(api, p, n=64, reps=3):
     """Uneven-size batch (sizes drawn from the four photo sizes) in one batched
     solve: images/s and MPix*iter/s (device time, inputs resident)."""
@@ -456,6 +483,12 @@ def main():
             "sample": (f"1920x1080 scene: FP64 oracle front end ({fe:.1f} s) + {args.cpu_iters} fixed-point "
                        f"iterations ({per_iter:.2f} s each), extrapolated to the GPU's {per_img[0]['n_iter']} "
                        "iterations")}
+        st = cpu_single_thread(im["seed"], im["H"], im["W"], 3, per_img[0]["n_iter"])
+        if st is not None:
+            line["cpu_baseline"]["single_thread"] = {
+                "value": im["H"] * im["W"] * per_img[0]["n_iter"] / 1e6 / st[0], "unit": UNIT, "cores": st[3],
+                "sample": (f"the same scene on one thread: front end ({st[1]:.1f} s) + 3 fixed-point iterations "
+                           f"({st[2]:.2f} s each), extrapolated the same way")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
