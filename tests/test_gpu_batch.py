@@ -120,3 +120,19 @@ def test_batch_switched_storage_reaches_tolerance(api, orc, storage):
         e16 = np.max(np.abs(host(o16[k]["u"]) - ustar))
         assert e16 <= 2 * e32 + 2e-4, (k, e16, e32)
         assert torch.equal(torch.clamp(o16[k]["u"], 0, 1), o16[k]["J"])
+
+
+def test_batch_switched_storage_graph_equals_host_loop(api):
+    """The two-phase (16-bit, then float32) batched schedule queued as host
+    launches gives the graph loop's result bit for bit, Dirichlet boundary
+    included."""
+    shapes = [(64, 128), (37, 72)]
+    imgs = [torch.from_numpy(scenes.hazy_scene(900 + k, H, W)["I"]).cuda() for k, (H, W) in enumerate(shapes)]
+    for boundary in (0, 1):
+        p = api.params("stable", storage=3, boundary=boundary, max_iter=2500)
+        a = api.dehaze_batch(imgs, p)
+        b = api.dehaze_batch(imgs, p.replace(use_graph=0))
+        for k in range(len(shapes)):
+            assert a[k]["report"].n_iter == b[k]["report"].n_iter, (boundary, k)
+            assert a[k]["report"].status == b[k]["report"].status == 0, (boundary, k)
+            assert torch.equal(a[k]["u"], b[k]["u"]), (boundary, k)
