@@ -29,6 +29,8 @@ namespace dh {
 
 int encode_tiled(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *base, const cuuint64_t *dims,
                  const cuuint64_t *strides, const cuuint32_t *box);
+int encode_tiled_sw(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *base, const cuuint64_t *dims,
+                    const cuuint64_t *strides, const cuuint32_t *box, CUtensorMapSwizzle swizzle);
 
 namespace {
 
@@ -232,6 +234,188 @@ k_conv3x3_tc(const bf16 *__restrict__ x, int ldx, int C, int Nimg, int H, int W,
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::TMEM_COLS)
                      : "memory");
+}
+
+// TMA-fed variant for images whose rows fill 128-pixel segments well: a tile
+// is a 128-pixel segment of one image row (N tile as above).  For each k-block
+// (tap, 32 channels) one TMA box brings the A tile - the segment's pixels
+// shifted by the tap, zero filled outside the image and past C - and one the
+// weights (NT output channels x 32 input channels of that tap), both with the
+// 64-byte swizzle, i.e. the K-major layout the descriptors above read.  One
+// thread issues the loads into a ring of stages, another the MMAs; a "full"
+// mbarrier per stage (TMA transaction bytes) and an "empty" one (tcgen05.commit)
+// order them, so no block barrier sits in the k loop.
+template <int NT>
+__global__ void __launch_bounds__(128, 2)
+k_conv3x3_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw, int C, int H, int W,
+              int segs, const float *__restrict__ bias, int Cout, int relu, bf16 *__restrict__ y, int ldy, int *err) {
+    using P = TcPlan<NT>;
+    constexpr int S = P::STAGES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[S], empty[S], done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail, s_issued, s_consumed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int t = blockIdx.x;
+    const int seg = t % segs, row = t / segs, n = row / H, yy = row - n * H, x0 = seg * 128;
+    const int n0 = blockIdx.y * NT;
+    const int KC = (C + kTcBK - 1) / kTcBK, KB = 9 * KC;
+    const uint32_t sbase = smem_addr(smem);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(P::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        fence_mbar_init();
+        s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (tid == 0) {  // loads
+        int kb = 0;
+        for (; kb < KB; ++kb) {
+            const int s = kb % S;
+            if (kb >= S && !mbar_wait_bounded(&empty[s], (uint32_t)((kb / S) - 1) & 1u, kTcWaitCycles)) {
+                s_fail = 1;
+                break;
+            }
+            const int tap = kb / KC, c0 = (kb - tap * KC) * kTcBK;
+            unsigned char *As = smem + s * P::STAGE;
+            mbar_arrive_expect_tx(&full[s], P::STAGE);
+            tma_load_4d(smem_addr(As), &tmx, &full[s], c0, x0 + tap % 3 - 1, yy + tap / 3 - 1, n);
+            tma_load_2d(As + P::A_BYTES, &tmw, &full[s], tap * C + c0, n0);
+        }
+        s_issued = kb;
+    } else if (tid == 32) {  // MMAs
+        constexpr uint32_t IDESC = f16_idesc(kTcBM, NT);
+        int kb = 0;
+        for (; kb < KB; ++kb) {
+            const int s = kb % S;
+            if (!mbar_wait_bounded(&full[s], (uint32_t)(kb / S) & 1u, kTcWaitCycles)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const int c0 = (kb % KC) * kTcBK;
+            const int ksteps = C - c0 >= 32 ? 2 : 1;  // C % 16 == 0
+            const uint32_t As = sbase + s * P::STAGE, Bs = As + P::A_BYTES;
+            for (int k = 0; k < ksteps; ++k)
+                tc_mma(tmem, sw64_desc(As + 32 * k), sw64_desc(Bs + 32 * k), IDESC, (kb > 0 || k > 0) ? 1u : 0u);
+            tc_commit(&empty[s]);  // the stage is free once these MMAs are done
+        }
+        s_consumed = kb;
+        tc_commit(&done_bar);  // every MMA issued above
+    }
+    bool failed = !mbar_wait_bounded(&done_bar, 0, kTcWaitCycles);
+    __syncthreads();
+    failed = __syncthreads_or(failed || s_fail);
+    if (failed) {
+        // loads issued but never consumed land before the shared memory goes away
+        if (tid == 0) {
+            for (int kb = s_consumed; kb < s_issued; ++kb)
+                mbar_wait_bounded(&full[kb % S], (uint32_t)(kb / S) & 1u, kTcWaitCycles);
+            if (err) atomicExch(err, DH_ETIMEOUT);
+        }
+        __syncthreads();
+    }
+    tc_fence_after();
+
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 = pixels x0 + 32w + lane of the segment
+    const int px = x0 + warp * 32 + lane;
+    const size_t orow = (size_t)row * W + px;
+#pragma unroll 1
+    for (int c = 0; c < NT; c += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+        const int col = n0 + c;
+        if (px < W && col < Cout && !failed) {
+            uint32_t packed[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float v0 = __uint_as_float(r[2 * j]) + (bias ? __ldg(bias + col + 2 * j) : 0.f);
+                float v1 = __uint_as_float(r[2 * j + 1]) + (bias ? __ldg(bias + col + 2 * j + 1) : 0.f);
+                if (relu) {
+                    v0 = fmaxf(v0, 0.f);
+                    v1 = fmaxf(v1, 0.f);
+                }
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v0, v1);
+                packed[j] = *reinterpret_cast<const uint32_t *>(&h);
+            }
+            uint4 *dst = reinterpret_cast<uint4 *>(y + orow * ldy + col);
+            dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::TMEM_COLS)
+                     : "memory");
+}
+
+// Input and weight maps of the TMA-fed kernel: x as (channel, x, y, image)
+// with 32-channel x 128-pixel boxes, w ([cout][tap][cin]) as (tap*C + cin,
+// cout) with 32 x NT boxes; both with the 64-byte swizzle.
+static int encode_tc_maps(CUtensorMap *mx, CUtensorMap *mw, const bf16 *x, int ldx, int C, int N, int H, int W,
+                          const bf16 *w, int Cout, int NT) {
+    const cuuint64_t pitch = (cuuint64_t)ldx * sizeof(bf16);
+    const cuuint64_t xd[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    const cuuint64_t xs[3] = {pitch, pitch * (cuuint64_t)W, pitch * (cuuint64_t)W * (cuuint64_t)H};
+    const cuuint32_t xb[4] = {32, 128, 1, 1};
+    int rc = encode_tiled_sw(mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, x, xd, xs, xb, CU_TENSOR_MAP_SWIZZLE_64B);
+    if (rc) return rc;
+    const cuuint64_t wd[2] = {(cuuint64_t)9 * C, (cuuint64_t)Cout};
+    const cuuint64_t ws[1] = {(cuuint64_t)9 * C * sizeof(bf16)};
+    const cuuint32_t wb[2] = {32, (cuuint32_t)NT};
+    return encode_tiled_sw(mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, w, wd, ws, wb, CU_TENSOR_MAP_SWIZZLE_64B);
+}
+
+// Whether the TMA-fed kernel serves this layer: rows that fill at least 3/4
+// of their 128-pixel segments, 16-byte aligned activations and weights.
+static bool tma_conv_ok(const void *x, const void *w, int W) {
+    const int segs = (W + 127) / 128;
+    return 4 * W >= 3 * 128 * segs && ((uintptr_t)x % 16) == 0 && ((uintptr_t)w % 16) == 0;
+}
+
+template <int NT>
+int launch_tc_tma(const bf16 *x, int ldx, int C, int N, int H, int W, const bf16 *w, const float *b, int Cout,
+                  bool relu, bf16 *y, int ldy, int *err, cudaStream_t s) {
+    using P = TcPlan<NT>;
+    static std::mutex mu;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return DH_ECUDA;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!attr_set[dev]) {
+            DH_CUDA_TRY(cudaFuncSetAttribute(k_conv3x3_tma<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)P::SMEM));
+            attr_set[dev] = true;
+        }
+    }
+    CUtensorMap mx, mw;
+    const int rc = encode_tc_maps(&mx, &mw, x, ldx, C, N, H, W, w, Cout, NT);
+    if (rc) return rc;
+    const int segs = (W + 127) / 128;
+    dim3 grid((unsigned)(N * H * segs), (Cout + NT - 1) / NT);
+    k_conv3x3_tma<NT><<<grid, 128, P::SMEM, s>>>(mx, mw, C, H, W, segs, b, Cout, relu ? 1 : 0, y, ldy, err);
+    DH_CUDA_TRY(cudaGetLastError());
+    return DH_OK;
 }
 
 template <int NT>
@@ -585,6 +769,14 @@ int conv3x3_tc(const void *x, int ldx, int C, int N, int H, int W, const void *w
     if (C % 16 || Cout % 16 || ldx % 8 || ldy % 8) return DH_EINVAL;
     const bf16 *X = (const bf16 *)x, *Wt = (const bf16 *)w;
     bf16 *Y = (bf16 *)y;
+    if (tma_conv_ok(x, w, W)) {
+        if (Cout <= 32) return launch_tc_tma<32>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+        if (Cout <= 64) return launch_tc_tma<64>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+        if (Cout <= 96) return launch_tc_tma<96>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+        if (Cout <= 128) return launch_tc_tma<128>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+        if (Cout <= 192) return launch_tc_tma<192>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+        return launch_tc_tma<256>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
+    }
     if (Cout <= 32) return launch_tc<32>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
     if (Cout <= 64) return launch_tc<64>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);
     if (Cout <= 96) return launch_tc<96>(X, ldx, C, N, H, W, Wt, b, Cout, relu, Y, ldy, err, s);

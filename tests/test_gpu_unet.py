@@ -40,7 +40,15 @@ def host(t):
                                                    (1, 3, 200, 96, 96, 32, 1), (2, 4, 130, 32, 32, 32, 0),
                                                    (1, 5, 129, 64, 64, 64, 1), (1, 6, 140, 64, 80, 32, 0),
                                                    (1, 4, 257, 32, 32, 96, 1), (1, 2, 128, 16, 16, 32, 1),
-                                                   (2, 3, 64, 32, 40, 64, 0)])
+                                                   (2, 3, 64, 32, 40, 64, 0),
+                                                   # the TMA-fed general kernel (rows of >= 96 pixels):
+                                                   # ragged segments, C < 32 and C % 32 != 0, pitch != C,
+                                                   # every N tile
+                                                   (1, 3, 128, 64, 64, 128, 1), (2, 2, 100, 48, 48, 64, 0),
+                                                   (1, 2, 230, 192, 192, 64, 1), (1, 2, 256, 384, 384, 128, 1),
+                                                   (2, 3, 128, 16, 16, 64, 1), (1, 2, 120, 32, 40, 256, 0),
+                                                   (1, 3, 97, 96, 96, 192, 1), (1, 2, 128, 128, 128, 96, 0),
+                                                   (1, 2, 112, 64, 64, 48, 1)])
 def test_conv_forward(N, n, H, W, C, ldx, Cout, relu):
     from oracle import unet as U
 
