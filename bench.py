@@ -379,7 +379,7 @@ def main():
         Ih = torch.from_numpy(I).pin_memory()
         Id = Ih.cuda()
         if not args.no_tune:  # pick the sweep variant for this shape (untimed)
-            tuned[f"{W}x{H}"] = api.tune(Id, p, iters=100)["best"]
+            tuned[f"{W}x{H}"] = api.tune(Id, p, iters=300)["best"]
         imgs.append(dict(H=H, W=W, seed=seed, Inp=I, Ih=Ih, Id=Id, dz=api.Dehazer(H, W, p),
                          Jh=torch.empty((3, H, W), dtype=torch.float32).pin_memory()))
     stream = torch.cuda.current_stream()
