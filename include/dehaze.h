@@ -299,8 +299,10 @@ int dh_dehaze_warm(const float *params, int base, const float *I, int H, int W, 
  * 32 KiB array in device memory that every GPU which loads the library keeps
  * until the process exits; it does not grow with the image, so the size limit
  * is the library's own (1 <= H, W <= 32768, H*W <= 2^28; DH_EINVAL beyond).
- * The first call on a device looks up the array's device address and should
- * come before any stream capture on that device.  All calls share the array:
+ * Every call looks up the array's device address for the current device
+ * (cheap, no allocation); the first call on a device also loads the library's
+ * device code there, so it should come before any stream capture on that
+ * device.  All calls share the array:
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race and must be serialised by the caller. */
 int dh_atmospheric_light_noalloc(const float *I, const float *dc, int H, int W, int topk_permille,

@@ -98,14 +98,18 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
                  : "memory");
 }
 
+// The load and its wait are one asm statement: the destination registers are
+// written asynchronously, and with the wait in a statement of its own the
+// compiler was free to schedule their first uses between the two.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15}, [%16];"
+        "%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        : "r"(taddr)
+        : "memory");
 }
 
 template <int NT>
@@ -589,8 +593,12 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
 
     bool failed = false;
     if constexpr (P::CP_ASYNC) {
+        // two commit groups whatever nt is (an empty one when there is no
+        // tile 1), so that waiting for all but the newest one always means
+        // that tile 0 has landed
         if (nt > 0) stage(0);
         if (nt > 1) stage(1);
+        else cp_async_commit();
         if (nt > 0) {
             cp_async_wait<1>();
             fence_proxy_async_smem();  // generic-proxy copies, read by the MMAs

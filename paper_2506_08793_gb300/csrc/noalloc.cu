@@ -26,10 +26,6 @@ constexpr size_t kNaHist = align_up(sizeof(SelectState));
 constexpr size_t kNaBlk = kNaHist + align_up(256 * sizeof(unsigned));
 static_assert(kNaBlk + (size_t)kSelBlocks * 16 <= kNoAllocScratchBytes, "scratch too small");
 
-constexpr int kMaxDevices = 64;
-static std::mutex g_na_mu;
-static char *g_na_ptr[kMaxDevices];  // device address of g_select_scratch, per device
-
 }  // namespace dh
 
 using namespace dh;
@@ -39,22 +35,13 @@ extern "C" int dh_atmospheric_light_noalloc(const float *I, const float *dc, int
                                             void *stream) {
     if (!I || !dc || !A_out || !shape_ok(H, W) || topk_permille < 1 || topk_permille > 1000)
         return DH_EINVAL;
-    int dev = 0;
-    DH_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return DH_EINVAL;
-    char *scratch;
-    {
-        // First call on a device: look up the array's device address (the
-        // host-side name is only a stand-in and must not reach a kernel).
-        std::lock_guard<std::mutex> lk(g_na_mu);
-        if (!g_na_ptr[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_select_scratch);
-            if (e != cudaSuccess || !p) return cuda_fail(e);
-            g_na_ptr[dev] = (char *)p;
-        }
-        scratch = g_na_ptr[dev];
-    }
+    // The array's device address, looked up on every call for the current
+    // device and context (the host-side name is only a stand-in and must not
+    // reach a kernel; an address kept from an earlier context would go stale
+    // after a device reset).  The lookup allocates nothing.
+    char *scratch = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress((void **)&scratch, g_select_scratch);
+    if (e != cudaSuccess || !scratch) return cuda_fail(e);
     WsLayout L = {};
     L.sel = 0;
     L.hist = kNaHist;
