@@ -183,50 +183,126 @@ def batch_extra(api, p, n=64, reps=3):
             "all_converged": all(x.status == 0 for x in r)}
 
 
-def storage16_extra(api, p, n=64):
-    """The uneven 64-image batch with 16-bit iterate storage: pure bf16 / fp16
-    (which stall above 1e-4; run to the float32 batch's largest n) and the
-    switched forms (16-bit until an image's residual stalls, then float32 to
-    1e-4).  Per image: max-abs of u and PSNR of J against the float32 batch on
-    the same images (the float32 path itself agrees with the FP64 oracle to
-    about 1e-5 in the parity tests)."""
+GOLDEN_BATCH = os.path.join(ROOT, "tests", "golden", "fp_batch64_subset.npz")
+
+
+def golden_batch():
+    """The FP64 oracle's fixed points of every fourth image of the 64-image
+    batch (sampled pixels; written by tests/golden/make_fixed_points.py), or
+    None when the file is absent."""
+    try:
+        return dict(np.load(GOLDEN_BATCH))
+    except Exception:
+        return None
+
+
+def oracle_errors(outs, gold):
+    """Per-image error of a batch's u and J against the FP64 oracle at the
+    golden sample pixels: max-abs of u and J and PSNR of J against the
+    oracle's tol-1e-5 iterate (about ten times closer to the exact fixed point
+    than any tol-1e-4 one), and max-abs of u against the oracle's own tol-1e-4
+    stop."""
+    if gold is None:
+        return None
+    import torch
+
+    rows = []
+    for i, k in enumerate(gold["k"]):
+        ys = torch.from_numpy(gold["ys"][i]).cuda()
+        xs = torch.from_numpy(gold["xs"][i]).cuda()
+        u = outs[int(k)]["u"][:, ys, xs].double().cpu().numpy()
+        J = outs[int(k)]["J"][:, ys, xs].double().cpu().numpy()
+        u2, u1 = gold["u2"][i], gold["u1"][i]
+        mse = float(np.mean((J - np.clip(u2, 0.0, 1.0)) ** 2))
+        rows.append({"k": int(k), "size": f"{int(gold['W'][i])}x{int(gold['H'][i])}",
+                     "max_abs_u": float(np.max(np.abs(u - u2))),
+                     "max_abs_J": float(np.max(np.abs(J - np.clip(u2, 0.0, 1.0)))),
+                     "psnr_J_db": None if mse == 0 else 10 * math.log10(1.0 / mse),
+                     "max_abs_u_vs_oracle_tol1e-4": float(np.max(np.abs(u - u1)))})
+    psnr = [r["psnr_J_db"] for r in rows if r["psnr_J_db"] is not None]
+    return {"images": len(rows),
+            "reference": "FP64 oracle from u0 = Phi to tol 1e-5 (images 0, 4, ..., 60; 4096 sampled pixels each)",
+            "max_abs_u": {"max": max(r["max_abs_u"] for r in rows),
+                          "median": statistics.median(r["max_abs_u"] for r in rows)},
+            "max_abs_J": max(r["max_abs_J"] for r in rows),
+            "psnr_J_db_min": min(psnr) if psnr else None,
+            "max_abs_u_vs_oracle_tol1e-4": max(r["max_abs_u_vs_oracle_tol1e-4"] for r in rows),
+            "per_image": rows}
+
+
+def _batch_images(n):
     import torch
 
     from paper_2506_08793_gb300 import scenes
 
     sizes = scenes.batch_sizes(3000, n)
     imgs = [torch.from_numpy(scenes.hazy_scene(3000 + k, H, W)["I"]).cuda() for k, (H, W) in enumerate(sizes)]
+    return sizes, imgs
+
+
+def _time_batch(b, imgs, reps=3):
+    b(imgs)  # warm-up (graph build)
+    runs = [b(imgs) for _ in range(reps)]
+    ms = statistics.median(r[0].ms for r in runs)
+    return ms, runs[-1]
+
+
+def storage16_extra(api, p, n=64):
+    """The uneven 64-image batch with 16-bit iterate storage: pure bf16 / fp16
+    (which stall above 1e-4; run to the float32 batch's largest n) and the
+    switched forms (16-bit until an image's residual stalls, then float32 to
+    1e-4).  Per image: error of u and J against the FP64 oracle (golden
+    fixed points of every fourth image), beside the float32 batch's."""
+    import torch
+
+    sizes, imgs = _batch_images(n)
+    gold = golden_batch()
     ref = api.BatchDehazer(sizes, p)
-    ref(imgs)
-    r32 = ref(imgs)
-    u32 = [o["u"].clone() for o in ref.out]
-    j32 = [o["J"].clone() for o in ref.out]
+    ms32, r32 = _time_batch(ref, imgs)
     nmax = max(x.n_iter for x in r32)
-    out = {"images": n, "reference": "float32 batch of the same images",
-           "float32": {"ms": r32[0].ms, "images_per_s": n / (r32[0].ms / 1e3)}}
+    out = {"images": n, "float32": {"ms": ms32, "images_per_s": n / (ms32 / 1e3),
+                                    "oracle_error": oracle_errors(ref.out, gold)}}
     del ref
     for name, st in (("bf16", 1), ("fp16", 2), ("bf16_f32", 3), ("fp16_f32", 4)):
         pure = st in (1, 2)
         q = p.replace(storage=st, max_iter=nmax) if pure else p.replace(storage=st)
         b = api.BatchDehazer(sizes, q)
-        b(imgs)  # warm-up (graph build)
-        rep = b(imgs)
-        maxabs, psnr = [], []
-        for o, u, J in zip(b.out, u32, j32):
-            maxabs.append(float((o["u"] - u).abs().max()))
-            mse = float(((o["J"] - J) ** 2).mean())
-            psnr.append(None if mse == 0 else 10 * math.log10(1.0 / mse))
-        finite = [x for x in psnr if x is not None]
-        out[name] = {"ms": rep[0].ms, "images_per_s": n / (rep[0].ms / 1e3),
+        ms, rep = _time_batch(b, imgs)
+        out[name] = {"ms": ms, "images_per_s": n / (ms / 1e3),
                      "max_iter": nmax if pure else q.max_iter,
                      "converged_to_tol": sum(x.status == 0 for x in rep),
                      "iterations": {"min": min(x.n_iter for x in rep), "max": max(x.n_iter for x in rep)},
-                     "max_abs_u": {"max": max(maxabs), "median": statistics.median(maxabs)},
-                     "psnr_J_db": {"min": min(finite) if finite else None,
-                                   "median": statistics.median(finite) if finite else None,
-                                   "identical_images": len(psnr) - len(finite)}}
+                     "oracle_error": oracle_errors(b.out, gold)}
         del b
         torch.cuda.empty_cache()
+    return out
+
+
+def warm_batch_extra(api, p, net, n=64):
+    """The learned warm start on the uneven 64-image batch: per image the
+    network's u0 (forward pass inside the timed call), then the batched loop
+    to 1e-4, in float32 and in the switched 16-bit -> float32 storages,
+    against the plain cold float32 batch; images/s, iterations and the error
+    against the FP64 oracle (golden fixed points of every fourth image)."""
+    import torch
+
+    sizes, imgs = _batch_images(n)
+    gold = golden_batch()
+    out = {"images": n, "network": {"base": net.base, "trained_on": getattr(net, "trained_on", None)}}
+    forms = (("cold_f32", 0, False), ("warm_f32", 0, True), ("warm_bf16_f32", 3, True), ("warm_fp16_f32", 4, True))
+    for name, st, warm in forms:
+        b = api.BatchDehazer(sizes, p.replace(storage=st), net=net if warm else None)
+        ms, rep = _time_batch(b, imgs)
+        its = [x.n_iter for x in rep]
+        out[name] = {"ms": ms, "images_per_s": n / (ms / 1e3), "converged_to_tol": sum(x.status == 0 for x in rep),
+                     "iterations": {"mean": sum(its) / n, "min": min(its), "max": max(its)},
+                     "oracle_error": oracle_errors(b.out, gold)}
+        del b
+        torch.cuda.empty_cache()
+    c = out["cold_f32"]
+    for name, _, warm in forms[1:]:
+        out[name]["speedup_vs_cold_f32"] = c["ms"] / out[name]["ms"]
+        out[name]["iterations_saved"] = 1.0 - out[name]["iterations"]["mean"] / c["iterations"]["mean"]
     return out
 
 
@@ -264,28 +340,37 @@ def refine_extra(api, im, reps=5):
             "plain_front_end_ms": statistics.median(r.ms - r.ms_loop for r in plain)}
 
 
-def warm_extra(api, p, im, train_n=256, steps=600):
-    """Learned warm start: a network trained here on train_n solver-generated
-    256x256 scenes (the library's own kernels), then the 1080p scene from the
-    cold start (u0 = Phi) and from the network's u0, to the same residual."""
+def train_warm_net(p, train_n=256, size=512, steps=600):
+    """The warm-start network trained here on train_n solver-generated
+    size x size scenes (seeds 5e6 + i) by the library's own kernels."""
     import torch
 
     from paper_2506_08793_gb300 import warmstart as WS
 
     t0 = time.perf_counter()
-    data = WS.make_dataset(train_n, 256, 256, seed0=5_000_000, p=p)
+    data = WS.make_dataset(train_n, size, size, seed0=5_000_000, p=p)
     net = WS.WarmStartNet(32, seed=1)
     log = net.train(data, steps=steps, batch=8, lr=1e-3, lr_end=5e-5, log_every=steps)
+    del data
     torch.cuda.synchronize()
-    t_train = time.perf_counter() - t0
+    torch.cuda.empty_cache()
+    net.trained_on = {"scenes": train_n, "size": f"{size}x{size}", "adam_steps": steps, "batch": 8,
+                      "train_s": time.perf_counter() - t0, "final_loss": log[-1][1]}
+    return net
+
+
+def warm_extra(api, p, im, net):
+    """Learned warm start on the 1080p scene: cold start (u0 = Phi) against the
+    network's u0, to the same residual."""
+    from paper_2506_08793_gb300 import warmstart as WS
+
     wd = WS.WarmDehazer(net, im["H"], im["W"], p)
     wd(im["Id"])
     reps = [wd(im["Id"]) for _ in range(5)]
     cold = [im["dz"](im["Id"]) for _ in range(5)]
     ms_w = statistics.median(r.ms for r in reps)
     ms_c = statistics.median(r.ms for r in cold)
-    return {"image": f"{im['W']}x{im['H']}", "train_scenes": train_n, "train_steps": steps,
-            "train_s": t_train, "final_loss": log[-1][1],
+    return {"image": f"{im['W']}x{im['H']}", "network": net.trained_on,
             "cold": {"n_iter": cold[0].n_iter, "ms": ms_c, "images_per_s": 1e3 / ms_c},
             "warm": {"n_iter": reps[0].n_iter, "ms": ms_w, "images_per_s": 1e3 / ms_w,
                      "rho": max(reps[0].rho)},
@@ -471,7 +556,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras:
         line["batch"] = batch_extra(api, p)
         line["batch_16bit_storage"] = storage16_extra(api, p)
-        line["warm_start"] = warm_extra(api, p, imgs[0])
+        net = train_warm_net(p)
+        line["warm_start"] = warm_extra(api, p, imgs[0], net)
+        line["warm_batch_16bit"] = warm_batch_extra(api, p, net)
         line["semi_implicit"] = semi_extra(api, imgs[0])
         line["refinements"] = refine_extra(api, imgs[0])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

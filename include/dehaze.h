@@ -291,6 +291,21 @@ int dh_dehaze_warm(const float *params, int base, const float *I, int H, int W, 
                    float *u, float *t, float *A, void *workspace, size_t workspace_bytes, void *net_workspace,
                    size_t net_workspace_bytes, void *stream, dh_report *report);
 
+/* The batched solve of dh_dehaze_batch with the network's warm start for
+ * every image: per image the front end, then y = net(I, t, A, Phi) and
+ * u0 = y / lambda (as in dh_dehaze_warm), then the fixed-point loops of all
+ * images in one graph while loop, each to its own residual; p->storage may be
+ * any DH_STORE_* (the 16-bit phase of a switched form starts from the
+ * network's u0 rounded to 16 bits).  imgs[i].u0 must be NULL; every image's
+ * H and W are multiples of 8.  workspace: dh_batch_workspace_bytes(n, imgs, p);
+ * net_workspace: dh_batch_net_workspace_bytes(base, n, imgs) (one forward at a
+ * time, reused image after image), both 256-byte aligned.  The paper only
+ * points at hybrids of the PDE with learned models (Sec. I and V). */
+size_t dh_batch_net_workspace_bytes(int base, int n, const dh_image *imgs);
+int dh_dehaze_batch_warm(const float *params, int base, int n, const dh_image *imgs, const dh_params *p,
+                         void *workspace, size_t workspace_bytes, void *net_workspace, size_t net_workspace_bytes,
+                         void *stream, dh_report *reports);
+
 /* dh_atmospheric_light without a workspace and without any allocation.
  * The paper has no counterpart: this exists for callers that cannot call
  * cudaMalloc, such as a plug-in whose host application owns all device memory,

@@ -35,7 +35,7 @@ EXPORTS = ("dh_params_default", "dh_strerror", "dh_version", "dh_workspace_bytes
            "dh_conv3x3_forward",
            "dh_conv3x3_backward_weights", "dh_dehaze_warm", "dh_atmospheric_light_noalloc",
            "dh_semi_implicit_workspace_bytes", "dh_semi_implicit", "dh_transmission_ws",
-           "dh_selftest_bounded_wait")
+           "dh_selftest_bounded_wait", "dh_batch_net_workspace_bytes", "dh_dehaze_batch_warm")
 
 
 class DhParams(ctypes.Structure):
@@ -158,6 +158,8 @@ def lib(build_if_missing: bool = True):
             "dh_conv3x3_forward": ([P, I, I, I, I, I, P, P, I, I, P, I, P], I),
             "dh_conv3x3_backward_weights": ([P, I, I, P, I, I, I, I, I, P, P, P, S, P], I),
             "dh_dehaze_warm": ([P, I, P, I, I, PP, P, P, P, P, P, S, P, S, P, PR], I),
+            "dh_batch_net_workspace_bytes": ([I, I, ctypes.POINTER(DhImage)], S),
+            "dh_dehaze_batch_warm": ([P, I, I, ctypes.POINTER(DhImage), PP, P, S, P, S, P, PR], I),
             "dh_semi_implicit_workspace_bytes": ([I, I], S),
             "dh_transmission_ws": ([P, P, I, I, PP, P, P, P, P, P, S, P], I),
             "dh_selftest_bounded_wait": ([ctypes.c_longlong, P], I),
@@ -345,6 +347,20 @@ def dh_dehaze_warm(params, base, I, H, W, p: DhParams, J, u, t, A, workspace, wo
     return lib().dh_dehaze_warm(_p(params), base, _p(I), H, W, ctypes.byref(p), _p(J), _p(u), _p(t), _p(A),
                                 _p(workspace), workspace_bytes, _p(net_workspace), net_workspace_bytes,
                                 _stream(stream), _ref(report))
+
+
+def dh_batch_net_workspace_bytes(base, n, imgs) -> int:
+    arr = (DhImage * n)(*imgs)
+    return lib().dh_batch_net_workspace_bytes(base, n, arr)
+
+
+def dh_dehaze_batch_warm(params, base, n, imgs, p: DhParams, workspace, workspace_bytes, net_workspace,
+                         net_workspace_bytes, stream=None, reports=None) -> int:
+    """dh_dehaze_batch with the network's u0 for every image; reports: ctypes
+    array of n DhReport or None."""
+    arr = (DhImage * n)(*imgs)
+    return lib().dh_dehaze_batch_warm(_p(params), base, n, arr, ctypes.byref(p), _p(workspace), workspace_bytes,
+                                      _p(net_workspace), net_workspace_bytes, _stream(stream), reports)
 
 
 def dh_selftest_bounded_wait(limit_cycles: int, stream=None) -> int:

@@ -166,9 +166,13 @@ class BatchDehazer:
     persistent sweep launch per iteration over every image still iterating.
     Outputs and workspace stay resident between calls."""
 
-    def __init__(self, shapes, p: DhParams | None = None, device="cuda"):
+    def __init__(self, shapes, p: DhParams | None = None, device="cuda", net=None):
+        """net: a warm-start network (an object with .params, a float32 CUDA
+        tensor, and .base, e.g. warmstart.WarmStartNet); with it every image
+        starts from the network's u0 (dh_dehaze_batch_warm)."""
         import ctypes
 
+        self.net = net
         self.shapes = [tuple(map(int, s)) for s in shapes]
         self.p = p or params()
         self.device = torch.device(device)
@@ -185,6 +189,12 @@ class BatchDehazer:
         if nb == 0:
             raise ValueError("invalid batch")
         self.ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        self.nws = None
+        if net is not None:
+            nn = N.dh_batch_net_workspace_bytes(net.base, len(probe), probe)
+            if nn == 0:
+                raise ValueError("the network takes image sides that are multiples of 8")
+            self.nws = torch.empty(nn, dtype=torch.uint8, device=self.device)
         self._ctypes = ctypes
 
     def __call__(self, images, u0s=None, report: bool = True, stream=None):
@@ -196,9 +206,16 @@ class BatchDehazer:
                 raise ValueError(f"image {k} has the wrong shape")
             u0 = None if u0s is None else u0s[k]
             imgs.append(N.dh_image(I, H, W, u0, o["J"], o["u"], o["t"], o["A"]))
-        rc = N.dh_dehaze_batch(len(imgs), imgs, self.p, self.ws, self.ws.numel(), _stream(stream),
-                               self._reports if report else None)
-        _check(rc, "dh_dehaze_batch")
+        reps = self._reports if report else None
+        if self.net is not None:
+            if u0s is not None:
+                raise ValueError("a warm-started batch takes its u0 from the network")
+            rc = N.dh_dehaze_batch_warm(self.net.params, self.net.base, len(imgs), imgs, self.p, self.ws,
+                                        self.ws.numel(), self.nws, self.nws.numel(), _stream(stream), reps)
+            _check(rc, "dh_dehaze_batch_warm")
+        else:
+            rc = N.dh_dehaze_batch(len(imgs), imgs, self.p, self.ws, self.ws.numel(), _stream(stream), reps)
+            _check(rc, "dh_dehaze_batch")
         return [DhReport.from_buffer_copy(r) for r in self._reports] if report else None
 
 

@@ -23,6 +23,19 @@ int encode_f32_map(CUtensorMap *m, const void *base, int rank, int W, int H, int
 int encode_tiled(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *base, const cuuint64_t *dims,
                  const cuuint64_t *strides, const cuuint32_t *box);
 int sweep_tile_h(int depth);
+size_t warm_net_bytes(int base, int H, int W);
+int warm_u0(const float *params, int base, const float *I, const float *t, const float *A, const float *phi,
+            const float *lam, int H, int W, void *nws, size_t nws_bytes, float *u0, cudaStream_t s);
+
+// The warm-start network of dh_dehaze_batch_warm and the workspace of one forward.
+struct WarmNet {
+    const float *params;
+    int base;
+    void *ws;
+    size_t ws_bytes;
+};
+constexpr int kWarmLaunches = 37;  // weight packing (14), input packing, 14 convolutions, 3 pools, 3 upsamplings,
+                                   // head, u0 = y / lambda
 
 constexpr int kMaxBatch = 256;
 constexpr int kBR = 6, kBNW = 4, kBTH = kBR * kBNW;  // 128 x 24 tiles, 4 warps, 5 CTAs per SM
@@ -502,8 +515,10 @@ size_t dh_batch_workspace_bytes(int n, const dh_image *imgs, const dh_params *p)
     return batch_layout(n, imgs, p).total;
 }
 
-int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *workspace, size_t workspace_bytes,
-                    void *stream, dh_report *reports) {
+// The batched solve; with `warm`, each image's u0 is the network's prediction
+// (dh_dehaze_batch_warm), else the caller's u0 or Phi.
+static int batch_run(int n, const dh_image *imgs, const dh_params *p, void *workspace, size_t workspace_bytes,
+                     void *stream, dh_report *reports, const WarmNet *warm) {
     if (n < 1 || n > kMaxBatch || !imgs || !p) return DH_EINVAL;
     if (dh_workspace_bytes(1, 1, p) == 0) return DH_EINVAL;
     for (int i = 0; i < n; ++i)
@@ -569,11 +584,17 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
         float *dc = (float *)(iw + L.dc), *lam = (float *)(iw + L.lam), *phi = (float *)(iw + L.phi);
         int rc = launch_dark_channel(m.I, m.H, m.W, p->patch, nullptr, dc, s);
         if (!rc) rc = launch_select_A(m.I, dc, m.H, m.W, p->topk_permille, m.A, nullptr, iw, L, s);
-        if (!rc) rc = launch_transmission(m.I, m.H, m.W, p, m.A, nullptr, m.t, lam, phi, m.u0 ? nullptr : m.u,
-                                          (float2 *)(iw + L.phin_part), iw + L.refine, s);
+        if (!rc) rc = launch_transmission(m.I, m.H, m.W, p, m.A, nullptr, m.t, lam, phi,
+                                          (m.u0 || warm) ? nullptr : m.u, (float2 *)(iw + L.phin_part),
+                                          iw + L.refine, s);
         if (rc) return rc;
-        if (m.u0)
+        if (warm) {  // u0 = net(I, t, A, Phi) / lambda, into u (the network's workspace is reused per image)
+            rc = warm_u0(warm->params, warm->base, m.I, m.t, m.A, phi, lam, m.H, m.W, warm->ws, warm->ws_bytes, m.u,
+                         s);
+            if (rc) return rc;
+        } else if (m.u0) {
             DH_CUDA_TRY(cudaMemcpyAsync(m.u, m.u0, (size_t)3 * m.H * m.W * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        }
         rc = launch_phin_final((const float2 *)(iw + L.phin_part), m.H, m.W, (SolveState *)(iw + L.state), s);
         if (rc) return rc;
         BImg &r = recs[i];
@@ -709,13 +730,41 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
         DH_CUDA_TRY(cudaMemcpy(r.A, imgs[i].A, 3 * sizeof(float), cudaMemcpyDeviceToHost));
         r.a_index = sel.best;
         r.ms = ms;  // the whole batch
-        r.launches = 18 + 1;  // front end + output of this image
+        r.launches = 18 + 1 + (warm ? kWarmLaunches : 0);  // front end (+ network) + output of this image
         if (st.n_final > max_n) max_n = st.n_final;
         if (r.status < 0 && worst >= 0) worst = r.status;
         else if (worst == DH_OK && r.status > 0) worst = r.status;
     }
     reports[0].launches += (p->use_graph ? max_n + 1 : launches) + 1 + (n + kPutChunk - 1) / kPutChunk;
     return worst;
+}
+
+int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *workspace, size_t workspace_bytes,
+                    void *stream, dh_report *reports) {
+    return batch_run(n, imgs, p, workspace, workspace_bytes, stream, reports, nullptr);
+}
+
+size_t dh_batch_net_workspace_bytes(int base, int n, const dh_image *imgs) {
+    if (n < 1 || n > kMaxBatch || !imgs) return 0;
+    size_t most = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t b = warm_net_bytes(base, imgs[i].H, imgs[i].W);
+        if (b == 0) return 0;
+        if (b > most) most = b;
+    }
+    return most;
+}
+
+int dh_dehaze_batch_warm(const float *params, int base, int n, const dh_image *imgs, const dh_params *p,
+                         void *workspace, size_t workspace_bytes, void *net_workspace, size_t net_workspace_bytes,
+                         void *stream, dh_report *reports) {
+    if (!params || n < 1 || n > kMaxBatch || !imgs) return DH_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (imgs[i].u0 || warm_net_bytes(base, imgs[i].H, imgs[i].W) == 0) return DH_EINVAL;
+    const size_t need = dh_batch_net_workspace_bytes(base, n, imgs);
+    if (!net_workspace || ((uintptr_t)net_workspace % kAlign) || net_workspace_bytes < need) return DH_EWORKSPACE;
+    const WarmNet w{params, base, net_workspace, net_workspace_bytes};
+    return batch_run(n, imgs, p, workspace, workspace_bytes, stream, reports, &w);
 }
 
 }  // extern "C"

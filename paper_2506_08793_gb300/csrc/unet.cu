@@ -858,6 +858,28 @@ static int net_backward(const float *params, int b, const float *target, int N, 
 
 #undef BF
 
+// Workspace one network forward over a single HxW image needs (0: shape
+// the network does not take).
+size_t warm_net_bytes(int base, int H, int W) {
+    if (!unet_shape_ok(base, 1, H, W)) return 0;
+    return net_layout(base, 1, H, W, false).total;
+}
+
+// u0 = net(I, t, A, Phi) / lambda for one image, queued on s: the warm start of
+// the batched solve.  nws: warm_net_bytes(base, H, W) bytes, 256-byte aligned.
+int warm_u0(const float *params, int base, const float *I, const float *t, const float *A, const float *phi,
+            const float *lam, int H, int W, void *nws, size_t nws_bytes, float *u0, cudaStream_t s) {
+    if (!unet_shape_ok(base, 1, H, W)) return DH_EINVAL;
+    const NetLayout NL = net_layout(base, 1, H, W, false);
+    if (!nws || ((uintptr_t)nws % kAlign) || nws_bytes < NL.total) return DH_EWORKSPACE;
+    char *ws = (char *)nws;
+    RUN(net_forward(params, base, I, t, A, phi, 1, H, W, ws, NL, false, s));
+    k_warm_start<<<gs((size_t)3 * H * W), 256, 0, s>>>(reinterpret_cast<const float *>(ws + NL.y), lam,
+                                                      (size_t)H * W, u0);
+    DH_CUDA_TRY(cudaGetLastError());
+    return DH_OK;
+}
+
 }  // namespace dh
 
 using namespace dh;
