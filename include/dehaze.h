@@ -196,8 +196,8 @@ int dh_dehaze(const float *I, int H, int W, const dh_params *p, const float *u0,
 typedef struct dh_tune_result {
     int best;               /* fastest usable variant */
     int count;              /* entries below */
-    int variant[32];        /* variant ids timed */
-    float us_per_iter[32];  /* device time per iteration (graph loop, faster of two rounds) */
+    int variant[64];        /* variant ids timed */
+    float us_per_iter[64];  /* device time per iteration (graph loop, faster of two rounds) */
 } dh_tune_result;
 
 /* Number of sweep variants (valid ids are 1 .. count-1). */

@@ -91,8 +91,8 @@ class DhTuneResult(ctypes.Structure):
     _fields_ = [
         ("best", ctypes.c_int),
         ("count", ctypes.c_int),
-        ("variant", ctypes.c_int * 32),
-        ("us_per_iter", ctypes.c_float * 32),
+        ("variant", ctypes.c_int * 64),
+        ("us_per_iter", ctypes.c_float * 64),
     ]
 
 

@@ -332,10 +332,10 @@ int dh_tune(const float *Phi, const float *lam, float *u_scratch, int H, int W, 
     DH_CUDA_TRY(cudaEventCreate(&b));
     const size_t bytes = (size_t)3 * H * W * sizeof(float);
     rc = launch_phin(Phi, H, W, (float2 *)(ws + L.phin_part), (SolveState *)(ws + L.state), s);
-    int vs[32], nv = 0;
-    for (int v = 1; v < sweep_variant_count() && nv < 32; ++v)
+    int vs[64], nv = 0;
+    for (int v = 1; v < sweep_variant_count() && nv < 64; ++v)
         if (sweep_variant_usable(v, W, aligned)) vs[nv++] = v;
-    float us_min[32];
+    float us_min[64];
     // two rounds over all variants, the faster time of each kept: a clock or
     // thermal drift during one round does not decide the winner
     for (int round = 0; round < 2 && !rc; ++round) {

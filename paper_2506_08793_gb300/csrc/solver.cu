@@ -158,6 +158,9 @@ static const SweepCfg kVariants[] = {
     {4, 4, 2, 1, true}, {4, 4, 2, 1, true, 0, 1},
     // 31-32: two iterations per tile load (120 x 16 / 120 x 24 output tiles), multi-iteration launches
     {4, 4, 1, 4, true, 0, 1}, {6, 4, 1, 4, true, 0, 1},
+    // 33-35: one producer warp + NW compute warps, two stages, Phi/lambda staged, no block
+    // barrier inside an iteration (tma 5), multi-iteration launches
+    {4, 8, 2, 5, true, 2, 1}, {6, 4, 2, 5, true, 2, 1}, {8, 4, 2, 5, true, 2, 1},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 constexpr int kTb2Variant = 31;  // the two-iteration sweep with 120 x 16 tiles
@@ -229,12 +232,12 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
             c.minb = mb;
             c.tma = tma_ok ? t : 0;
             if (c.tma == 3 && p->boundary == DH_BOUNDARY_ZERO) c.tma = 1;
-            c.multi = c.tma == 1 ? (mu != 0) : (c.tma == 4 ? 1 : 0);
+            c.multi = c.tma == 1 ? (mu != 0) : ((c.tma == 4 || c.tma == 5 || c.tma == 6) ? 1 : 0);
         }
     }
     if (!c.tma && !sweep_fn<float>(c.R, c.NW, c.edge)) { c.R = 8; c.NW = 4; }
     if (!c.tma) c.stages = 1;
-    if (c.tma != 1 && c.tma != 4) c.multi = 0;
+    if (c.tma != 1 && c.tma != 4 && c.tma != 5 && c.tma != 6) c.multi = 0;
     if (c.tma == 0) c.minb = 0;
     return c;
 }
@@ -442,6 +445,27 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
         if (gmax <= 0) return DH_ECUDA;
         const int items = 3 * v.nblk;
         ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(cfg.NW * 32), smem, args_tma};
+        ls.coop = 1;
+        v.depth = kItersPerLaunch;
+    } else if ((cfg.tma == 5 || cfg.tma == 6) && esize == 4) {
+        // one producer warp and NW compute warps per CTA
+        const int TH = cfg.th();
+        if (TH < kMinTileH) return DH_EINVAL;
+        v.nblk = ntx * ((H + TH - 1) / TH);
+        if (v.nblk > L.nblk_sweep) return DH_EINVAL;
+        int rc = encode_f32_map(&maps[0], v.u[0], 3, W, H, 3, kTW + 8, TH + 4);
+        if (!rc) rc = encode_f32_map(&maps[1], v.u[1], 3, W, H, 3, kTW + 8, TH + 4);
+        if (!rc) rc = encode_f32_map(&maps[2], v.phi, 3, W, H, 3, kTW, TH);
+        if (!rc) rc = encode_f32_map(&maps[3], v.lam, 2, W, H, 1, kTW, TH);
+        if (rc) return rc;
+        SweepTmaFn fn = sweep_ws_fn(0, cfg.R, cfg.NW, cfg.stages, cfg.tma == 5, cfg.edge, cfg.minb, 1);
+        if (!fn) return DH_EINVAL;
+        const unsigned smem = tma_smem_bytes(TH, cfg.stages, cfg.tma == 5 ? 1 : 2, esize);
+        const int block = (cfg.NW + 1) * 32;
+        const int gmax = persistent_grid((void *)fn, block, smem);
+        if (gmax <= 0) return DH_ECUDA;
+        const int items = 3 * v.nblk;
+        ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(block), smem, args_tma};
         ls.coop = 1;
         v.depth = kItersPerLaunch;
     } else if (cfg.tma == 1 || cfg.tma == 2) {

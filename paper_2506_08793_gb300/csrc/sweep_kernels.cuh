@@ -856,6 +856,285 @@ k_sweep_stream(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant_
 }
 
 
+// ---------------------------------------------------------------- warp-specialised TMA sweep
+// Reflects the border halo cells (see reflect_border) in shared-memory rows
+// [r0, r0 + nr) of a staged tile, by the 32 lanes of one warp: exactly the
+// rows that warp's walk reads.  A cell another warp also reflects receives
+// the same value from both; the sources lie inside the image and are never
+// written.
+template <class T>
+__device__ __forceinline__ void reflect_rows_warp(T *s, int stride, int ncols, int r0, int nr, int cx0, int ry0,
+                                                  int H, int W, int lane) {
+    for (int r = r0; r < r0 + nr; ++r) {
+        const int gy = ry0 + r;
+        if (gy < -2 || gy > H + 1) continue;  // never read by a stored output
+        if (gy < 0 || gy >= H) {
+            const int sy = reflect_idx(gy, H) - ry0;
+            for (int q = lane; q < ncols; q += 32) {
+                const int gx = cx0 + q;
+                if (gx < -2 || gx > W + 1) continue;
+                s[r * stride + q] = s[sy * stride + reflect_idx(gx, W) - cx0];
+            }
+        } else if (lane < 4) {
+            const int g = lane < 2 ? lane - 2 : W + lane - 2;  // -2, -1, W, W + 1
+            const int q = g - cx0;
+            if (q >= 0 && q < ncols) s[r * stride + q] = s[r * stride + reflect_idx(g, W) - cx0];
+        }
+    }
+}
+
+// TMA sweep with one producer warp and NW compute warps per CTA (W % 4 == 0,
+// 16-byte aligned planes).  Persistent CTAs walk the (tile, channel) items as
+// k_sweep_tma does.  Lane 0 of the producer warp loads each item's u^n tile
+// (with halo) and, when PL_SMEM, its Phi and lambda tiles into a ring of
+// STAGES stages by TMA (full[s] completes on the transaction bytes), pulls
+// the item STAGES further on into L2, and refills a stage once all NW compute
+// warps have released it (empty[s], NW arrivals); at that point it also merges
+// the NW per-warp residual partials the warps left in the stage's slots, in
+// warp order (the same order as block_pair_sum), into the item's partial.
+// Compute warp w walks rows [w*R, w*R + R) of every item: it reflects the
+// border cells its own walk reads, walks, reduces its residual over the warp,
+// stores it in the slot and releases the stage.  No block barrier is taken
+// inside an iteration, so a warp that finishes early goes on to the next
+// staged item.  MULTI: as k_sweep_tma, up to d->depth iterations per
+// cooperative launch with a grid barrier between them.
+template <int R, int NW, int STAGES, bool PL_SMEM, class T, bool EDGE, int MINB, bool MULTI>
+__global__ void __launch_bounds__((NW + 1) * 32, MINB)
+k_sweep_ws(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
+           const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
+           const SolveDesc *__restrict__ d) {
+    constexpr int TH = R * NW;
+    constexpr int HALO = Store<T>::HALO;
+    using P = TmaPlan<TH, PL_SMEM, T>;
+    constexpr int SW = P::SW, SH = P::SH;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+    __shared__ float2 slot[STAGES][NW];
+    __shared__ int s_last, s_timeout;
+    __shared__ volatile int s_fail;
+
+    SolveState *st = d->st;
+    clear_condition(d);
+    if (__ldcg(&st->done)) return;
+    unsigned gen = 0;
+    if (MULTI) gen = ld_acquire_gpu(&st->gen);  // before this CTA can arrive anywhere
+    const int H = d->H, W = d->W;
+    const size_t N = (size_t)H * W;
+    const int ntx = (W + kTW - 1) / kTW, nty = (H + TH - 1) / TH;
+    const int ntiles = ntx * nty, nitems = 3 * ntiles;
+    const int G = gridDim.x;
+    const int m = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;  // items of this CTA
+
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < STAGES; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], NW);
+        }
+        fence_mbar_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
+    const bool dirichlet = d->dirichlet != 0;
+    const float *__restrict__ phi_all = d->phi;
+    const float *__restrict__ glam = d->lam;
+    float2 *__restrict__ part = d->part;
+    const int nblk = d->nblk;
+    const int iters = MULTI ? d->depth : 1;
+    int k = 0;        // ring position of this CTA's first item in the current iteration
+    int issued = 0;   // producer: ring positions whose loads were issued
+    for (int it = 0; it < iters; ++it) {
+        const int cur = __ldcg(&st->cur);
+        const bool rev = (__ldcg(&st->n) & 1) != 0;
+        const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
+        T *__restrict__ ubase = static_cast<T *>(d->u[cur ^ 1]);
+        auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
+        auto tile_xy = [&](int item, int &c, int &x0, int &y0) {
+            const int tile = item / 3;
+            c = item - 3 * tile;
+            x0 = (tile % ntx) * kTW;
+            y0 = (tile / ntx) * TH;
+            return tile;
+        };
+        if (w == NW) {
+            if (lane == 0) {
+                // item j's partial from the NW slots of its stage, in warp order
+                auto store_partial = [&](int j, int stage) {
+                    int c, x0, y0;
+                    const int tile = tile_xy(item_at(j), c, x0, y0);
+                    float a = slot[stage][0].x, b = slot[stage][0].y;
+#pragma unroll
+                    for (int q = 1; q < NW; ++q) neumaier_merge(a, b, slot[stage][q].x, slot[stage][q].y);
+                    part[(size_t)c * nblk + tile] = make_float2(a, b);
+                };
+                if (MULTI && it > 0) fence_proxy_async_global();
+                for (int j = 0; j < m; ++j) {
+                    const int kk = k + j, stage = kk % STAGES;
+                    if (kk >= STAGES) {  // the stage held ring position kk - STAGES
+                        if (!mbar_wait_bounded(&empty[stage], (uint32_t)((kk / STAGES) - 1) & 1u, kWaitLimitCycles)) {
+                            s_fail = 1;
+                            break;
+                        }
+                        if (j >= STAGES) store_partial(j - STAGES, stage);
+                    }
+                    if (s_fail) break;
+                    int c, x0, y0;
+                    tile_xy(item_at(j), c, x0, y0);
+                    unsigned char *sb = smem + stage * P::STAGE;
+                    fence_proxy_async_smem();
+                    mbar_arrive_expect_tx(&full[stage], P::TX);
+                    tma_load_3d(sb + P::U_OFF, tm_u, &full[stage], x0 - HALO, y0 - 2, c);
+                    if (PL_SMEM) {
+                        tma_load_3d(sb + P::PHI_OFF, &tm_phi, &full[stage], x0, y0, c);
+                        tma_load_2d(sb + P::LAM_OFF, &tm_lam, &full[stage], x0, y0);
+                    }
+                    ++issued;
+                    if (j + STAGES < m) {
+                        int c2, x2, y2;
+                        tile_xy(item_at(j + STAGES), c2, x2, y2);
+                        tma_prefetch_3d(tm_u, x2 - HALO, y2 - 2, c2);
+                        if (PL_SMEM) {
+                            tma_prefetch_3d(&tm_phi, x2, y2, c2);
+                            tma_prefetch_2d(&tm_lam, x2, y2);
+                        }
+                    }
+                }
+                // the partials of the last items (not yet waited for)
+                for (int j = m > STAGES ? m - STAGES : 0; j < m && !s_fail; ++j) {
+                    const int kk = k + j, stage = kk % STAGES;
+                    if (!mbar_wait_bounded(&empty[stage], (uint32_t)(kk / STAGES) & 1u, kWaitLimitCycles)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    store_partial(j, stage);
+                }
+            }
+        } else {
+            for (int j = 0; j < m; ++j) {
+                const int kk = k + j, stage = kk % STAGES;
+                const bool ok = mbar_wait_bounded(&full[stage], (uint32_t)(kk / STAGES) & 1u, kWaitLimitCycles);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    if (lane == 0) s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                int c, x0, y0;
+                tile_xy(item_at(j), c, x0, y0);
+                unsigned char *sb = smem + stage * P::STAGE;
+                T *s = reinterpret_cast<T *>(sb + P::U_OFF);
+                const float *sphi = reinterpret_cast<const float *>(sb + P::PHI_OFF);
+                const float *slam = reinterpret_cast<const float *>(sb + P::LAM_OFF);
+                const bool border = !dirichlet && (x0 == 0 || y0 == 0 || x0 + kTW + 2 > W || y0 + TH + 2 > H);
+                if (border) {
+                    reflect_rows_warp(s, SW, SW, w * R, R + 4, x0 - HALO, y0 - 2, H, W, lane);
+                    __syncwarp();
+                }
+                T *__restrict__ un = ubase + c * N;
+                const int x = x0 + 4 * lane;
+                float rs = 0.f, rc = 0.f;
+                const float *__restrict__ gphi = phi_all + c * N;
+                auto pl = [&](int ty, float *ph, float *la) {
+                    float4 p4, l4;
+                    if (PL_SMEM) {
+                        p4 = *reinterpret_cast<const float4 *>(sphi + ty * kTW + 4 * lane);
+                        l4 = *reinterpret_cast<const float4 *>(slam + ty * kTW + 4 * lane);
+                    } else {
+                        const int y = y0 + ty;
+                        p4 = l4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (y < H && x < W) {
+                            p4 = __ldg(reinterpret_cast<const float4 *>(gphi + (size_t)y * W + x));
+                            l4 = __ldg(reinterpret_cast<const float4 *>(glam + (size_t)y * W + x));
+                        }
+                    }
+                    ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
+                    la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
+                };
+                auto sink = [&](int ty, const float *nu, const float *F) {
+                    const int y = y0 + ty;
+                    if (y >= H || x >= W) return;  // W % 4 == 0: x < W covers all 4 columns
+                    float q = 0.f;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) q = fmaf(F[jj], F[jj], q);
+                    neumaier_add(rs, rc, q);
+                    Store<T>::write4(un + (size_t)y * W + x, nu[0], nu[1], nu[2], nu[3]);
+                };
+                walk_rows<R, SW, T, EDGE>(s, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
+                for (int off = 16; off; off >>= 1) {
+                    const float s2 = __shfl_down_sync(0xffffffffu, rs, off);
+                    const float c2 = __shfl_down_sync(0xffffffffu, rc, off);
+                    neumaier_merge(rs, rc, s2, c2);
+                }
+                if (lane == 0) slot[stage][w] = make_float2(rs, rc);
+                if (border) fence_proxy_async_smem();  // the reflected cells precede the stage's next TMA load
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[stage]);
+            }
+        }
+        k += m;
+        __syncthreads();
+        if (s_fail) {
+            // let every load issued and not waited for land (bounded) before going on
+            if (w == NW && lane == 0) {
+                for (int q = issued > STAGES ? issued - STAGES : 0; q < issued; ++q)
+                    mbar_wait_bounded(&full[q % STAGES], (uint32_t)(q / STAGES) & 1u, kWaitLimitCycles);
+                atomicCAS(&st->err, 0, DH_ETIMEOUT);
+            }
+            __syncthreads();
+            if (MULTI) {
+                if (threadIdx.x == 0) {
+                    st->status = DH_ETIMEOUT;
+                    st->done = 1;
+                }
+                return;
+            }
+        }
+        if (!MULTI) break;
+
+        // grid barrier; the last CTA to arrive finishes the iteration
+        fence_proxy_async_global();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&st->arrive, 1u);
+            s_last = prev == (unsigned)G - 1u;
+            s_timeout = 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            finish_iteration(d, st);
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release_gpu(&st->gen, gen + 1u);
+            }
+        } else if (threadIdx.x == 0) {
+            const long long t0 = clock64();
+            while (ld_acquire_gpu(&st->gen) == gen) {
+                if (clock64() - t0 > kWaitLimitCycles) {
+                    s_timeout = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        ++gen;
+        __syncthreads();
+        if (s_timeout) {  // another CTA never arrived: give up, report
+            if (threadIdx.x == 0) {
+                atomicCAS(&st->err, 0, DH_ETIMEOUT);
+                st->status = DH_ETIMEOUT;
+                st->done = 1;
+            }
+            return;
+        }
+        if (__ldcg(&st->done)) return;
+    }
+    if (!MULTI) arrive_and_finish(d, st, &s_last);
+}
+
+
 typedef void (*SweepFn)(const SolveDesc *);
 typedef void (*SweepTmaFn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const SolveDesc *);
 typedef void (*SweepStreamFn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const SolveDesc *, int);
@@ -871,6 +1150,7 @@ SweepTmaFn sweep_tma_16(int kind, int R, int NW, int stages, int tma, bool edge,
 SweepTmaFn sweep_tb2_fn(int R, int NW, bool edge);
 uint32_t tb2_smem_bytes(int R, int NW);
 SweepStreamFn sweep_stream_fn(int NW, int NSLOT, bool edge);
+SweepTmaFn sweep_ws_fn(int kind, int R, int NW, int stages, int pl, bool edge, int minb, int multi);
 
 // Instance selector shared by the sweep_inst_*.cu files.
 #define DH_STX_T(T, r, nw, st, pls, mb, mu)                                                         \
