@@ -84,6 +84,16 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+def bf16(x):
+    """x rounded to float32, then to bfloat16, both to nearest even, returned
+    as float64: the storage format of the network's weights and activations
+    (BF16 weights and activations with FP32 accumulation)."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    b = f.view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
 def pool(x):
     N, H, W, C = x.shape
     return x.reshape(N, H // 2, 2, W // 2, 2, C).mean(axis=(2, 4))
@@ -102,76 +112,107 @@ def up_backward(g):
     return g.reshape(N, H // 2, 2, W // 2, 2, C).sum(axis=(2, 4))
 
 
-def forward(params, b, I, t, A, Phi):
-    """Returns (y (N,3,H,W) = lambda*u* prediction = Phi + head, cache)."""
+def forward(params, b, I, t, A, Phi, q=None):
+    """Returns (y (N,3,H,W) = lambda*u* prediction = Phi + head, cache).
+
+    q: None for the exact network, or a rounding function (bf16) applied
+    where the network stores a value: the packed input, the convolution
+    weights, every convolution output (after bias and ReLU) and every pooled
+    map; the head accumulates without rounding."""
+    r = q or (lambda v: v)
     ws, bs, hw, hb = unpack(np.asarray(params, np.float64), b)
-    c = {}
+    ws = [r(w) for w in ws]
+    c = {"ws": ws}
     Phi = np.asarray(Phi, np.float64)
-    x0 = pack_input(np.asarray(I, np.float64), np.asarray(t, np.float64), np.asarray(A, np.float64), Phi)
+    x0 = r(pack_input(np.asarray(I, np.float64), np.asarray(t, np.float64), np.asarray(A, np.float64), Phi))
     c["x0"] = x0
-    a1 = relu(conv3x3(x0, ws[0], bs[0])); c["a1"] = a1
-    e1 = relu(conv3x3(a1, ws[1], bs[1])); c["e1"] = e1
-    p1 = pool(e1); c["p1"] = p1
-    a2 = relu(conv3x3(p1, ws[2], bs[2])); c["a2"] = a2
-    e2 = relu(conv3x3(a2, ws[3], bs[3])); c["e2"] = e2
-    p2 = pool(e2); c["p2"] = p2
-    a3 = relu(conv3x3(p2, ws[4], bs[4])); c["a3"] = a3
-    e3 = relu(conv3x3(a3, ws[5], bs[5])); c["e3"] = e3
-    p3 = pool(e3); c["p3"] = p3
-    a4 = relu(conv3x3(p3, ws[6], bs[6])); c["a4"] = a4
-    e4 = relu(conv3x3(a4, ws[7], bs[7])); c["e4"] = e4
+
+    def conv(x, k):
+        return r(relu(conv3x3(x, ws[k], bs[k])))
+
+    a1 = conv(x0, 0); c["a1"] = a1
+    e1 = conv(a1, 1); c["e1"] = e1
+    p1 = r(pool(e1)); c["p1"] = p1
+    a2 = conv(p1, 2); c["a2"] = a2
+    e2 = conv(a2, 3); c["e2"] = e2
+    p2 = r(pool(e2)); c["p2"] = p2
+    a3 = conv(p2, 4); c["a3"] = a3
+    e3 = conv(a3, 5); c["e3"] = e3
+    p3 = r(pool(e3)); c["p3"] = p3
+    a4 = conv(p3, 6); c["a4"] = a4
+    e4 = conv(a4, 7); c["e4"] = e4
     cat3 = np.concatenate([up(e4), e3], axis=-1); c["cat3"] = cat3
-    d3a = relu(conv3x3(cat3, ws[8], bs[8])); c["d3a"] = d3a
-    d3 = relu(conv3x3(d3a, ws[9], bs[9])); c["d3"] = d3
+    d3a = conv(cat3, 8); c["d3a"] = d3a
+    d3 = conv(d3a, 9); c["d3"] = d3
     cat2 = np.concatenate([up(d3), e2], axis=-1); c["cat2"] = cat2
-    d2a = relu(conv3x3(cat2, ws[10], bs[10])); c["d2a"] = d2a
-    d2 = relu(conv3x3(d2a, ws[11], bs[11])); c["d2"] = d2
+    d2a = conv(cat2, 10); c["d2a"] = d2a
+    d2 = conv(d2a, 11); c["d2"] = d2
     cat1 = np.concatenate([up(d2), e1], axis=-1); c["cat1"] = cat1
-    d1a = relu(conv3x3(cat1, ws[12], bs[12])); c["d1a"] = d1a
-    d1 = relu(conv3x3(d1a, ws[13], bs[13])); c["d1"] = d1
+    d1a = conv(cat1, 12); c["d1a"] = d1a
+    d1 = conv(d1a, 13); c["d1"] = d1
     y = d1 @ hw.T + hb  # (N,H,W,3)
+    c["y_scale"] = np.moveaxis(np.abs(d1) @ np.abs(hw).T + np.abs(hb), -1, 1)  # sum of |terms| of the head
     return np.moveaxis(y, -1, 1) + Phi, c
 
 
-def loss_and_grads(params, b, I, t, A, Phi, target):
-    """MSE loss mean((y - target)^2) and its gradient w.r.t. params."""
+def loss_and_grads(params, b, I, t, A, Phi, target, q=None, scales=False):
+    """MSE loss mean((y - target)^2) and its gradient w.r.t. params.
+
+    q: as in forward(); it also rounds every stored gradient map (the head's
+    input gradient, each data gradient, the upsampling adjoints and the
+    skip + pooled gradient sums).  scales: also return, in the parameters'
+    layout, the sum of the absolute values of the terms each gradient element
+    sums (the natural scale of its rounding error)."""
+    r = q or (lambda v: v)
     params = np.asarray(params, np.float64)
-    ws, bs, hw, hb = unpack(params, b)
-    y, c = forward(params, b, I, t, A, Phi)
+    _, _, hw, hb = unpack(params, b)
+    y, c = forward(params, b, I, t, A, Phi, q)
+    ws = c["ws"]
     d = y - np.asarray(target, np.float64)
     loss = float(np.mean(d * d))
     gy = np.moveaxis(2.0 * d / d.size, 1, -1)  # NHWC
     gws = [None] * 14
     gbs = [None] * 14
+    sws = [None] * 14
+    sbs = [None] * 14
     ghw = np.einsum("nhwo,nhwc->oc", gy, c["d1"])
     ghb = gy.sum(axis=(0, 1, 2))
-    g = gy @ hw
+    shw = np.einsum("nhwo,nhwc->oc", np.abs(gy), np.abs(c["d1"]))
+    shb = np.abs(gy).sum(axis=(0, 1, 2))
+    g = r(gy @ hw)
 
     def conv_back(k, x, g_out, y_out):
         g_pre = g_out * (y_out > 0)
         gx, gws[k], gbs[k] = conv3x3_backward(x, ws[k], g_pre)
-        return gx
+        if scales:
+            _, sws[k], sbs[k] = conv3x3_backward(np.abs(x), ws[k], np.abs(g_pre))
+        return r(gx)
 
     B = b
     g = conv_back(13, c["d1a"], g, c["d1"])
     g = conv_back(12, c["cat1"], g, c["d1a"])
-    g_d2, g_e1 = up_backward(g[..., :2 * B]), g[..., 2 * B:]
+    g_d2, g_e1 = r(up_backward(g[..., :2 * B])), g[..., 2 * B:]
     g = conv_back(11, c["d2a"], g_d2, c["d2"])
     g = conv_back(10, c["cat2"], g, c["d2a"])
-    g_d3, g_e2 = up_backward(g[..., :4 * B]), g[..., 4 * B:]
+    g_d3, g_e2 = r(up_backward(g[..., :4 * B])), g[..., 4 * B:]
     g = conv_back(9, c["d3a"], g_d3, c["d3"])
     g = conv_back(8, c["cat3"], g, c["d3a"])
-    g_e4, g_e3 = up_backward(g[..., :8 * B]), g[..., 8 * B:]
+    g_e4, g_e3 = r(up_backward(g[..., :8 * B])), g[..., 8 * B:]
     g = conv_back(7, c["a4"], g_e4, c["e4"])
     g_p3 = conv_back(6, c["p3"], g, c["a4"])
-    g = conv_back(5, c["a3"], g_e3 + pool_backward(g_p3, c["e3"].shape), c["e3"])
+    g = conv_back(5, c["a3"], r(g_e3 + pool_backward(g_p3, c["e3"].shape)), c["e3"])
     g_p2 = conv_back(4, c["p2"], g, c["a3"])
-    g = conv_back(3, c["a2"], g_e2 + pool_backward(g_p2, c["e2"].shape), c["e2"])
+    g = conv_back(3, c["a2"], r(g_e2 + pool_backward(g_p2, c["e2"].shape)), c["e2"])
     g_p1 = conv_back(2, c["p1"], g, c["a2"])
-    g = conv_back(1, c["a1"], g_e1 + pool_backward(g_p1, c["e1"].shape), c["e1"])
+    g = conv_back(1, c["a1"], r(g_e1 + pool_backward(g_p1, c["e1"].shape)), c["e1"])
     conv_back(0, c["x0"], g, c["a1"])
-    parts = []
+    parts, sparts = [], []
     for k in range(14):
         parts += [gws[k].ravel(), gbs[k].ravel()]
+        if scales:
+            sparts += [sws[k].ravel(), sbs[k].ravel()]
     parts += [ghw.ravel(), ghb.ravel()]
+    sparts += [shw.ravel(), shb.ravel()]
+    if scales:
+        return loss, np.concatenate(parts), np.concatenate(sparts)
     return loss, np.concatenate(parts)

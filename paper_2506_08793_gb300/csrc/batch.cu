@@ -167,6 +167,17 @@ __global__ void k_b_handoff(SolveState *st) {
 }
 
 
+// Tile t of an image, numbered down the columns of tiles (t = column * nty +
+// row): consecutive tiles of a CTA's run are vertical neighbours, so the halo
+// rows a tile loads were loaded or written by the tile just before it and are
+// still in L2.
+__device__ __forceinline__ void tile_origin(const BImg *im, int tile, int &x0, int &y0) {
+    const int nty = (im->d.H + kBTH - 1) / kBTH;
+    const int tx = tile / nty;
+    x0 = tx * kTW;
+    y0 = (tile - tx * nty) * kBTH;
+}
+
 // T: storage of the iterates (float, or bf16 / fp16 with float arithmetic)
 template <bool EDGE, class T>
 __global__ void __launch_bounds__(kBNW * 32, 5)
@@ -241,9 +252,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         locate(item, slot, img, tile, c);
         const BImg *im = imgs + img;
         if (!im->tma) return nullptr;
-        const int ntx = im->ntx;
-        x0 = (tile % ntx) * kTW;
-        y0 = (tile / ntx) * kBTH;
+        tile_origin(im, tile, x0, y0);
         if (img != s_acq_img) {
             tensormap_acquire(&im->tm[s_cur[slot]]);
             tensormap_acquire(&im->tm[2]);
@@ -296,8 +305,8 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         SolveState *st = d->st;
         const int H = d->H, W = d->W;
         const size_t N = (size_t)H * W;
-        const int ntx = im->ntx;
-        const int x0 = (tile % ntx) * kTW, y0 = (tile / ntx) * kBTH;
+        int x0, y0;
+        tile_origin(im, tile, x0, y0);
         const int cur = s_cur[slot];
         if (threadIdx.x == 0 && j + 1 < m) prefetch(item_at(j + 1));
         if (im->tma) {

@@ -97,6 +97,17 @@ def _net_inputs(n, H, W, seed):
 
 
 def test_network_forward_backward_against_oracle(N):
+    """The whole network, element by element, against the oracle network
+    with bf16 storage (oracle/unet.py, q = bf16: the same rounding points as
+    the library, FP64 arithmetic in between).  What remains is the order of
+    the float32 sums, which can move a stored value to the neighbouring bf16
+    value (one ulp, at most 2^-7 relative) now and then; so each output or
+    gradient element is held to a few bf16 ulps of the sum of the absolute
+    values of the terms it adds up (its scale).  In the backward pass such
+    moves add up along the chain of rounded gradient maps between the loss
+    and a layer (the head's input gradient, each data gradient, each
+    upsampling adjoint and skip + pooled sum): a layer whose gradient map went
+    through s rounding stages is held to 2 + s ulps of its scale."""
     from oracle import unet as U
 
     base, n, H, W = 16, 2, 16, 24
@@ -112,26 +123,31 @@ def test_network_forward_backward_against_oracle(N):
     y = torch.empty((n, 3, H, W), device="cuda")
     assert N.dh_unet_forward(params, base, d["I"], d["t"], d["A"], d["Phi"], n, H, W, y, ws, ws.numel()) == 0
     P = host(params).astype(np.float64)
-    yo, _ = U.forward(P, base, I, t, A, Phi)
-    assert np.linalg.norm((host(y) - Phi) - (yo - Phi)) <= 3e-2 * np.linalg.norm(yo - Phi)
+    yo, c = U.forward(P, base, I, t, A, Phi, q=U.bf16)
+    ulp = 2.0 ** -7
+    dy = np.abs(host(y) - yo)
+    bad = dy > 2 * ulp * c["y_scale"] + 1e-6
+    assert not bad.any(), (int(bad.sum()), float((dy / (c["y_scale"] + 1e-30)).max()))
     grads = torch.empty(npar, device="cuda")
     loss = torch.empty(1, device="cuda")
     assert N.dh_unet_backward(params, base, d["I"], d["t"], d["A"], d["Phi"], d["tgt"], n, H, W, grads, loss, ws,
                               ws.numel()) == 0
-    lo, go = U.loss_and_grads(P, base, I, t, A, Phi, tgt)
-    assert abs(host(loss)[0] - lo) <= 3e-2 * lo
+    lo, go, so = U.loss_and_grads(P, base, I, t, A, Phi, tgt, q=U.bf16, scales=True)
+    assert abs(host(loss)[0] - lo) <= 1e-3 * lo
     g = host(grads).astype(np.float64)
+    # rounding stages of the gradient map each convolution's weight gradient sums
+    # (counted along oracle/unet.py loss_and_grads, from the loss down)
+    stages = {13: 1, 12: 2, 11: 4, 10: 5, 9: 7, 8: 8, 7: 10, 6: 11, 5: 13, 4: 14, 3: 16, 2: 17, 1: 19, 0: 20}
     o = 0
     for k, (cin, cout) in enumerate(U.convs(base)):
         for size in (cout * 9 * cin, cout):
-            a, b = g[o:o + size], go[o:o + size]
+            a, b, sc = g[o:o + size], go[o:o + size], so[o:o + size]
             o += size
-            if np.linalg.norm(b) < 1e-8:
-                continue
-            cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b))
-            assert cos >= 0.99 and np.linalg.norm(a - b) <= 0.1 * np.linalg.norm(b), (k, size, cos)
-    a, b = g[o:], go[o:]
-    assert np.linalg.norm(a - b) <= 0.05 * np.linalg.norm(b)
+            err = np.abs(a - b)
+            bad = err > (2 + stages[k]) * ulp * sc + 1e-6 * max(sc.max(), 1e-30)
+            assert not bad.any(), (k, size, int(bad.sum()), float((err / (sc + 1e-30)).max()))
+    a, b, sc = g[o:], go[o:], so[o:]  # the head: no rounded gradient map before it
+    assert np.all(np.abs(a - b) <= 2 * ulp * sc + 1e-6 * sc.max())
 
 
 def test_adam_training_reduces_loss(N):

@@ -65,3 +65,35 @@ def test_network_gradient_finite_differences():
         lm, _ = U.loss_and_grads(params - e, b, I, t, A, Phi, tgt)
         num = (lp - lm) / (2 * h)
         assert abs(num - g[i]) <= 1e-4 * max(1.0, abs(num)), (i, num, g[i])
+
+
+def test_bf16_rounding_matches_torch():
+    """The oracle's bfloat16 rounding (float32 first, nearest even) against
+    torch's float32 -> bfloat16 conversion, exact ties and signs included."""
+    import torch
+
+    rng = np.random.default_rng(3)
+    f = (rng.normal(0, 1, 4000) * np.exp2(rng.integers(-30, 30, 4000))).astype(np.float32)
+    ties = f.view(np.uint32) & np.uint32(0xFFFF0000) | np.uint32(0x8000)  # halfway between two bf16 values
+    vals = np.concatenate([f, ties.view(np.float32), np.float32([0.0, -0.0, 1.0, -3.5, 65504.0])])
+    want = torch.from_numpy(vals).to(torch.bfloat16).to(torch.float32).numpy().astype(np.float64)
+    assert np.array_equal(U.bf16(vals.astype(np.float64)), want)
+
+
+def test_gradient_scales_bound_the_gradients():
+    """The per-element scale (sum of |terms|) bounds |gradient| (triangle
+    inequality), in the exact and in the bf16 network."""
+    b, N, H, W = 8, 1, 8, 8
+    rng = np.random.default_rng(1)
+    params = rng.normal(0, 0.3, U.param_count(b))
+    I = rng.uniform(0, 1, (N, 3, H, W))
+    t = rng.uniform(0.1, 1, (N, H, W))
+    A = rng.uniform(0.8, 1, (N, 3))
+    tgt = rng.normal(0, 1, (N, 3, H, W))
+    Phi = rng.normal(0, 1, (N, 3, H, W))
+    for q in (None, U.bf16):
+        _, g, s = U.loss_and_grads(params, b, I, t, A, Phi, tgt, q=q, scales=True)
+        assert g.shape == s.shape and np.all(np.abs(g) <= s * (1 + 1e-12) + 1e-300)
+    y, c = U.forward(params, b, I, t, A, Phi, q=U.bf16)
+    assert np.all(np.abs(y - Phi - (c["d1"] @ U.unpack(params, b)[2].T + U.unpack(params, b)[3]).transpose(0, 3, 1, 2))
+                  <= 1e-12 * (1 + c["y_scale"]))
