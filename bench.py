@@ -361,6 +361,30 @@ def train_warm_net(p, train_n=256, size=512, steps=600):
     return net
 
 
+WARM_NET = os.path.join(ROOT, "paper_2506_08793_gb300", "weights", "warmstart_b32_20k_512.npy")
+
+
+def warm_net(p):
+    """The warm-start network of config 5: the parameters stored beside the
+    package (trained by `python -m paper_2506_08793_gb300.warmstart --pairs
+    20000 --size 512 --chunk 1000 --epochs 1 --batch 8 --save ...` with the
+    library's own forward / backward / Adam kernels; the .json beside them
+    records the run), else one trained here on 256 pairs."""
+    from paper_2506_08793_gb300 import warmstart as WS
+
+    if not os.path.exists(WARM_NET):
+        return train_warm_net(p)
+    net = WS.WarmStartNet(32, seed=1)
+    net.load(WARM_NET)
+    rec = json.load(open(WARM_NET[:-4] + ".json"))
+    net.trained_on = {"scenes": rec["pairs"], "size": f"{rec['size']}x{rec['size']}",
+                      "adam_steps": int(round(rec["epochs"] * rec["chunk"] / rec["batch"])) * (
+                          (rec["pairs"] + rec["chunk"] - 1) // rec["chunk"]),
+                      "batch": rec["batch"], "train_s": rec["train_s"], "final_loss": rec["loss_last"],
+                      "parameters": os.path.relpath(WARM_NET, ROOT)}
+    return net
+
+
 def warm_extra(api, p, im, net):
     """Learned warm start on the 1080p scene: cold start (u0 = Phi) against the
     network's u0, to the same residual."""
@@ -632,7 +656,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras:
         line["batch"] = batch_extra(api, p)
         line["batch_16bit_storage"] = storage16_extra(api, p)
-        net = train_warm_net(p)
+        net = warm_net(p)
         line["warm_start"] = warm_extra(api, p, imgs[0], net)
         line["warm_batch_16bit"] = warm_batch_extra(api, p, net)
         line["semi_implicit"] = semi_extra(api, imgs[0])

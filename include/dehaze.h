@@ -90,7 +90,7 @@ typedef struct dh_params {
     float tol;          /* stop when max_c ||F^c(u^n)|| / ||Phi^c|| <= tol (1e-4) */
     int max_iter;       /* at most this many updates (default 5000) */
     int tb_depth;       /* fixed-point iterations per tile load: 0 = library choice (tuned or
-                           default), 1 = one, 2 = the temporally blocked sweep (W % 4 == 0,
+                           default), 1 = one, 2..4 = the temporally blocked sweeps (W % 4 == 0,
                            float32 storage; otherwise one) */
     int storage;        /* DH_STORE_* */
     int variant;        /* DH_VAR_* bits, 0 = the full method */

@@ -127,8 +127,15 @@ def forward(params, b, I, t, A, Phi, q=None):
     x0 = r(pack_input(np.asarray(I, np.float64), np.asarray(t, np.float64), np.asarray(A, np.float64), Phi))
     c["x0"] = x0
 
+    c["margin"] = [None] * 14
+
     def conv(x, k):
-        return r(relu(conv3x3(x, ws[k], bs[k])))
+        pre = conv3x3(x, ws[k], bs[k])
+        # how far the ReLU decisions are from zero, relative to the sum of the
+        # absolute values of each pre-activation's terms (smallest over units)
+        sc = conv3x3(np.abs(x), np.abs(ws[k]), np.abs(bs[k]))
+        c["margin"][k] = float(np.min(np.where(sc > 0, np.abs(pre) / np.where(sc > 0, sc, 1.0), 0.0)))
+        return r(relu(pre))
 
     a1 = conv(x0, 0); c["a1"] = a1
     e1 = conv(a1, 1); c["e1"] = e1

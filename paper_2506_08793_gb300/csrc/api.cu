@@ -50,7 +50,7 @@ static bool params_ok(const dh_params *p) {
     if (!(p->tau > 0.f) || !std::isfinite(p->tau)) return false;
     if (!(p->tol >= 0.f)) return false;
     if (p->max_iter < 0 || p->max_iter > 10000000) return false;
-    if (p->tb_depth < 0 || p->tb_depth > 2) return false;
+    if (p->tb_depth < 0 || p->tb_depth > 4) return false;
     if (p->storage < DH_STORE_F32 || p->storage > DH_STORE_F16_F32) return false;
     if (p->variant & ~(DH_VAR_NO_ADAPTIVE | DH_VAR_NO_EDGE | DH_VAR_NO_NONLOCAL)) return false;
     if (p->sweep_variant < 0 || p->sweep_variant >= sweep_variant_count()) return false;

@@ -18,8 +18,10 @@ constexpr size_t kAlign = 256;
 // columns and walks R rows; a warp covers the 128 columns of the tile.
 constexpr int kTW = 128;
 // The two-iteration sweep writes 120 output columns per tile (its first
-// iteration covers the 128 columns around them).
+// iteration covers the 128 columns around them); a sweep of depth K writes
+// 128 - 8(K-1), the narrowest 104 (K = 4).
 constexpr int kTW2 = 120;
+constexpr int kTWmin = kTW - 8 * 3;
 
 // ---------------------------------------------------------------- device state
 // Iteration state of one image, in the workspace.
@@ -108,9 +110,9 @@ static inline WsLayout ws_layout(int H, int W, int depth, int tile_h, size_t ref
     const size_t N = (size_t)H * W;
     L.depth = depth;
     L.tile_h = tile_h;
-    // tiles of the widest tiling any sweep uses (128 columns, or 120 for the
-    // two-iteration sweep) and the shortest (tile_h rows)
-    L.nblk_sweep = ((W + kTW2 - 1) / kTW2) * ((H + tile_h - 1) / tile_h);
+    // tiles of the narrowest tiling any sweep uses (128 columns, or down to
+    // 104 for the temporally blocked sweeps) and the shortest (tile_h rows)
+    L.nblk_sweep = ((W + kTWmin - 1) / kTWmin) * ((H + tile_h - 1) / tile_h);
     L.nblk_dcp = dcp_blocks(H, W);
     L.nblk_sel = kSelBlocks;
     size_t o = 0;

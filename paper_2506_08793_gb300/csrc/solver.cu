@@ -97,7 +97,7 @@ constexpr int kItersPerLaunch = 64;
 
 constexpr int kMinTileH = 16;  // smallest tile height any variant uses
 
-int sweep_depth(const dh_params *) { return 2; }  // residual levels per tile (two-iteration sweep)
+int sweep_depth(const dh_params *) { return 4; }  // residual levels per tile (temporally blocked sweeps)
 int sweep_tile_h(int) { return kMinTileH; }
 
 template <class T>
@@ -161,9 +161,13 @@ static const SweepCfg kVariants[] = {
     // 33-35: one producer warp + NW compute warps, two stages, Phi/lambda staged, no block
     // barrier inside an iteration (tma 5), multi-iteration launches
     {4, 8, 2, 5, true, 2, 1}, {6, 4, 2, 5, true, 2, 1}, {8, 4, 2, 5, true, 2, 1},
+    // 36-38: K iterations per tile load (tma 7, stages = K): 112 x 16, 112 x 24 and 104 x 16 output tiles
+    {4, 4, 3, 7, true, 3, 1}, {6, 4, 3, 7, true, 2, 1}, {4, 4, 4, 7, true, 2, 1},
 };
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 constexpr int kTb2Variant = 31;  // the two-iteration sweep with 120 x 16 tiles
+constexpr int kTb3Variant = 36;  // depth 3, 112 x 16 output tiles
+constexpr int kTb4Variant = 38;  // depth 4, 104 x 16 output tiles
 
 int sweep_variant_count() { return kNumVariants; }
 bool sweep_variant_usable(int v, int W, bool aligned) {
@@ -213,9 +217,12 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) v = tune_get(dev, H, W, p->storage);
         // tb_depth: iterations per tile load requested by the caller
-        const bool two = v > 0 && v < kNumVariants && kVariants[v].tma == 4;
-        if (p->tb_depth == 2 && !two) v = kTb2Variant;
-        if (p->tb_depth == 1 && two) v = 0;
+        const int t = v > 0 && v < kNumVariants ? kVariants[v].tma : 0;
+        const int depth = t == 4 ? 2 : (t == 7 ? kVariants[v].stages : 1);
+        if (p->tb_depth == 2 && depth != 2) v = kTb2Variant;
+        if (p->tb_depth == 3 && depth != 3) v = kTb3Variant;
+        if (p->tb_depth == 4 && depth != 4) v = kTb4Variant;
+        if (p->tb_depth == 1 && depth != 1) v = 0;
     }
     if (p->boundary == DH_BOUNDARY_ZERO && v > 0 && v < kNumVariants && kVariants[v].tma == 3) v = 0;
     if (v > 0 && v < kNumVariants && (kVariants[v].tma == 0 || tma_ok)) {
@@ -232,12 +239,12 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
             c.minb = mb;
             c.tma = tma_ok ? t : 0;
             if (c.tma == 3 && p->boundary == DH_BOUNDARY_ZERO) c.tma = 1;
-            c.multi = c.tma == 1 ? (mu != 0) : ((c.tma == 4 || c.tma == 5 || c.tma == 6) ? 1 : 0);
+            c.multi = c.tma == 1 ? (mu != 0) : ((c.tma == 4 || c.tma == 5 || c.tma == 6 || c.tma == 7) ? 1 : 0);
         }
     }
     if (!c.tma && !sweep_fn<float>(c.R, c.NW, c.edge)) { c.R = 8; c.NW = 4; }
     if (!c.tma) c.stages = 1;
-    if (c.tma != 1 && c.tma != 4 && c.tma != 5 && c.tma != 6) c.multi = 0;
+    if (c.tma != 1 && c.tma != 4 && c.tma != 5 && c.tma != 6 && c.tma != 7) c.multi = 0;
     if (c.tma == 0) c.minb = 0;
     return c;
 }
@@ -440,6 +447,26 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
         if (rc) return rc;
         SweepTmaFn fn = sweep_tb2_fn(cfg.R, cfg.NW, cfg.edge);
         const unsigned smem = tb2_smem_bytes(cfg.R, cfg.NW);
+        if (!fn || !smem) return DH_EINVAL;
+        const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
+        if (gmax <= 0) return DH_ECUDA;
+        const int items = 3 * v.nblk;
+        ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(cfg.NW * 32), smem, args_tma};
+        ls.coop = 1;
+        v.depth = kItersPerLaunch;
+    } else if (cfg.tma == 7 && esize == 4) {
+        // K = cfg.stages iterations per tile load: (128 - 8(K-1)) x TH output tiles
+        const int K = cfg.stages, TH = cfg.th(), WO = kTW - 8 * (K - 1);
+        if (TH < kMinTileH || K < 2 || K > 4) return DH_EINVAL;
+        v.nblk = ((W + WO - 1) / WO) * ((H + TH - 1) / TH);
+        if (v.nblk > L.nblk_sweep || L.depth < K) return DH_EINVAL;
+        int rc = encode_f32_map(&maps[0], v.u[0], 3, W, H, 3, kTW + 8, TH + 4 * K);
+        if (!rc) rc = encode_f32_map(&maps[1], v.u[1], 3, W, H, 3, kTW + 8, TH + 4 * K);
+        if (!rc) rc = encode_f32_map(&maps[2], v.phi, 3, W, H, 3, kTW, TH + 4 * (K - 1));
+        if (!rc) rc = encode_f32_map(&maps[3], v.lam, 2, W, H, 1, kTW, TH + 4 * (K - 1));
+        if (rc) return rc;
+        SweepTmaFn fn = sweep_tbk_fn(K, cfg.R, cfg.NW, cfg.edge);
+        const unsigned smem = tbk_smem_bytes(K, cfg.R, cfg.NW);
         if (!fn || !smem) return DH_EINVAL;
         const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
         if (gmax <= 0) return DH_ECUDA;

@@ -856,6 +856,371 @@ k_sweep_stream(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant_
 }
 
 
+// ---------------------------------------------------------------- K iterations per tile load
+// Temporally blocked sweep of depth K (float iterates, W % 4 == 0, 16-byte
+// aligned planes): the generalisation of k_sweep_tb2 to K = 2..4.  An item is
+// a WO x TH output tile of one channel, WO = 128 - 8(K-1).  All K steps walk
+// one frame of 128 columns: lane L owns global columns xf + 4L .. xf + 4L + 3,
+// xf = x0 - 4(K-1).  TMA loads u^n on the frame with a 4-column / 2K-row ring
+// (136 x (TH + 4K), starting at (x0 - 4K, y0 - 2K)) and Phi / lambda on the
+// frame's 128 columns and the TH + 4(K-1) rows of step 1.  Step s (1..K) walks
+// the frame rows y0 - 2(K-s) .. y0 + TH + 2(K-s) - 1 from the iterate of step
+// s-1 (the TMA tile for s = 1, else a shared buffer in which the boundary rule
+// has been applied) and writes u^{n+s} to the other shared buffer, or for s = K
+// the output tile to global memory.  Lanes s-1 .. 32-s hold valid values after
+// step s; the output lanes are K-1 .. 32-K.  The residual of step s over the
+// output tile is F(u^{n+s-1}), the quantity one iteration at a time gives; the
+// last CTA at the grid barrier decides with all K of them (finish_tbk): stop
+// at n, advance by K, or, when some u^{n+l} with 0 < l < K is the iterate to
+// return, switch the rest of the solve to one iteration per load (step 1 writes
+// the output tile to global memory), which recomputes u^{n+1} .. and stops there.
+template <int K, int RO, int NW>
+struct TbkPlan {
+    static constexpr int TH = RO * NW;
+    static constexpr int WO = kTW - 8 * (K - 1);  // output columns
+    static constexpr int SW = kTW + 8;             // 136 floats per shared row
+    static constexpr int F1 = TH + 4 * (K - 1);    // frame rows of step 1
+    static constexpr uint32_t U0_BYTES = (TH + 4 * K) * SW * 4;
+    static constexpr uint32_t PL_BYTES = F1 * kTW * 4;
+    static constexpr uint32_t BUF_BYTES = F1 * SW * 4;
+    static constexpr uint32_t U0_OFF = 0;
+    static constexpr uint32_t PHI_OFF = (U0_BYTES + 1023) / 1024 * 1024;
+    static constexpr uint32_t LAM_OFF = PHI_OFF + PL_BYTES;
+    static constexpr uint32_t B0_OFF = (LAM_OFF + PL_BYTES + 1023) / 1024 * 1024;
+    static constexpr uint32_t B1_OFF = (B0_OFF + BUF_BYTES + 1023) / 1024 * 1024;
+    static constexpr uint32_t SMEM = (K >= 3 ? B1_OFF + BUF_BYTES : B0_OFF + BUF_BYTES) + 1024;  // + alignment slack
+    static constexpr uint32_t TX = U0_BYTES + 2 * PL_BYTES;
+    static_assert(K >= 2 && K <= 4, "depth 2..4");
+    static_assert((4 * (K - 1)) % NW == 0, "every step's frame rows must split evenly over the warps");
+};
+
+// Last CTA of a depth-K sweep: residuals of the K levels, decision.
+template <int K>
+static __device__ void finish_tbk(const SolveDesc *d, SolveState *st) {
+    constexpr int L3 = 3 * K;
+    __shared__ float2 wsum[L3][32];
+    __shared__ float sq[L3];
+    const int tid = threadIdx.x, nt = blockDim.x, w = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    __threadfence();
+    const int nblk = d->nblk;
+    const float2 *part = d->part;
+    float s[L3], cc[L3];
+#pragma unroll
+    for (int q = 0; q < L3; ++q) s[q] = cc[q] = 0.f;
+    for (int b = tid; b < nblk; b += nt) {
+#pragma unroll
+        for (int q = 0; q < L3; ++q) {
+            const float2 v = __ldcg(part + (size_t)q * nblk + b);
+            neumaier_merge(s[q], cc[q], v.x, v.y);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < L3; ++q) {
+        for (int off = 16; off; off >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s[q], off);
+            const float c2 = __shfl_down_sync(0xffffffffu, cc[q], off);
+            neumaier_merge(s[q], cc[q], s2, c2);
+        }
+        if (lane == 0) wsum[q][w] = make_float2(s[q], cc[q]);
+    }
+    __syncthreads();
+    if (tid < L3) {
+        float a = wsum[tid][0].x, b = wsum[tid][0].y;
+        for (int q = 1; q < nw; ++q) neumaier_merge(a, b, wsum[tid][q].x, wsum[tid][q].y);
+        sq[tid] = a + b;
+    }
+    __syncthreads();
+    if (tid != 0) return;
+    const int n = st->n, deep = st->tb2;
+    auto rho_of = [&](int lv, float *rho, float &worst) {
+        bool finite = true;
+        worst = 0.f;
+        for (int c = 0; c < 3; ++c) {
+            const float pn = st->phin2[c], q = sq[3 * lv + c];
+            rho[c] = pn > 0.f ? sqrtf(q / pn) : sqrtf(q);
+            if (!isfinite(rho[c])) finite = false;
+            else worst = fmaxf(worst, rho[c]);
+        }
+        return finite;
+    };
+    float rho0[3], w0;
+    const bool fin0 = rho_of(0, rho0, w0);
+    if (d->rho_hist)
+        for (int c = 0; c < 3; ++c) d->rho_hist[3 * n + c] = rho0[c];
+    const int err = __ldcg(&st->err);
+    const bool conv = fin0 && w0 <= d->tol;
+    unsigned cont = 1;
+    if (err || conv || !fin0 || n >= d->max_iter) {
+        st->done = 1;
+        st->n_final = n;
+        st->status = err ? err : (!fin0 ? DH_ENONFINITE : (conv ? DH_OK : DH_WNOCONV));
+        for (int c = 0; c < 3; ++c) st->rho[c] = rho0[c];
+        cont = 0;
+    } else if (!deep) {
+        st->n = n + 1;
+        st->cur ^= 1;
+    } else {
+        // u^{n+l}, 0 < l < K, is the answer if its residual meets tol, is not
+        // finite or n + l reaches max_iter: then redo it one iteration at a time
+        bool redo = false;
+        for (int l = 1; l < K && !redo; ++l) {
+            float rl[3], wl;
+            const bool fin = rho_of(l, rl, wl);
+            redo = !fin || wl <= d->tol || n + l >= d->max_iter;
+        }
+        if (redo) {
+            st->tb2 = 0;
+        } else {
+            if (d->rho_hist)
+                for (int l = 1; l < K; ++l) {
+                    float rl[3], wl;
+                    rho_of(l, rl, wl);
+                    for (int c = 0; c < 3; ++c) d->rho_hist[3 * (n + l) + c] = rl[c];
+                }
+            st->n = n + K;
+            st->cur ^= 1;
+        }
+    }
+    st->arrive = 0;
+    __threadfence();
+    if (d->use_cond) cudaGraphSetConditional(d->cond, cont);
+}
+
+// Step S of a depth-K item: walks the step's frame rows from `src` (row 0 =
+// global row y0 - 2(K-S+1) + 2 - 2 ... see TbkPlan), accumulates F over the
+// output tile into (rs, rc), and writes u^{n+S} to `dst` (S < K, depth mode)
+// or the output tile to global memory (S = K, or S = 1 one iteration at a time).
+template <int K, int RO, int NW, int S, bool EDGE>
+__device__ __forceinline__ void tbk_step(const float *src, float *dst, float *__restrict__ gout, const float *sphi,
+                                         const float *slam, bool deep, int x0, int y0, int H, int W, int lane, int w,
+                                         float eps, float tau, float wg0, float wg1, float wg2, float &rs, float &rc) {
+    using P = TbkPlan<K, RO, NW>;
+    constexpr int TH = P::TH, SW = P::SW;
+    constexpr int R = RO + 4 * (K - S) / NW;  // rows per warp of this step
+    constexpr int T0 = 2 * (K - S);           // first frame row of the output tile
+    const int gx = x0 - 4 * (K - 1) + 4 * lane;
+    const bool lane_out = lane >= K - 1 && lane <= 32 - K && gx < W;
+    const bool to_global = S == K || !deep;
+    auto pl = [&](int t, float *ph, float *la) {
+        const int r = t + 2 * (S - 1);
+        const float4 p4 = *reinterpret_cast<const float4 *>(sphi + r * kTW + 4 * lane);
+        const float4 l4 = *reinterpret_cast<const float4 *>(slam + r * kTW + 4 * lane);
+        ph[0] = p4.x; ph[1] = p4.y; ph[2] = p4.z; ph[3] = p4.w;
+        la[0] = l4.x; la[1] = l4.y; la[2] = l4.z; la[3] = l4.w;
+    };
+    auto sink = [&](int t, const float *nu, const float *F) {
+        const int gy = y0 - T0 + t;
+        const bool in = lane_out && t >= T0 && t < T0 + TH && gy < H;
+        if (in) {
+            float q = 0.f;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) q = fmaf(F[jj], F[jj], q);
+            neumaier_add(rs, rc, q);
+        }
+        if (!to_global) {
+            *reinterpret_cast<float4 *>(dst + t * SW + 4 + 4 * lane) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+        } else if (in) {
+            *reinterpret_cast<float4 *>(gout + (size_t)gy * W + gx) = make_float4(nu[0], nu[1], nu[2], nu[3]);
+        }
+    };
+    walk_rows<R, SW, float, EDGE>(src, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
+}
+
+// The boundary rule on a shared iterate written by step s: its rows start at
+// global row ry0, its columns at global column cx0 (= x0 - 4K); nrows rows.
+template <int NW>
+__device__ __forceinline__ void tbk_boundary(float *buf, int nrows, int cx0, int ry0, int H, int W, bool dirichlet) {
+    constexpr int SW = kTW + 8;
+    if (dirichlet) {
+        for (int e = threadIdx.x; e < nrows * SW; e += NW * 32) {
+            const int r = e / SW, q = e - r * SW;
+            const int gy = ry0 + r, gx = cx0 + q;
+            if (gy < 0 || gy >= H || gx < 0 || gx >= W) buf[e] = 0.f;
+        }
+    } else {
+        reflect_border(buf, SW, SW, nrows, cx0, ry0, H, W);
+    }
+}
+
+template <int K, int RO, int NW, bool EDGE, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB)
+k_sweep_tbk(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
+            const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
+            const SolveDesc *__restrict__ d) {
+    using P = TbkPlan<K, RO, NW>;
+    constexpr int TH = P::TH, WO = P::WO, SW = P::SW;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float2 red[K][NW];
+    __shared__ int s_last, s_timeout;
+    float *s0 = reinterpret_cast<float *>(smem + P::U0_OFF);
+    const float *sphi = reinterpret_cast<const float *>(smem + P::PHI_OFF);
+    const float *slam = reinterpret_cast<const float *>(smem + P::LAM_OFF);
+    float *b0 = reinterpret_cast<float *>(smem + P::B0_OFF);
+    float *b1 = reinterpret_cast<float *>(smem + (K >= 3 ? P::B1_OFF : P::B0_OFF));
+
+    SolveState *st = d->st;
+    clear_condition(d);
+    if (__ldcg(&st->done)) return;
+    unsigned gen = ld_acquire_gpu(&st->gen);
+    const int H = d->H, W = d->W;
+    const size_t N = (size_t)H * W;
+    const int ntx = (W + WO - 1) / WO, nty = (H + TH - 1) / TH;
+    const int nitems = 3 * ntx * nty;
+    const int G = gridDim.x;
+    const int m = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const float eps = d->eps, tau = d->tau, wg0 = d->wg0, wg1 = d->wg1, wg2 = d->wg2;
+    const bool dirichlet = d->dirichlet != 0;
+    float2 *__restrict__ part = d->part;
+    const int nblk = d->nblk;
+    int k = 0;
+    bool failed = false;
+    for (int it = 0; it < d->depth; ++it) {
+        const int cur = __ldcg(&st->cur);
+        const bool rev = (__ldcg(&st->n) & 1) != 0;
+        const bool deep = __ldcg(&st->tb2) != 0;
+        const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
+        float *__restrict__ uout = static_cast<float *>(d->u[cur ^ 1]);
+        auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
+        auto tile_xy = [&](int item, int &c, int &x0, int &y0) {
+            const int tile = item / 3;
+            c = item - 3 * tile;
+            x0 = (tile % ntx) * WO;
+            y0 = (tile / ntx) * TH;
+            return tile;
+        };
+        auto issue = [&](int j) {
+            int c, x0, y0;
+            tile_xy(item_at(j), c, x0, y0);
+            mbar_arrive_expect_tx(&bar, P::TX);
+            tma_load_3d(smem + P::U0_OFF, tm_u, &bar, x0 - 4 * K, y0 - 2 * K, c);
+            tma_load_3d(smem + P::PHI_OFF, &tm_phi, &bar, x0 - 4 * (K - 1), y0 - 2 * (K - 1), c);
+            tma_load_2d(smem + P::LAM_OFF, &tm_lam, &bar, x0 - 4 * (K - 1), y0 - 2 * (K - 1));
+        };
+        auto prefetch = [&](int j) {
+            int c, x0, y0;
+            tile_xy(item_at(j), c, x0, y0);
+            tma_prefetch_3d(tm_u, x0 - 4 * K, y0 - 2 * K, c);
+            tma_prefetch_3d(&tm_phi, x0 - 4 * (K - 1), y0 - 2 * (K - 1), c);
+            tma_prefetch_2d(&tm_lam, x0 - 4 * (K - 1), y0 - 2 * (K - 1));
+        };
+        if (threadIdx.x == 0) {
+            if (it > 0) fence_proxy_async_global();
+            if (m > 0) issue(0);
+        }
+        int j = 0;
+        for (; j < m; ++j, ++k) {
+            int c, x0, y0;
+            const int tile = tile_xy(item_at(j), c, x0, y0);
+            if (threadIdx.x == 0 && j + 1 < m) prefetch(j + 1);
+            const bool ok = mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);
+            if (__syncthreads_or(!ok)) {
+                failed = true;
+                break;
+            }
+            const int cx0 = x0 - 4 * K;  // global column of shared column 0 (every buffer)
+            const bool border = cx0 < 0 || y0 - 2 * K < 0 || cx0 + SW > W || y0 + TH + 2 * K > H;
+            if (border && !dirichlet) {  // the reflecting boundary on the u^n tile
+                reflect_border(s0, SW, SW, TH + 4 * K, cx0, y0 - 2 * K, H, W);
+                fence_proxy_async_smem();  // these writes precede the next TMA load into this buffer
+            }
+            __syncthreads();
+            float rs[K], rc[K];
+#pragma unroll
+            for (int l = 0; l < K; ++l) rs[l] = rc[l] = 0.f;
+            float *__restrict__ gout = uout + c * N;
+            tbk_step<K, RO, NW, 1, EDGE>(s0, b0, gout, sphi, slam, deep, x0, y0, H, W, lane, w, eps, tau, wg0, wg1,
+                                         wg2, rs[0], rc[0]);
+            if (deep) {
+                __syncthreads();
+                if (border) {
+                    tbk_boundary<NW>(b0, TH + 4 * (K - 1), cx0, y0 - 2 * (K - 1), H, W, dirichlet);
+                    __syncthreads();
+                }
+                tbk_step<K, RO, NW, 2, EDGE>(b0, b1, gout, sphi, slam, deep, x0, y0, H, W, lane, w, eps, tau, wg0,
+                                             wg1, wg2, rs[1], rc[1]);
+                if constexpr (K >= 3) {
+                    __syncthreads();
+                    if (border) {
+                        tbk_boundary<NW>(b1, TH + 4 * (K - 2), cx0, y0 - 2 * (K - 2), H, W, dirichlet);
+                        __syncthreads();
+                    }
+                    tbk_step<K, RO, NW, 3, EDGE>(b1, b0, gout, sphi, slam, deep, x0, y0, H, W, lane, w, eps, tau,
+                                                 wg0, wg1, wg2, rs[2], rc[2]);
+                }
+                if constexpr (K >= 4) {
+                    __syncthreads();
+                    if (border) {
+                        tbk_boundary<NW>(b0, TH + 4 * (K - 3), cx0, y0 - 2 * (K - 3), H, W, dirichlet);
+                        __syncthreads();
+                    }
+                    tbk_step<K, RO, NW, 4, EDGE>(b0, b1, gout, sphi, slam, deep, x0, y0, H, W, lane, w, eps, tau,
+                                                 wg0, wg1, wg2, rs[3], rc[3]);
+                }
+            }
+            float2 tot[K];
+#pragma unroll
+            for (int l = 0; l < K; ++l) tot[l] = block_pair_sum<NW>(rs[l], rc[l], red[l]);  // each ends with a barrier
+            if (threadIdx.x == 0) {
+#pragma unroll
+                for (int l = 0; l < K; ++l) part[(size_t)(3 * l + c) * nblk + tile] = tot[l];
+                if (j + 1 < m) {
+                    fence_proxy_async_smem();
+                    issue(j + 1);
+                }
+            }
+            __syncthreads();
+        }
+        if (failed) {
+            if (j < m) mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);  // the load in flight
+            if (threadIdx.x == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
+        }
+        // grid barrier; the last CTA to arrive decides
+        fence_proxy_async_global();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(&st->arrive, 1u) == (unsigned)G - 1u;
+            s_timeout = 0;
+        }
+        __syncthreads();
+        if (s_last) {
+            finish_tbk<K>(d, st);
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release_gpu(&st->gen, gen + 1u);
+            }
+        } else if (threadIdx.x == 0) {
+            const long long t0 = clock64();
+            while (ld_acquire_gpu(&st->gen) == gen) {
+                if (clock64() - t0 > kWaitLimitCycles) {
+                    s_timeout = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        ++gen;
+        __syncthreads();
+        if (s_timeout) {
+            if (threadIdx.x == 0) {
+                atomicCAS(&st->err, 0, DH_ETIMEOUT);
+                st->status = DH_ETIMEOUT;
+                st->done = 1;
+            }
+            return;
+        }
+        if (__ldcg(&st->done) || failed) return;
+    }
+}
+
 // ---------------------------------------------------------------- warp-specialised TMA sweep
 // Reflects the border halo cells (see reflect_border) in shared-memory rows
 // [r0, r0 + nr) of a staged tile, by the 32 lanes of one warp: exactly the
@@ -1151,6 +1516,8 @@ SweepTmaFn sweep_tb2_fn(int R, int NW, bool edge);
 uint32_t tb2_smem_bytes(int R, int NW);
 SweepStreamFn sweep_stream_fn(int NW, int NSLOT, bool edge);
 SweepTmaFn sweep_ws_fn(int kind, int R, int NW, int stages, int pl, bool edge, int minb, int multi);
+SweepTmaFn sweep_tbk_fn(int K, int RO, int NW, bool edge);
+uint32_t tbk_smem_bytes(int K, int RO, int NW);
 
 // Instance selector shared by the sweep_inst_*.cu files.
 #define DH_STX_T(T, r, nw, st, pls, mb, mu)                                                         \

@@ -197,12 +197,19 @@ def main():
     ap.add_argument("--epochs", type=float, default=1.0)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--eval", type=int, default=4, help="held-out 1080p scenes (seeds 6e6 + i)")
+    ap.add_argument("--save", default="", help="write the trained parameters (float32 .npy) and, beside "
+                                               "them, a .json record of the run")
     a = ap.parse_args()
     net, log, secs = train_chunked(a.pairs, a.size, a.chunk, a.epochs, a.batch)
     ev = evaluate(net, range(6_000_000, 6_000_000 + a.eval), 1080, 1920)
-    print(json.dumps({"pairs": a.pairs, "size": a.size, "chunk": a.chunk, "epochs": a.epochs, "batch": a.batch,
-                      "train_s": secs, "loss_first": log[0][1], "loss_last": log[-1][1],
-                      "eval_1080p": ev["summary"]}))
+    rec = {"pairs": a.pairs, "size": a.size, "chunk": a.chunk, "epochs": a.epochs, "batch": a.batch,
+           "base": net.base, "train_s": secs, "loss_first": log[0][1], "loss_last": log[-1][1], "log": log,
+           "eval_1080p": ev["summary"], "device": torch.cuda.get_device_name()}
+    if a.save:
+        net.save(a.save)
+        with open(a.save[:-4] + ".json" if a.save.endswith(".npy") else a.save + ".json", "w") as f:
+            json.dump(rec, f, indent=1)
+    print(json.dumps({k: v for k, v in rec.items() if k != "log"}))
 
 
 if __name__ == "__main__":

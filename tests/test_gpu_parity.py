@@ -228,7 +228,7 @@ def test_graph_and_host_loop_identical_and_resume_exact(N, api, orc):
 @pytest.mark.parametrize("H,W", [(64, 128), (100, 260), (33, 4), (300, 516), (1, 200), (2, 8), (45, 132)])
 def test_sweep_variants_agree(N, api, orc, H, W, monkeypatch):
     """Every sweep kernel (generic gather, TMA tiles of every shape, per-warp
-    row streams, two iterations per tile load, the warp-specialised kernel)
+    row streams, two to four iterations per tile load, the warp-specialised kernel)
     applies the same float32 operations to each pixel, but the PTX
     approximate square root and reciprocal of the face flux are not specified
     to the bit: their results can differ by an ulp from one code location to
@@ -239,7 +239,8 @@ def test_sweep_variants_agree(N, api, orc, H, W, monkeypatch):
     outs = {}
     for cfg in ("8,4,2,0", "8,4,2,1", "8,4,1,1", "4,8,2,1", "8,4,1,2", "4,8,2,2", "16,4,1,2", "16,4,2,0",
                 "8,4,1,3", "8,8,1,3", "16,4,1,3", "8,2,1,3", "4,8,1,3", "6,4,1,1,1,5", "8,4,1,1,1,0",
-                "4,4,1,4", "6,4,1,4", "4,8,2,5,1,2", "6,4,2,5,1,2", "8,4,2,5,1,2"):
+                "4,4,1,4", "6,4,1,4", "4,8,2,5,1,2", "6,4,2,5,1,2", "8,4,2,5,1,2", "4,4,3,7,1,3",
+                "6,4,3,7,1,2", "4,4,4,7,1,2"):
         monkeypatch.setenv("DH_SWEEP", cfg)
         u = dev(Phi.copy())
         rep, _ = api.fixed_point(u, dev(Phi), dev(lam), api.params("stable", tol=0.0, max_iter=12))

@@ -107,23 +107,35 @@ def test_network_forward_backward_against_oracle(N):
     moves add up along the chain of rounded gradient maps between the loss
     and a layer (the head's input gradient, each data gradient, each
     upsampling adjoint and skip + pooled sum): a layer whose gradient map went
-    through s rounding stages is held to 2 + s ulps of its scale."""
+    through s rounding stages is held to 2 + s ulps of its scale.  A ReLU
+    decision within such rounding of zero could go either way and pass or stop
+    a whole gradient value, so the test's network keeps every pre-activation
+    at least 2^-4 of its scale away from zero (checked on the oracle side):
+    half of each layer's channels have bias +0.5, half -0.5, and the weights
+    are uniform in +-1 / (9 C_in), so both ReLU paths are exercised."""
     from oracle import unet as U
 
     base, n, H, W = 16, 2, 16, 24
     I, t, A, tgt, Phi = _net_inputs(n, H, W, 40)
     npar = N.dh_unet_param_count(base)
     assert npar == U.param_count(base)
-    params = torch.empty(npar, device="cuda")
-    assert N.dh_unet_init(params, base, 7) == 0
+    host_params = np.zeros(npar)
+    o = 0
+    for k, (cin, cout) in enumerate(U.convs(base)):
+        nw = cout * 9 * cin
+        host_params[o:o + nw] = rnd(100 + k, nw, lo=-1.0, hi=1.0) / (9 * cin)
+        host_params[o + nw:o + nw + cout] = np.where(np.arange(cout) % 2 == 0, 0.5, -0.5)
+        o += nw + cout
+    # a head of ordinary size, so that the network's part of y is not negligible next to Phi
+    host_params[o:] = rnd(41, 3 * base + 3, lo=-0.3, hi=0.3)
+    params = torch.from_numpy(host_params.astype(np.float32)).cuda()
     ws = torch.empty(N.dh_unet_workspace_bytes(base, n, H, W, 1), dtype=torch.uint8, device="cuda")
     d = {k: torch.from_numpy(v).cuda() for k, v in dict(I=I, t=t, A=A, tgt=tgt, Phi=Phi).items()}
-    # a head of ordinary size, so that the network's part of y is not negligible next to Phi
-    params[-(3 * base + 3):] = torch.from_numpy(rnd(41, 3 * base + 3, lo=-0.3, hi=0.3).astype(np.float32)).cuda()
     y = torch.empty((n, 3, H, W), device="cuda")
     assert N.dh_unet_forward(params, base, d["I"], d["t"], d["A"], d["Phi"], n, H, W, y, ws, ws.numel()) == 0
     P = host(params).astype(np.float64)
     yo, c = U.forward(P, base, I, t, A, Phi, q=U.bf16)
+    assert min(c["margin"]) >= 2.0 ** -4, c["margin"]  # no ReLU decision near zero
     ulp = 2.0 ** -7
     dy = np.abs(host(y) - yo)
     bad = dy > 2 * ulp * c["y_scale"] + 1e-6

@@ -97,3 +97,25 @@ def test_gradient_scales_bound_the_gradients():
     y, c = U.forward(params, b, I, t, A, Phi, q=U.bf16)
     assert np.all(np.abs(y - Phi - (c["d1"] @ U.unpack(params, b)[2].T + U.unpack(params, b)[3]).transpose(0, 3, 1, 2))
                   <= 1e-12 * (1 + c["y_scale"]))
+
+
+def test_relu_margin():
+    """forward() reports, per convolution, the smallest |pre-activation| over
+    the sum of |terms| of the pre-activation: 1 for a single positive term,
+    and 0 when a unit sits exactly at zero."""
+    b = 8
+    params = np.zeros(U.param_count(b))
+    N, H, W = 1, 8, 8
+    I = np.full((N, 3, H, W), 0.5)
+    t = np.full((N, H, W), 0.5)
+    A = np.full((N, 3), 0.9)
+    Phi = np.full((N, 3, H, W), 0.2)
+    _, c = U.forward(params, b, I, t, A, Phi)
+    assert all(m == 0.0 for m in c["margin"])  # zero weights and biases: every unit at zero
+    o = 0
+    for cin, cout in U.convs(b):
+        o += cout * 9 * cin
+        params[o:o + cout] = 1.0  # biases only: every pre-activation is its bias
+        o += cout
+    _, c = U.forward(params, b, I, t, A, Phi)
+    assert all(m == 1.0 for m in c["margin"])
