@@ -445,6 +445,224 @@ int launch_tc(const bf16 *x, int ldx, int C, int N, int H, int W, const bf16 *w,
     return DH_OK;
 }
 
+// ---------------------------------------------------------------- weight gradient
+// dw[co][tap][ci] = sum_p dy[p][co] * x[p + tap][ci] on the tensor cores: a GEMM
+// with M = 128 output channels, N = NT input channels of one tap and K =
+// pixels, walked in k-blocks of one 32-pixel row segment.  The activations are
+// NHWC, so both operands come MN-major (channels contiguous): TMA loads
+// 32-channel x 32-pixel boxes with the 64-byte swizzle (one 64-byte row per
+// pixel, 8-pixel groups 512 bytes apart, each 32-channel box 2048 bytes after
+// the previous one) and the MMA reads them with its transpose bits set.  The
+// tap's shift is applied to the boxes' pixel coordinates (zero filled outside
+// the image), never to the channel coordinate.  One thread loads, one issues
+// the MMAs, on full/empty mbarriers; each CTA sums one split of the k-blocks
+// and writes its partial, which a second pass sums over the splits in order.
+constexpr int kWgBK = 32;  // pixels per k-block
+
+template <int NT>
+struct WgPlan {
+    static constexpr uint32_t A_BYTES = 4 * 2048;               // 128 output channels
+    static constexpr uint32_t B_BYTES = (NT / 32) * 2048;
+    static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = (int)(kTcSmemBudget / STAGE) < 8 ? (int)(kTcSmemBudget / STAGE) : 8;
+    static constexpr uint32_t SMEM = STAGES * STAGE + 1024;
+    static constexpr uint32_t TMEM_COLS = NT;
+};
+
+// Shared-memory descriptor of an MN-major operand with the 64-byte swizzle:
+// leading byte offset = distance between 32-element blocks along M/N, stride
+// byte offset = distance between 8-row groups along K.
+__device__ __forceinline__ uint64_t sw64_mn_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128, 1)
+k_wgrad_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmdy, int C, int Cout, int H,
+           int W, int nci, int kb_per_split, int total_kb, float *__restrict__ part, int *err) {
+    using P = WgPlan<NT>;
+    constexpr int S = P::STAGES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[S], empty[S], done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail, s_issued, s_consumed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int co0 = blockIdx.x * 128;
+    const int tap = blockIdx.y / nci, ci0 = (blockIdx.y - tap * nci) * NT;
+    const int dyt = tap / 3 - 1, dxt = tap % 3 - 1;
+    const int split = blockIdx.z;
+    const int kb0 = split * kb_per_split, kb1 = min(total_kb, kb0 + kb_per_split), nkb = max(0, kb1 - kb0);
+    const int segs = (W + kWgBK - 1) / kWgBK;
+    const int na = min(4, (Cout - co0 + 31) / 32);  // 32-channel boxes of dy inside Cout
+    const uint32_t tx = (uint32_t)na * 2048 + P::B_BYTES;
+    const uint32_t sbase = smem_addr(smem);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(P::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // the A boxes past Cout are never loaded: zero them once in every stage
+    for (int st = 0; st < S; ++st)
+        for (int e = tid; e < (4 - na) * 2048 / 16; e += 128)
+            *reinterpret_cast<uint4 *>(smem + st * P::STAGE + na * 2048 + e * 16) = make_uint4(0, 0, 0, 0);
+    fence_proxy_async_smem();
+    if (tid == 0) {
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        mbar_init(&done_bar, 1);
+        fence_mbar_init();
+        s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (tid == 0) {  // loads
+        int k = 0;
+        for (; k < nkb; ++k) {
+            const int st = k % S;
+            if (k >= S && !mbar_wait_bounded(&empty[st], (uint32_t)((k / S) - 1) & 1u, kTcWaitCycles)) {
+                s_fail = 1;
+                break;
+            }
+            const int kb = kb0 + k;
+            const int row = kb / segs, seg = kb - row * segs, n = row / H, y = row - n * H, x0 = seg * kWgBK;
+            unsigned char *As = smem + st * P::STAGE, *Bs = As + P::A_BYTES;
+            mbar_arrive_expect_tx(&full[st], tx);
+            for (int a = 0; a < na; ++a) tma_load_4d(smem_addr(As + a * 2048), &tmdy, &full[st], co0 + 32 * a, x0, y, n);
+#pragma unroll
+            for (int b = 0; b < NT / 32; ++b)
+                tma_load_4d(smem_addr(Bs + b * 2048), &tmx, &full[st], ci0 + 32 * b, x0 + dxt, y + dyt, n);
+        }
+        s_issued = k;
+    } else if (tid == 32) {  // MMAs: D[co][ci] += A[co][p] B[ci][p], both MN-major
+        constexpr uint32_t IDESC = f16_idesc(kTcBM, NT) | (1u << 15) | (1u << 16);
+        int k = 0;
+        for (; k < nkb; ++k) {
+            const int st = k % S;
+            if (!mbar_wait_bounded(&full[st], (uint32_t)(k / S) & 1u, kTcWaitCycles)) {
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t As = sbase + st * P::STAGE, Bs = As + P::A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < kWgBK / 16; ++kk)  // 16 pixels = two 8-row groups per MMA
+                tc_mma(tmem, sw64_mn_desc(As + kk * 1024, 2048, 512), sw64_mn_desc(Bs + kk * 1024, 2048, 512), IDESC,
+                       (k > 0 || kk > 0) ? 1u : 0u);
+            tc_commit(&empty[st]);
+        }
+        s_consumed = k;
+        tc_commit(&done_bar);
+    }
+    bool failed = !mbar_wait_bounded(&done_bar, 0, kTcWaitCycles);
+    __syncthreads();
+    failed = __syncthreads_or(failed || s_fail);
+    if (failed) {
+        if (tid == 0) {
+            for (int k = s_consumed; k < s_issued; ++k)
+                mbar_wait_bounded(&full[k % S], (uint32_t)(k / S) & 1u, kTcWaitCycles);
+            if (err) atomicExch(err, DH_ETIMEOUT);
+        }
+        __syncthreads();
+    }
+    tc_fence_after();
+
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 = output channels co0 + 32w + lane
+    const int co = co0 + warp * 32 + lane;
+    float *dst = part + (((size_t)split * Cout + co) * 9 + tap) * C + ci0;
+#pragma unroll 1
+    for (int c = 0; c < NT; c += 16) {
+        uint32_t r[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, r);
+        if (co < Cout && !failed) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (ci0 + c + j < C) dst[c + j] = nkb > 0 ? __uint_as_float(r[j]) : 0.f;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::TMEM_COLS)
+                     : "memory");
+}
+
+template <int NT>
+int launch_wgrad_tc(const bf16 *x, int ldx, int C, const bf16 *dy, int lddy, int Cout, int N, int H, int W,
+                    float *part, int splits, int *err, cudaStream_t s) {
+    using P = WgPlan<NT>;
+    static std::mutex mu;
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) return DH_ECUDA;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!attr_set[dev]) {
+            DH_CUDA_TRY(cudaFuncSetAttribute(k_wgrad_tc<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)P::SMEM));
+            attr_set[dev] = true;
+        }
+    }
+    CUtensorMap mx, mdy;
+    const cuuint32_t box[4] = {32, (cuuint32_t)kWgBK, 1, 1};
+    {
+        const cuuint64_t pitch = (cuuint64_t)ldx * sizeof(bf16);
+        const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+        const cuuint64_t strides[3] = {pitch, pitch * (cuuint64_t)W, pitch * (cuuint64_t)W * (cuuint64_t)H};
+        const int rc = encode_tiled_sw(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, x, dims, strides, box,
+                                       CU_TENSOR_MAP_SWIZZLE_64B);
+        if (rc) return rc;
+    }
+    {
+        const cuuint64_t pitch = (cuuint64_t)lddy * sizeof(bf16);
+        const cuuint64_t dims[4] = {(cuuint64_t)Cout, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+        const cuuint64_t strides[3] = {pitch, pitch * (cuuint64_t)W, pitch * (cuuint64_t)W * (cuuint64_t)H};
+        const int rc = encode_tiled_sw(&mdy, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, dy, dims, strides, box,
+                                       CU_TENSOR_MAP_SWIZZLE_64B);
+        if (rc) return rc;
+    }
+    const int total_kb = N * H * ((W + kWgBK - 1) / kWgBK);
+    const int kbps = (total_kb + splits - 1) / splits;
+    const int nci = (C + NT - 1) / NT;
+    dim3 grid((Cout + 127) / 128, 9 * nci, splits);
+    k_wgrad_tc<NT><<<grid, 128, P::SMEM, s>>>(mx, mdy, C, Cout, H, W, nci, kbps, total_kb, part, err);
+    DH_CUDA_TRY(cudaGetLastError());
+    return DH_OK;
+}
+
+}  // namespace
+
+// Weight gradient on the tensor cores into part[split][co][tap][ci] (fp32),
+// `splits` pixel splits; DH_EINVAL (nothing queued) when the layer is not one
+// it takes (C, Cout multiples of 16, 16-byte aligned pitches and bases).
+int conv3x3_wgrad_tc(const void *x, int ldx, int C, const void *dy, int lddy, int Cout, int N, int H, int W,
+                     float *part, int splits, int *err, cudaStream_t s) {
+    if (C % 16 || Cout % 16 || ldx % 8 || lddy % 8 || ((uintptr_t)x % 16) || ((uintptr_t)dy % 16) || splits < 1)
+        return DH_EINVAL;
+    const bf16 *X = (const bf16 *)x, *D = (const bf16 *)dy;
+    if (C <= 32) return launch_wgrad_tc<32>(X, ldx, C, D, lddy, Cout, N, H, W, part, splits, err, s);
+    if (C <= 64) return launch_wgrad_tc<64>(X, ldx, C, D, lddy, Cout, N, H, W, part, splits, err, s);
+    if (C <= 128) return launch_wgrad_tc<128>(X, ldx, C, D, lddy, Cout, N, H, W, part, splits, err, s);
+    return launch_wgrad_tc<256>(X, ldx, C, D, lddy, Cout, N, H, W, part, splits, err, s);
+}
+
+namespace {
+
 // ---------------------------------------------------------------- shallow layers
 // Layers with few channels (C <= 96 in, <= 96 out) are bound by reading their
 // input, which the general kernel above stages once per tap.  Here a tile is

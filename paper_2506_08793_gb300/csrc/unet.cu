@@ -663,6 +663,8 @@ int conv3x3_tc(const void *x, int ldx, int C, int N, int H, int W, const void *w
                void *y, int ldy, int *err, cudaStream_t s);
 int conv3x3_halo(const void *x, int ldx, int C, int N, int H, int W, const void *w, const float *b, int Cout,
                  bool relu, void *y, int ldy, int *err, cudaStream_t s);
+int conv3x3_wgrad_tc(const void *x, int ldx, int C, const void *dy, int lddy, int Cout, int N, int H, int W,
+                     float *part, int splits, int *err, cudaStream_t s);
 
 // tcgen05 kernel when the channel counts allow it (every layer of the
 // network does), else the mma.sync kernel below.
@@ -698,8 +700,17 @@ static int conv_wgrad(const bf16 *x, int ldx, int C, const bf16 *dy, int lddy, i
     int split_px = (M + splits - 1) / splits;
     split_px = (split_px + kWBK - 1) / kWBK * kWBK;
     splits = (M + split_px - 1) / split_px;
-    dim3 grid((Cout + 63) / 64, 9 * ((C + 63) / 64), splits);
-    k_conv3x3_wgrad<<<grid, 128, 0, s>>>(x, ldx, C, dy, lddy, Cout, N, H, W, split_px, part);
+    // tensor cores (tcgen05) from 96 input or 128 output channels (1.4-1.7x the
+    // mma.sync kernel there); below that the M = 128 output-channel tile is
+    // mostly empty and the mma.sync kernel is 6-10 % faster
+    int rc = (C >= 96 || Cout >= 128) ? conv3x3_wgrad_tc(x, ldx, C, dy, lddy, Cout, N, H, W, part, splits, nullptr, s)
+                                      : DH_EINVAL;
+    if (rc == DH_EINVAL) {
+        dim3 grid((Cout + 63) / 64, 9 * ((C + 63) / 64), splits);
+        k_conv3x3_wgrad<<<grid, 128, 0, s>>>(x, ldx, C, dy, lddy, Cout, N, H, W, split_px, part);
+    } else if (rc) {
+        return rc;
+    }
     k_sum_splits<<<gs((size_t)Cout * 9 * C), 256, 0, s>>>(part, splits, (size_t)Cout * 9 * C, dw, 0);
     const int bsplits = (M + 1023) / 1024;
     k_bias_grad<<<bsplits, 256, 0, s>>>(dy, lddy, Cout, M, 1024, part);

@@ -68,18 +68,25 @@ def test_conv_forward(N, n, H, W, C, ldx, Cout, relu):
     assert np.all(host(y)[..., Cout:] == 0)
 
 
-@pytest.mark.parametrize("n,H,W,C,Cout", [(2, 7, 13, 16, 32), (1, 30, 41, 64, 32), (2, 16, 16, 96, 64)])
-def test_conv_weight_gradient(N, n, H, W, C, Cout):
+@pytest.mark.parametrize("n,H,W,C,ldx,Cout,lddy", [
+    (2, 7, 13, 16, 16, 32, 32), (1, 30, 41, 64, 64, 32, 32), (2, 16, 16, 96, 96, 64, 64),
+    # the tensor-core kernel (C >= 96 or Cout >= 128) and the mma.sync one:
+    # channel pitches wider than C (skip concatenations), rows that end inside a
+    # 32-pixel segment, two output-channel tiles, two input-channel tiles,
+    # several pixel splits
+    (1, 9, 40, 48, 96, 16, 48), (1, 34, 70, 128, 128, 128, 128), (1, 9, 40, 384, 384, 256, 256),
+    (2, 64, 96, 32, 96, 32, 32), (1, 5, 3, 192, 192, 64, 64), (1, 9, 40, 96, 144, 32, 48)])
+def test_conv_weight_gradient(N, n, H, W, C, ldx, Cout, lddy):
     from oracle import unet as U
 
-    x = bf(rnd(5 + C, n, H, W, C))
-    dy = bf(rnd(6 + C, n, H, W, Cout))
-    _, gw, gb = U.conv3x3_backward(x.float().numpy().astype(np.float64), np.zeros((Cout, 3, 3, C)),
-                                   dy.float().numpy().astype(np.float64))
+    x = bf(rnd(5 + C, n, H, W, ldx))
+    dy = bf(rnd(6 + C, n, H, W, lddy))
+    _, gw, gb = U.conv3x3_backward(x.float().numpy()[..., :C].astype(np.float64), np.zeros((Cout, 3, 3, C)),
+                                   dy.float().numpy()[..., :Cout].astype(np.float64))
     dw = torch.zeros(Cout * 9 * C, device="cuda")
     db = torch.zeros(Cout, device="cuda")
-    scratch = torch.empty(16 << 20, dtype=torch.uint8, device="cuda")
-    rc = N.dh_conv3x3_backward_weights(x.cuda(), C, C, dy.cuda(), Cout, Cout, n, H, W, dw, db, scratch,
+    scratch = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    rc = N.dh_conv3x3_backward_weights(x.cuda(), ldx, C, dy.cuda(), lddy, Cout, n, H, W, dw, db, scratch,
                                        scratch.numel())
     assert rc == 0
     assert np.max(np.abs(host(dw).reshape(gw.shape) - gw)) <= 1e-4 * np.abs(gw).max()
