@@ -699,7 +699,12 @@ struct HaloPlan {
     static constexpr uint32_t ACC_COLS = CO <= 32 ? 32 : CO <= 64 ? 64 : 128;  // one accumulator
     static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
     static constexpr bool CP_ASYNC = C >= 64 || CO >= 96;    // staging by cp.async instead of TMA
+    // threads: 8 warps when all threads stage by cp.async (two warps per TMEM lane
+    // quadrant in the epilogue, each with half of the output channels), else 4
+    static constexpr int NTHR = CP_ASYNC ? 256 : 128;
+    static constexpr int NH = NTHR / 128;                     // warps per lane quadrant
     static_assert(C % 16 == 0 && CO % 16 == 0 && CO <= 128, "channel counts");
+    static_assert((CO / NH) % 16 == 0, "each epilogue warp takes whole 16-column loads");
 };
 
 // K-major, no swizzle: leading byte offset = K-direction core-matrix stride,
@@ -713,7 +718,7 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t lbo, ui
 }
 
 template <int C, int CO>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(HaloPlan<C, CO>::NTHR)
 k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__ x, int ldx, int Nimg, int H, int W,
                const bf16 *__restrict__ w, const float *__restrict__ bias, int relu, bf16 *__restrict__ y, int ldy,
                int *err) {
@@ -744,9 +749,10 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
         }
         fence_mbar_init();
     }
-    for (int c = tid; c < CO; c += 128) s_bias[c] = bias ? __ldg(bias + c) : 0.f;
+    constexpr int NTHR = P::NTHR;
+    for (int c = tid; c < CO; c += NTHR) s_bias[c] = bias ? __ldg(bias + c) : 0.f;
     // weights [co][tap][ci] -> shared [tap][chunk][co] 16-byte rows
-    for (int e = tid; e < 9 * QC * CO; e += 128) {
+    for (int e = tid; e < 9 * QC * CO; e += NTHR) {
         const int co = e % CO, rest = e / CO, q = rest % QC, tap = rest / QC;
         cp_async_16(sbase + P::W_OFF + (uint32_t)e * 16, w + ((size_t)co * 9 + tap) * C + 8 * q, 16u);
     }
@@ -788,17 +794,36 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
         ++n_mma;
     };
     // all threads: the halo of tile i into stage i & 1 by cp.async (zero fill
-    // outside the image), one commit group per tile
+    // outside the image), one commit group per tile.  A halo row is 130 pixels
+    // x QC chunks; consecutive threads take consecutive chunks (of a pixel,
+    // then of the next pixel), and each thread advances its (pixel, chunk) by
+    // the thread count without dividing, from a per-row base pointer.
     auto stage = [&](int i) {
         const int t = (int)blockIdx.x + i * G;
         const int seg = t % segs, row = t / segs, n = row / H, yy = row - n * H;
         const uint32_t hb = sbase + P::H_OFF + (uint32_t)(i & 1) * P::H_STRIDE;
-        for (int e = tid; e < 390 * QC; e += 128) {
-            const int q = e % QC, rp = e / QC, r = rp / 130, p = rp - r * 130;
-            const int gx = seg * 128 + p - 1, gy = yy + r - 1;
-            const bool ok = gx >= 0 && gx < W && gy >= 0 && gy < H;
-            const bf16 *src = ok ? x + ((size_t)(n * H + gy) * W + gx) * ldx + 8 * q : x;
-            cp_async_16(hb + (uint32_t)q * P::CHUNK_BYTES + (uint32_t)rp * 16, src, ok ? 16u : 0u);
+        const int gx0 = seg * 128 - 1;
+        constexpr int PER_ROW = 130 * QC, DP = NTHR / QC, DQ = NTHR % QC;
+        const int p0 = tid / QC, q0 = tid - p0 * QC;
+#pragma unroll 1
+        for (int r = 0; r < 3; ++r) {
+            const int gy = yy + r - 1;
+            const bool rowok = gy >= 0 && gy < H;
+            const bf16 *rowbase = x + (size_t)(n * H + (rowok ? gy : 0)) * W * ldx;
+            const uint32_t rdst = hb + (uint32_t)(r * 130) * 16;
+            int p = p0, q = q0;
+            for (int e = tid; e < PER_ROW; e += NTHR) {
+                const int gx = gx0 + p;
+                const bool ok = rowok && gx >= 0 && gx < W;
+                const bf16 *src = ok ? rowbase + gx * ldx + 8 * q : x;
+                cp_async_16(rdst + (uint32_t)q * P::CHUNK_BYTES + (uint32_t)p * 16, src, ok ? 16u : 0u);
+                p += DP;
+                q += DQ;
+                if (q >= QC) {
+                    q -= QC;
+                    ++p;
+                }
+            }
         }
         cp_async_commit();
     };
@@ -863,13 +888,16 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
             if constexpr (P::CP_ASYNC) stage(i + 2);
             else if (tid == 0) issue(i + 2);
         }
-        // epilogue: TMEM lane = pixel of the segment
+        // epilogue: TMEM lane = pixel of the segment; warp w reads lane quadrant
+        // w % 4 (the only one it can access) and output channels of half w / 4
         const int t = (int)blockIdx.x + i * G;
         const int seg = t % segs, row = t / segs;
-        const int px = seg * 128 + warp * 32 + lane;
-        const uint32_t acc = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(i & 1) * P::ACC_COLS;
+        const int quad = warp & 3, half = warp >> 2;
+        const int px = seg * 128 + quad * 32 + lane;
+        const uint32_t acc = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(i & 1) * P::ACC_COLS;
 #pragma unroll
-        for (int c = 0; c < CO; c += 16) {
+        for (int cc = 0; cc < CO / P::NH; cc += 16) {
+            const int c = half * (CO / P::NH) + cc;
             uint32_t r[16];
             tmem_ld16(acc + (uint32_t)c, r);
             if (px < W && !failed) {
@@ -957,7 +985,7 @@ int launch_halo(const bf16 *x, int ldx, int N, int H, int W, const bf16 *w, cons
     }
     const long long T = (long long)N * H * ((W + 127) / 128);
     const int grid = (int)(T < grid_cache[dev] ? T : grid_cache[dev]);
-    k_conv3x3_halo<C, CO><<<grid, 128, P::SMEM, s>>>(map, x, ldx, N, H, W, w, b, relu ? 1 : 0, y, ldy, err);
+    k_conv3x3_halo<C, CO><<<grid, P::NTHR, P::SMEM, s>>>(map, x, ldx, N, H, W, w, b, relu ? 1 : 0, y, ldy, err);
     DH_CUDA_TRY(cudaGetLastError());
     return DH_OK;
 }
