@@ -667,38 +667,52 @@ namespace {
 // Layers with few channels (C <= 96 in, <= 96 out) are bound by reading their
 // input, which the general kernel above stages once per tap.  Here a tile is
 // a 128-pixel segment of one image row; its three input rows with a one-pixel
-// margin (3 x 130 pixels x C) are loaded once by TMA, one 8-channel chunk at a
-// time (box: 8 channels x 130 pixels x 3 rows = 6240 bytes, zero filled outside
-// the image, each chunk at a 128-byte aligned 6272-byte slot), so that chunk q
-// of pixel p of halo row r sits at q*6272 + (r*130 + p)*16 bytes: the
-// non-swizzled K-major layout ("core matrices" of 8 rows x 16 bytes).  Each of
-// the nine taps is the same staging viewed through a shifted descriptor: for
-// any start pixel the M = 128 rows of a tap are core matrices 128 bytes apart
-// (stride byte offset) and the two chunks of a K = 16 step are 6272 bytes
-// apart (leading byte offset).  With 64 or more input channels, or 96 output
-// channels (one or two CTAs per SM), the halo is instead staged by all threads
-// with 16-byte cp.async copies, consecutive threads on consecutive chunks of a
-// pixel (measured faster there: 96 -> 32 at 1080p 446 vs 578 us; TMA faster
-// for 16 and 32 input channels: 32 -> 32 125 vs 142 us).  All the weights stay in shared memory for the
+// margin (3 x 130 pixels x C) are loaded once by TMA and each of the nine taps
+// is the same staging viewed through a shifted descriptor.  Below 64 channels
+// the halo comes one 8-channel chunk at a time (box: 8 channels x 130 pixels x
+// 3 rows = 6240 bytes, zero filled outside the image, each chunk at a 128-byte
+// aligned 6272-byte slot), so that chunk q of pixel p of halo row r sits at
+// q*6272 + (r*130 + p)*16 bytes: the non-swizzled K-major layout ("core
+// matrices" of 8 rows x 16 bytes), in which the M = 128 rows of a tap starting
+// at any pixel are core matrices 128 bytes apart (stride byte offset) and the
+// two chunks of a K = 16 step are 6272 bytes apart (leading byte offset).  From
+// 64 channels, channels 0-63 come in one box with the 128-byte swizzle (a
+// 128-byte row per pixel; the swizzle follows the address bits, so a tap's
+// descriptor simply starts at its first pixel's row), the rest in 8-channel
+// chunks as above: 2 + 4 boxes per tile for 96 channels instead of 12 (the
+// 16-byte rows of the chunk boxes are what limits TMA there).  For 32 input and
+// 96 output channels the halo is staged by all threads with 16-byte cp.async
+// copies instead (eight warps).  All the weights stay in shared memory for the
 // CTA's lifetime ([tap][chunk][cout] 16-byte rows).  CTAs are persistent over
-// the tiles with two halo stages and two TMEM accumulators: while the warps run
-// the epilogue of tile i, the MMAs of tile i+1 run and the loads of tile i+2
-// are in flight.
+// the tiles with two TMEM accumulators and two halo stages (three for the wide
+// staging where shared memory allows): while the warps run the epilogue of tile
+// i, the MMAs of tile i+1 run and the loads of the following tiles are in flight.
 template <int C, int CO>
 struct HaloPlan {
     static constexpr int QC = C / 8;                         // 8-channel chunks
     static constexpr uint32_t W_BYTES = 9u * QC * CO * 16;
+    // "wide" staging (64 or more input channels): channels 0-63 of the three
+    // rows come in one TMA box with the 128-byte swizzle (one 128-byte row per
+    // pixel, 390 rows); the remaining channels, and all of them below 64, in
+    // 8-channel boxes of the non-swizzled core-matrix layout
+    static constexpr bool WIDE = C >= 64;
+    static constexpr int CW = WIDE ? 64 : 0;                 // channels in the swizzled box
+    static constexpr int QN = (C - CW) / 8;                  // 8-channel boxes
+    static constexpr uint32_t SW_BYTES = WIDE ? (390u * 128 + 1023) / 1024 * 1024 : 0;
     static constexpr uint32_t BOX_BYTES = 3u * 130 * 16;     // one chunk of the three rows
     static constexpr uint32_t CHUNK_BYTES = (BOX_BYTES + 127) / 128 * 128;  // its slot (TMA: 128-byte aligned)
-    static constexpr uint32_t TX_BYTES = QC * BOX_BYTES;     // bytes a tile's loads deliver
-    static constexpr uint32_t HALO_BYTES = QC * CHUNK_BYTES;
+    static constexpr uint32_t TX_BYTES = (WIDE ? 390u * 128 : 0) + QN * BOX_BYTES;  // bytes a tile's loads deliver
+    static constexpr uint32_t HALO_BYTES = SW_BYTES + QN * CHUNK_BYTES;
     static constexpr uint32_t W_OFF = 0;
     static constexpr uint32_t H_OFF = (W_BYTES + 1023) / 1024 * 1024;
     static constexpr uint32_t H_STRIDE = (HALO_BYTES + 1023) / 1024 * 1024;
-    static constexpr uint32_t SMEM = H_OFF + 2 * H_STRIDE + 1024;
+    // halo stages: three for the wide staging where they fit (the load of tile
+    // i+3 then has two tiles' time to land), else two
+    static constexpr int NST = (WIDE && H_OFF + 3 * H_STRIDE + 1024 <= 232448u) ? 3 : 2;
+    static constexpr uint32_t SMEM = H_OFF + NST * H_STRIDE + 1024;
     static constexpr uint32_t ACC_COLS = CO <= 32 ? 32 : CO <= 64 ? 64 : 128;  // one accumulator
     static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
-    static constexpr bool CP_ASYNC = C >= 64 || CO >= 96;    // staging by cp.async instead of TMA
+    static constexpr bool CP_ASYNC = !WIDE && CO >= 96;      // staging by cp.async instead of TMA
     // threads: 8 warps when all threads stage by cp.async (two warps per TMEM lane
     // quadrant in the epilogue, each with half of the output channels), else 4
     static constexpr int NTHR = CP_ASYNC ? 256 : 128;
@@ -706,6 +720,19 @@ struct HaloPlan {
     static_assert(C % 16 == 0 && CO % 16 == 0 && CO <= 128, "channel counts");
     static_assert((CO / NH) % 16 == 0, "each epilogue warp takes whole 16-column loads");
 };
+
+// K-major, 128-byte swizzle (rows of 128 bytes, 8-row groups 1024 bytes apart).
+// The swizzle follows the shared-memory address bits, so a start address
+// anywhere on a 128-byte row boundary of a 1024-byte aligned region reads the
+// rows from there on (the base offset field stays 0).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
 
 // K-major, no swizzle: leading byte offset = K-direction core-matrix stride,
 // stride byte offset = M/N-direction core-matrix stride.
@@ -719,14 +746,15 @@ __device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t lbo, ui
 
 template <int C, int CO>
 __global__ void __launch_bounds__(HaloPlan<C, CO>::NTHR)
-k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__ x, int ldx, int Nimg, int H, int W,
+k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUtensorMap tmw,
+               const bf16 *__restrict__ x, int ldx, int Nimg, int H, int W,
                const bf16 *__restrict__ w, const float *__restrict__ bias, int relu, bf16 *__restrict__ y, int ldy,
                int *err) {
     using P = HaloPlan<C, CO>;
     constexpr int QC = P::QC;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t tma_bar[2], mma_bar[2];
+    __shared__ __align__(8) uint64_t tma_bar[P::NST], mma_bar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ float s_bias[CO];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -743,10 +771,8 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int k = 0; k < 2; ++k) {
-            mbar_init(&tma_bar[k], 1);
-            mbar_init(&mma_bar[k], 1);
-        }
+        for (int k = 0; k < P::NST; ++k) mbar_init(&tma_bar[k], 1);
+        for (int k = 0; k < 2; ++k) mbar_init(&mma_bar[k], 1);
         fence_mbar_init();
     }
     constexpr int NTHR = P::NTHR;
@@ -767,27 +793,38 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
     // thread 0 alone issues the loads and the MMAs and counts them, so that a
     // CTA that gives up can still let everything in flight finish
     int n_load = 0, n_load_done = 0, n_mma = 0;
-    auto issue = [&](int i) {  // the halo of tile i into stage i & 1
+    auto issue = [&](int i) {  // the halo of tile i into stage i % NST
         const int t = (int)blockIdx.x + i * G;
         const int seg = t % segs, row = t / segs, n = row / H, yy = row - n * H;
-        const uint32_t hb = sbase + P::H_OFF + (uint32_t)(i & 1) * P::H_STRIDE;
-        mbar_arrive_expect_tx(&tma_bar[i & 1], P::TX_BYTES);
+        const uint32_t hb = sbase + P::H_OFF + (uint32_t)(i % P::NST) * P::H_STRIDE;
+        uint64_t *bar = &tma_bar[i % P::NST];
+        mbar_arrive_expect_tx(bar, P::TX_BYTES);
+        if constexpr (P::WIDE) tma_load_4d(hb, &tmw, bar, 0, seg * 128 - 1, yy - 1, n);
 #pragma unroll
-        for (int q = 0; q < QC; ++q)
-            tma_load_4d(hb + (uint32_t)q * P::CHUNK_BYTES, &tmx, &tma_bar[i & 1], 8 * q, seg * 128 - 1, yy - 1, n);
+        for (int q = 0; q < P::QN; ++q)
+            tma_load_4d(hb + P::SW_BYTES + (uint32_t)q * P::CHUNK_BYTES, &tmx, bar, P::CW + 8 * q,
+                        seg * 128 - 1, yy - 1, n);
         ++n_load;
     };
     constexpr uint32_t IDESC = f16_idesc(kTcBM, CO);
-    auto mmas = [&](int i) {  // the nine taps of tile i into accumulator i & 1
-        const uint32_t hb = sbase + P::H_OFF + (uint32_t)(i & 1) * P::H_STRIDE;
+    auto mmas = [&](int i) {  // the nine taps of tile i (stage i % NST) into accumulator i & 1
+        const uint32_t hb = sbase + P::H_OFF + (uint32_t)(i % P::NST) * P::H_STRIDE;
         const uint32_t acc = tmem + (uint32_t)(i & 1) * P::ACC_COLS;
         for (int tap = 0; tap < 9; ++tap) {
             const int dy = tap / 3, dx = tap % 3;  // halo row, start pixel
-            for (int kk = 0; kk < QC / 2; ++kk) {
-                const uint32_t a = hb + (uint32_t)(2 * kk) * P::CHUNK_BYTES + (uint32_t)((dy * 130 + dx) * 16);
-                const uint32_t b = sbase + P::W_OFF + (uint32_t)((tap * QC + 2 * kk) * CO * 16);
+            const int rowoff = dy * 130 + dx;      // first halo row (pixel) of the tap's 128 rows
+            if constexpr (P::WIDE) {
+                for (int kk = 0; kk < 4; ++kk) {  // channels 16kk .. 16kk+15 of the swizzled box
+                    const uint32_t a = hb + (uint32_t)rowoff * 128 + 32 * kk;
+                    const uint32_t b = sbase + P::W_OFF + (uint32_t)((tap * QC + 2 * kk) * CO * 16);
+                    tc_mma(acc, sw128_desc(a), kmajor_desc(b, CO * 16, 128), IDESC, (tap > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            for (int kk = 0; kk < P::QN / 2; ++kk) {
+                const uint32_t a = hb + P::SW_BYTES + (uint32_t)(2 * kk) * P::CHUNK_BYTES + (uint32_t)(rowoff * 16);
+                const uint32_t b = sbase + P::W_OFF + (uint32_t)((tap * QC + P::CW / 8 + 2 * kk) * CO * 16);
                 tc_mma(acc, kmajor_desc(a, P::CHUNK_BYTES, 128), kmajor_desc(b, CO * 16, 128), IDESC,
-                       (tap > 0 || kk > 0) ? 1u : 0u);
+                       (tap > 0 || P::WIDE || kk > 0) ? 1u : 0u);
             }
         }
         tc_commit(&mma_bar[i & 1]);
@@ -829,7 +866,7 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
     };
     // tile i's halo has landed (thread 0)
     auto landed = [&](int i) {
-        const bool ok = mbar_wait_bounded(&tma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles);
+        const bool ok = mbar_wait_bounded(&tma_bar[i % P::NST], (uint32_t)(i / P::NST) & 1u, kTcWaitCycles);
         if (ok) ++n_load_done;
         return ok;
     };
@@ -852,8 +889,7 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
             }
         }
     } else if (tid == 0 && nt > 0) {
-        issue(0);
-        if (nt > 1) issue(1);
+        for (int k = 0; k < P::NST && k < nt; ++k) issue(k);
         if (landed(0)) {
             tc_fence_after();
             mmas(0);
@@ -873,20 +909,42 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
                     mmas(i + 1);
                 }
             }
-        } else if (tid == 0 && !failed && i + 1 < nt) {
-            if (landed(i + 1)) {
-                tc_fence_after();
-                mmas(i + 1);
-            } else {
-                failed = true;
+            // tile i's MMAs are done: its accumulator is ready and its stage is free
+            if (!failed && !mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles)) failed = true;
+            tc_fence_after();
+            if (!failed && i + 2 < nt) stage(i + 2);
+        } else if constexpr (P::WIDE && P::NST == 2) {
+            // Wide halo in two stages (96 channels): thread 0 refills the stage
+            // tile i's MMAs release before it waits for tile i+1's halo, so that
+            // both stages' loads are in flight together (the load latency, not
+            // the MMAs, sets the pace here: 439 -> 346 us for 96 -> 32 at 1080p).
+            if (!failed && !mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles)) failed = true;
+            tc_fence_after();
+            if (tid == 0 && !failed) {
+                if (i + P::NST < nt) issue(i + P::NST);
+                if (i + 1 < nt) {
+                    if (landed(i + 1)) {
+                        tc_fence_after();
+                        mmas(i + 1);
+                    } else {
+                        failed = true;
+                    }
+                }
             }
-        }
-        // tile i's MMAs are done: its accumulator is ready and its stage is free
-        if (!failed && !mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles)) failed = true;
-        tc_fence_after();
-        if (!failed && i + 2 < nt) {
-            if constexpr (P::CP_ASYNC) stage(i + 2);
-            else if (tid == 0) issue(i + 2);
+        } else {
+            // the next tile's MMAs go in right behind this tile's, then the stage
+            // this tile's MMAs release is refilled
+            if (tid == 0 && !failed && i + 1 < nt) {
+                if (landed(i + 1)) {
+                    tc_fence_after();
+                    mmas(i + 1);
+                } else {
+                    failed = true;
+                }
+            }
+            if (!failed && !mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles)) failed = true;
+            tc_fence_after();
+            if (!failed && tid == 0 && i + P::NST < nt) issue(i + P::NST);
         }
         // epilogue: TMEM lane = pixel of the segment; warp w reads lane quadrant
         // w % 4 (the only one it can access) and output channels of half w / 4
@@ -930,7 +988,7 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const bf16 *__restrict__
         // shared and tensor memory go away
         if (tid == 0) {
             for (int k = n_load_done; k < n_load; ++k)
-                mbar_wait_bounded(&tma_bar[k & 1], (uint32_t)(k >> 1) & 1u, kTcWaitCycles);
+                mbar_wait_bounded(&tma_bar[k % P::NST], (uint32_t)(k / P::NST) & 1u, kTcWaitCycles);
             if (n_mma > 0) mbar_wait_bounded(&mma_bar[(n_mma - 1) & 1], (uint32_t)((n_mma - 1) >> 1) & 1u, kTcWaitCycles);
             if (err) atomicExch(err, DH_ETIMEOUT);
         }
@@ -958,10 +1016,20 @@ int launch_halo(const bf16 *x, int ldx, int N, int H, int W, const bf16 *w, cons
                 int ldy, int *err, cudaStream_t s) {
     using P = HaloPlan<C, CO>;
     if ((uintptr_t)x % 16) return DH_EINVAL;  // TMA and cp.async need a 16-byte aligned base
-    CUtensorMap map;
+    CUtensorMap map, wmap;
     std::memset(&map, 0, sizeof(map));
-    if (!P::CP_ASYNC) {
+    std::memset(&wmap, 0, sizeof(wmap));
+    if (!P::CP_ASYNC && P::QN > 0) {
         const int rc = encode_halo_map(&map, x, ldx, C, N, H, W);
+        if (rc) return rc;
+    }
+    if (P::WIDE) {
+        const cuuint64_t pitch = (cuuint64_t)ldx * sizeof(bf16);
+        const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+        const cuuint64_t strides[3] = {pitch, pitch * (cuuint64_t)W, pitch * (cuuint64_t)W * (cuuint64_t)H};
+        const cuuint32_t box[4] = {64, 130, 3, 1};
+        const int rc = encode_tiled_sw(&wmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, x, dims, strides, box,
+                                       CU_TENSOR_MAP_SWIZZLE_128B);
         if (rc) return rc;
     }
     static std::mutex mu;
@@ -985,7 +1053,8 @@ int launch_halo(const bf16 *x, int ldx, int N, int H, int W, const bf16 *w, cons
     }
     const long long T = (long long)N * H * ((W + 127) / 128);
     const int grid = (int)(T < grid_cache[dev] ? T : grid_cache[dev]);
-    k_conv3x3_halo<C, CO><<<grid, P::NTHR, P::SMEM, s>>>(map, x, ldx, N, H, W, w, b, relu ? 1 : 0, y, ldy, err);
+    k_conv3x3_halo<C, CO><<<grid, P::NTHR, P::SMEM, s>>>(map, wmap, x, ldx, N, H, W, w, b, relu ? 1 : 0, y, ldy,
+                                                         err);
     DH_CUDA_TRY(cudaGetLastError());
     return DH_OK;
 }
