@@ -291,20 +291,29 @@ def warm_batch_extra(api, p, net, n=64):
     sizes, imgs = _batch_images(n)
     gold = golden_batch()
     out = {"images": n, "network": {"base": net.base, "trained_on": getattr(net, "trained_on", None)}}
-    forms = (("cold_f32", 0, False), ("warm_f32", 0, True), ("warm_bf16_f32", 3, True), ("warm_fp16_f32", 4, True))
-    for name, st, warm in forms:
-        b = api.BatchDehazer(sizes, p.replace(storage=st), net=net if warm else None)
+    # the warm forms to the same residual (1e-4) and to 1e-5: the network leaves a
+    # smooth error along the iteration's slowest modes, so at the same residual a
+    # warm solution sits farther from the fixed point (max-abs) than the cold one
+    forms = (("cold_f32", 0, False, 1e-4), ("warm_f32", 0, True, 1e-4), ("warm_bf16_f32", 3, True, 1e-4),
+             ("warm_fp16_f32", 4, True, 1e-4), ("warm_f32_tol1e-5", 0, True, 1e-5),
+             ("warm_bf16_f32_tol1e-5", 3, True, 1e-5))
+    for name, st, warm, tol in forms:
+        b = api.BatchDehazer(sizes, p.replace(storage=st, tol=tol), net=net if warm else None)
         ms, rep = _time_batch(b, imgs)
         its = [x.n_iter for x in rep]
-        out[name] = {"ms": ms, "images_per_s": n / (ms / 1e3), "converged_to_tol": sum(x.status == 0 for x in rep),
+        out[name] = {"tol": tol, "ms": ms, "images_per_s": n / (ms / 1e3),
+                     "converged_to_tol": sum(x.status == 0 for x in rep),
                      "iterations": {"mean": sum(its) / n, "min": min(its), "max": max(its)},
                      "oracle_error": oracle_errors(b.out, gold)}
         del b
         torch.cuda.empty_cache()
     c = out["cold_f32"]
-    for name, _, warm in forms[1:]:
+    for name, _, _, _ in forms[1:]:
         out[name]["speedup_vs_cold_f32"] = c["ms"] / out[name]["ms"]
         out[name]["iterations_saved"] = 1.0 - out[name]["iterations"]["mean"] / c["iterations"]["mean"]
+        e, ec = out[name]["oracle_error"], c["oracle_error"]
+        if e and ec:  # max-abs error of u against the FP64 reference no larger than the cold batch's
+            out[name]["as_accurate_as_cold_f32"] = e["max_abs_u"]["max"] <= ec["max_abs_u"]["max"]
     return out
 
 
