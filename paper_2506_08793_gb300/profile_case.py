@@ -24,6 +24,8 @@ def main():
     ap.add_argument("--variant", type=int, default=0, help="sweep variant (0: library default)")
     ap.add_argument("--net", type=int, default=0, help="instead: N images through the warm-start network forward")
     ap.add_argument("--conv", default="", help="instead: one 3x3 convolution 'C,Cout' on 1 x H x W, --repeat times")
+    ap.add_argument("--wgrad", default="", help="instead: the weight gradient of one 3x3 convolution 'C,Cout' "
+                                                "on 1 x H x W, --repeat times")
     ap.add_argument("--batch", type=int, default=0,
                     help="instead: N images of the mixed photo sizes (seed 3000) in one batched solve")
     ap.add_argument("--semi", type=int, default=0,
@@ -70,6 +72,23 @@ def main():
                 raise SystemExit(f"dh_conv3x3_forward: {rc}")
         torch.cuda.synchronize()
         print(f"conv {C}->{Cout} on {a.H}x{a.W} x{a.repeat}: done")
+        return
+    if a.wgrad:
+        from . import _native as N
+
+        C, Cout = (int(v) for v in a.wgrad.split(","))
+        g = torch.Generator().manual_seed(a.seed)
+        x = (torch.rand(a.H * a.W * C, generator=g) - 0.5).to(torch.bfloat16).cuda()
+        dy = (torch.rand(a.H * a.W * Cout, generator=g) - 0.5).to(torch.bfloat16).cuda()
+        dw = torch.empty(Cout * 9 * C, device="cuda")
+        db = torch.empty(Cout, device="cuda")
+        scratch = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        for _ in range(a.repeat):
+            rc = N.dh_conv3x3_backward_weights(x, C, C, dy, Cout, Cout, 1, a.H, a.W, dw, db, scratch, scratch.numel())
+            if rc:
+                raise SystemExit(f"dh_conv3x3_backward_weights: {rc}")
+        torch.cuda.synchronize()
+        print(f"weight gradient {C}->{Cout} on {a.H}x{a.W} x{a.repeat}: done")
         return
     if a.net:
         from . import warmstart as WS
