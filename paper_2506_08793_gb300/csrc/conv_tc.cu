@@ -685,8 +685,13 @@ namespace {
 // copies instead (eight warps).  All the weights stay in shared memory for the
 // CTA's lifetime ([tap][chunk][cout] 16-byte rows).  CTAs are persistent over
 // the tiles with two TMEM accumulators and two halo stages (three for the wide
-// staging where shared memory allows): while the warps run the epilogue of tile
-// i, the MMAs of tile i+1 run and the loads of the following tiles are in flight.
+// staging where shared memory allows): the epilogue of tile i runs while the
+// MMAs of tile i+1 and the loads of the following tiles proceed.  With the wide
+// staging (one CTA per SM) the warps specialise: one warp loads halos as stages
+// free up, one issues each tile's MMAs as its halo lands and its accumulator
+// frees up, and four run the epilogues, all ordered by mbarriers (1.3-1.4x the
+// single-thread hand-off with a block barrier per tile, which the 16/32-channel
+// layers, three CTAs per SM, keep).
 template <int C, int CO>
 struct HaloPlan {
     static constexpr int QC = C / 8;                         // 8-channel chunks
@@ -714,9 +719,10 @@ struct HaloPlan {
     static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
     static constexpr bool CP_ASYNC = !WIDE && CO >= 96;      // staging by cp.async instead of TMA
     // threads: 8 warps when all threads stage by cp.async (two warps per TMEM lane
-    // quadrant in the epilogue, each with half of the output channels), else 4
-    static constexpr int NTHR = CP_ASYNC ? 256 : 128;
-    static constexpr int NH = NTHR / 128;                     // warps per lane quadrant
+    // quadrant in the epilogue, each with half of the output channels); with the
+    // wide staging 4 epilogue warps, a load warp and an MMA warp; else 4 warps
+    static constexpr int NTHR = CP_ASYNC ? 256 : (WIDE ? 192 : 128);
+    static constexpr int NH = CP_ASYNC ? 2 : 1;               // epilogue warps per lane quadrant
     static_assert(C % 16 == 0 && CO % 16 == 0 && CO <= 128, "channel counts");
     static_assert((CO / NH) % 16 == 0, "each epilogue warp takes whole 16-column loads");
 };
@@ -754,9 +760,11 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     constexpr int QC = P::QC;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t tma_bar[P::NST], mma_bar[2];
+    __shared__ __align__(8) uint64_t tma_bar[P::NST], mma_bar[2], stage_free[P::NST], acc_free[2];
     __shared__ uint32_t tmem_slot;
     __shared__ float s_bias[CO];
+    __shared__ volatile int s_fail;
+    __shared__ int s_issued, s_landed, s_mmas;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int segs = (W + 127) / 128;
     const int T = Nimg * H * segs;
@@ -771,9 +779,19 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int k = 0; k < P::NST; ++k) mbar_init(&tma_bar[k], 1);
-        for (int k = 0; k < 2; ++k) mbar_init(&mma_bar[k], 1);
+        for (int k = 0; k < P::NST; ++k) {
+            mbar_init(&tma_bar[k], 1);
+            mbar_init(&stage_free[k], 1);
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&mma_bar[k], 1);
+            mbar_init(&acc_free[k], 4);
+        }
         fence_mbar_init();
+        s_fail = 0;
+        s_issued = 0;
+        s_landed = 0;
+        s_mmas = 0;
     }
     constexpr int NTHR = P::NTHR;
     for (int c = tid; c < CO; c += NTHR) s_bias[c] = bias ? __ldg(bias + c) : 0.f;
@@ -790,8 +808,8 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    // thread 0 alone issues the loads and the MMAs and counts them, so that a
-    // CTA that gives up can still let everything in flight finish
+    // the thread that issues the loads (the MMAs) counts them, so that a CTA
+    // that gives up can still let everything in flight finish
     int n_load = 0, n_load_done = 0, n_mma = 0;
     auto issue = [&](int i) {  // the halo of tile i into stage i % NST
         const int t = (int)blockIdx.x + i * G;
@@ -871,83 +889,10 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
         return ok;
     };
 
-    bool failed = false;
-    if constexpr (P::CP_ASYNC) {
-        // two commit groups whatever nt is (an empty one when there is no
-        // tile 1), so that waiting for all but the newest one always means
-        // that tile 0 has landed
-        if (nt > 0) stage(0);
-        if (nt > 1) stage(1);
-        else cp_async_commit();
-        if (nt > 0) {
-            cp_async_wait<1>();
-            fence_proxy_async_smem();  // generic-proxy copies, read by the MMAs
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                mmas(0);
-            }
-        }
-    } else if (tid == 0 && nt > 0) {
-        for (int k = 0; k < P::NST && k < nt; ++k) issue(k);
-        if (landed(0)) {
-            tc_fence_after();
-            mmas(0);
-        } else {
-            failed = true;
-        }
-    }
-    for (int i = 0; i < nt; ++i) {
-        // the next tile's MMAs run while this tile's epilogue does
-        if constexpr (P::CP_ASYNC) {
-            if (i + 1 < nt) {
-                cp_async_wait<0>();
-                fence_proxy_async_smem();
-                __syncthreads();
-                if (tid == 0 && !failed) {
-                    tc_fence_after();
-                    mmas(i + 1);
-                }
-            }
-            // tile i's MMAs are done: its accumulator is ready and its stage is free
-            if (!failed && !mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles)) failed = true;
-            tc_fence_after();
-            if (!failed && i + 2 < nt) stage(i + 2);
-        } else if constexpr (P::WIDE && P::NST == 2) {
-            // Wide halo in two stages (96 channels): thread 0 refills the stage
-            // tile i's MMAs release before it waits for tile i+1's halo, so that
-            // both stages' loads are in flight together (the load latency, not
-            // the MMAs, sets the pace here: 439 -> 346 us for 96 -> 32 at 1080p).
-            if (!failed && !mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles)) failed = true;
-            tc_fence_after();
-            if (tid == 0 && !failed) {
-                if (i + P::NST < nt) issue(i + P::NST);
-                if (i + 1 < nt) {
-                    if (landed(i + 1)) {
-                        tc_fence_after();
-                        mmas(i + 1);
-                    } else {
-                        failed = true;
-                    }
-                }
-            }
-        } else {
-            // the next tile's MMAs go in right behind this tile's, then the stage
-            // this tile's MMAs release is refilled
-            if (tid == 0 && !failed && i + 1 < nt) {
-                if (landed(i + 1)) {
-                    tc_fence_after();
-                    mmas(i + 1);
-                } else {
-                    failed = true;
-                }
-            }
-            if (!failed && !mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles)) failed = true;
-            tc_fence_after();
-            if (!failed && tid == 0 && i + P::NST < nt) issue(i + P::NST);
-        }
-        // epilogue: TMEM lane = pixel of the segment; warp w reads lane quadrant
-        // w % 4 (the only one it can access) and output channels of half w / 4
+    // epilogue of tile i: TMEM lane = pixel of the segment; warp w reads lane
+    // quadrant w % 4 (the only one it can access) and the output channels of
+    // half w / 4 (eight warps with cp.async staging, four otherwise)
+    auto epilogue = [&](int i, bool skip) {
         const int t = (int)blockIdx.x + i * G;
         const int seg = t % segs, row = t / segs;
         const int quad = warp & 3, half = warp >> 2;
@@ -958,7 +903,7 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
             const int c = half * (CO / P::NH) + cc;
             uint32_t r[16];
             tmem_ld16(acc + (uint32_t)c, r);
-            if (px < W && !failed) {
+            if (px < W && !skip) {
                 uint32_t packed[8];
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -976,20 +921,153 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
                 dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
             }
         }
-        tc_fence_before();
-        if (__syncthreads_or(failed)) {  // accumulator i & 1 is free for tile i+2 once all pass here
-            failed = true;
-            break;
+    };
+
+    bool failed = false;
+    if constexpr (P::CP_ASYNC) {
+        // two commit groups whatever nt is (an empty one when there is no
+        // tile 1), so that waiting for all but the newest one always means
+        // that tile 0 has landed
+        if (nt > 0) stage(0);
+        if (nt > 1) stage(1);
+        else cp_async_commit();
+        if (nt > 0) {
+            cp_async_wait<1>();
+            fence_proxy_async_smem();  // generic-proxy copies, read by the MMAs
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                mmas(0);
+            }
         }
-    }
-    cp_async_wait<0>();
-    if (failed) {
-        // let every load and MMA thread 0 issued finish (bounded) before the
-        // shared and tensor memory go away
-        if (tid == 0) {
+        for (int i = 0; i < nt; ++i) {
+            // the next tile's MMAs run while this tile's epilogue does
+            if (i + 1 < nt) {
+                cp_async_wait<0>();
+                fence_proxy_async_smem();
+                __syncthreads();
+                if (tid == 0 && !failed) {
+                    tc_fence_after();
+                    mmas(i + 1);
+                }
+            }
+            // tile i's MMAs are done: its accumulator is ready and its stage is free
+            if (!failed && !mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles)) failed = true;
+            tc_fence_after();
+            if (!failed && i + 2 < nt) stage(i + 2);
+            epilogue(i, failed);
+            tc_fence_before();
+            if (__syncthreads_or(failed)) {  // accumulator i & 1 is free for tile i+2 once all pass here
+                failed = true;
+                break;
+            }
+        }
+        cp_async_wait<0>();
+        if (failed && tid == 0) {
+            // let every MMA thread 0 issued finish (bounded) before the shared
+            // and tensor memory go away
+            if (n_mma > 0) mbar_wait_bounded(&mma_bar[(n_mma - 1) & 1], (uint32_t)((n_mma - 1) >> 1) & 1u, kTcWaitCycles);
+            if (err) atomicExch(err, DH_ETIMEOUT);
+        }
+    } else if constexpr (!P::WIDE) {
+        // 8-channel boxes, three CTAs per SM: thread 0 issues the loads and the
+        // MMAs; the next tile's MMAs go in right behind the current ones, then
+        // the stage the current tile's MMAs release is refilled
+        if (tid == 0 && nt > 0) {
+            for (int k = 0; k < P::NST && k < nt; ++k) issue(k);
+            if (landed(0)) {
+                tc_fence_after();
+                mmas(0);
+            } else {
+                failed = true;
+            }
+        }
+        for (int i = 0; i < nt; ++i) {
+            if (tid == 0 && !failed && i + 1 < nt) {
+                if (landed(i + 1)) {
+                    tc_fence_after();
+                    mmas(i + 1);
+                } else {
+                    failed = true;
+                }
+            }
+            if (!failed && !mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles)) failed = true;
+            tc_fence_after();
+            if (!failed && tid == 0 && i + P::NST < nt) issue(i + P::NST);
+            epilogue(i, failed);
+            tc_fence_before();
+            if (__syncthreads_or(failed)) {  // accumulator i & 1 is free for tile i+2 once all pass here
+                failed = true;
+                break;
+            }
+        }
+        if (failed && tid == 0) {
             for (int k = n_load_done; k < n_load; ++k)
                 mbar_wait_bounded(&tma_bar[k % P::NST], (uint32_t)(k / P::NST) & 1u, kTcWaitCycles);
             if (n_mma > 0) mbar_wait_bounded(&mma_bar[(n_mma - 1) & 1], (uint32_t)((n_mma - 1) >> 1) & 1u, kTcWaitCycles);
+            if (err) atomicExch(err, DH_ETIMEOUT);
+        }
+    } else {
+        // Warp roles: warps 0-3 run the epilogues, lane 0 of warp 4 the halo
+        // loads, lane 0 of warp 5 the MMAs, ordered by mbarriers alone (no
+        // block barrier in the loop):
+        //   tma_bar[s]    the halo of the tile in stage s has landed (TMA bytes)
+        //   stage_free[s] the MMAs that read stage s are done (tcgen05.commit)
+        //   mma_bar[a]    accumulator a holds its tile's sums (tcgen05.commit)
+        //   acc_free[a]   the four epilogue warps have read accumulator a
+        // Each barrier is waited for at most one phase behind its last use,
+        // so no wait can mistake an older phase for the one it wants.
+        if (warp == 4) {
+            if (lane == 0) {
+                for (int i = 0; i < nt && !s_fail; ++i) {
+                    const int st = i % P::NST;
+                    if (i >= P::NST &&
+                        !mbar_wait_bounded(&stage_free[st], (uint32_t)(i / P::NST - 1) & 1u, kTcWaitCycles)) {
+                        s_fail = 1;
+                        break;
+                    }
+                    issue(i);
+                }
+                s_issued = n_load;
+            }
+        } else if (warp == 5) {
+            if (lane == 0) {
+                for (int i = 0; i < nt && !s_fail; ++i) {
+                    const int st = i % P::NST, a = i & 1;
+                    if (!landed(i) ||
+                        (i >= 2 && !mbar_wait_bounded(&acc_free[a], (uint32_t)((i >> 1) - 1) & 1u, kTcWaitCycles))) {
+                        s_fail = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    mmas(i);                  // commits to mma_bar[a]
+                    tc_commit(&stage_free[st]);  // the same MMAs free the halo stage
+                }
+                s_landed = n_load_done;
+                s_mmas = n_mma;
+            }
+        } else {
+            for (int i = 0; i < nt; ++i) {
+                const bool ok = mbar_wait_bounded(&mma_bar[i & 1], (uint32_t)(i >> 1) & 1u, kTcWaitCycles);
+                if (__any_sync(0xffffffffu, !ok)) {
+                    if (lane == 0) s_fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                epilogue(i, false);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_free[i & 1]);
+            }
+        }
+        __syncthreads();
+        failed = s_fail != 0;
+        if (failed && tid == 0) {
+            // let every load and MMA issued finish (bounded) before the shared
+            // and tensor memory go away
+            for (int k = s_landed; k < s_issued; ++k)
+                mbar_wait_bounded(&tma_bar[k % P::NST], (uint32_t)(k / P::NST) & 1u, kTcWaitCycles);
+            if (s_mmas > 0) mbar_wait_bounded(&mma_bar[(s_mmas - 1) & 1], (uint32_t)((s_mmas - 1) >> 1) & 1u, kTcWaitCycles);
             if (err) atomicExch(err, DH_ETIMEOUT);
         }
     }
