@@ -297,10 +297,14 @@ int dh_dehaze_warm(const float *params, int base, const float *I, int H, int W, 
  * images in one graph while loop, each to its own residual; p->storage may be
  * any DH_STORE_* (the 16-bit phase of a switched form starts from the
  * network's u0 rounded to 16 bits).  imgs[i].u0 must be NULL; every image's
- * H and W are multiples of 8.  workspace: dh_batch_workspace_bytes(n, imgs, p);
- * net_workspace: dh_batch_net_workspace_bytes(base, n, imgs) (one forward at a
- * time, reused image after image), both 256-byte aligned.  The paper only
- * points at hybrids of the PDE with learned models (Sec. I and V). */
+ * H and W are multiples of 8.  Images of one shape go through the network
+ * together, in groups of up to about 4.2 million pixels (at most 64 images);
+ * each image's u0 equals that of its own single-image forward.
+ * workspace: dh_batch_workspace_bytes(n, imgs, p); net_workspace:
+ * dh_batch_net_workspace_bytes(base, n, imgs) (the largest group's gathered
+ * inputs and network workspace, reused group after group), both 256-byte
+ * aligned.  The paper only points at hybrids of the PDE with learned models
+ * (Sec. I and V). */
 size_t dh_batch_net_workspace_bytes(int base, int n, const dh_image *imgs);
 int dh_dehaze_batch_warm(const float *params, int base, int n, const dh_image *imgs, const dh_params *p,
                          void *workspace, size_t workspace_bytes, void *net_workspace, size_t net_workspace_bytes,

@@ -23,19 +23,43 @@ int encode_f32_map(CUtensorMap *m, const void *base, int rank, int W, int H, int
 int encode_tiled(CUtensorMap *m, CUtensorMapDataType dt, int rank, const void *base, const cuuint64_t *dims,
                  const cuuint64_t *strides, const cuuint32_t *box);
 int sweep_tile_h(int depth);
-size_t warm_net_bytes(int base, int H, int W);
-int warm_u0(const float *params, int base, const float *I, const float *t, const float *A, const float *phi,
-            const float *lam, int H, int W, void *nws, size_t nws_bytes, float *u0, cudaStream_t s);
+int warm_group_size(int H, int W);
+size_t warm_net_bytes(int base, int n, int H, int W);
+int warm_u0_group(const float *params, int base, int n, const float *const *I, const float *const *t,
+                  const float *const *A, const float *const *phi, const float *const *lam, float *const *u0, int H,
+                  int W, void *nws, size_t nws_bytes, cudaStream_t s);
 
-// The warm-start network of dh_dehaze_batch_warm and the workspace of one forward.
+// The warm-start network of dh_dehaze_batch_warm and the workspace of its forwards.
 struct WarmNet {
     const float *params;
     int base;
     void *ws;
     size_t ws_bytes;
 };
-constexpr int kWarmLaunches = 37;  // weight packing (14), input packing, 14 convolutions, 3 pools, 3 upsamplings,
-                                   // head, u0 = y / lambda
+constexpr int kWarmForwardLaunches = 36;  // weight packing (14), input packing, 14 convolutions, 3 pools,
+                                          // 3 upsamplings, head; plus u0 = y / lambda per image
+
+// Same-shape images of a batch in order of first appearance, cut into groups
+// of at most warm_group_size(H, W) images: one network forward per group.
+static std::vector<std::vector<int>> warm_groups(int n, const dh_image *imgs) {
+    std::vector<std::vector<int>> shapes, out;
+    for (int i = 0; i < n; ++i) {
+        bool placed = false;
+        for (auto &g : shapes)
+            if (imgs[g[0]].H == imgs[i].H && imgs[g[0]].W == imgs[i].W) {
+                g.push_back(i);
+                placed = true;
+                break;
+            }
+        if (!placed) shapes.push_back({i});
+    }
+    for (auto &g : shapes) {
+        const int cap = warm_group_size(imgs[g[0]].H, imgs[g[0]].W);
+        for (size_t k = 0; k < g.size(); k += cap)
+            out.emplace_back(g.begin() + k, g.begin() + (k + cap < g.size() ? k + cap : g.size()));
+    }
+    return out;
+}
 
 constexpr int kMaxBatch = 256;
 constexpr int kBR = 6, kBNW = 4, kBTH = kBR * kBNW;  // 128 x 24 tiles, 4 warps, 5 CTAs per SM
@@ -591,11 +615,7 @@ static int batch_run(int n, const dh_image *imgs, const dh_params *p, void *work
                                           (m.u0 || warm) ? nullptr : m.u, (float2 *)(iw + L.phin_part),
                                           iw + L.refine, s);
         if (rc) return rc;
-        if (warm) {  // u0 = net(I, t, A, Phi) / lambda, into u (the network's workspace is reused per image)
-            rc = warm_u0(warm->params, warm->base, m.I, m.t, m.A, phi, lam, m.H, m.W, warm->ws, warm->ws_bytes, m.u,
-                         s);
-            if (rc) return rc;
-        } else if (m.u0) {
+        if (m.u0) {
             DH_CUDA_TRY(cudaMemcpyAsync(m.u, m.u0, (size_t)3 * m.H * m.W * sizeof(float), cudaMemcpyDeviceToDevice, s));
         }
         rc = launch_phin_final((const float2 *)(iw + L.phin_part), m.H, m.W, (SolveState *)(iw + L.state), s);
@@ -628,12 +648,39 @@ static int batch_run(int n, const dh_image *imgs, const dh_params *p, void *work
         d.phase_stop = switched ? 1 : 0;
         const int rc2 = set_iterates(r, i, kind1);
         if (rc2) return rc2;
-        if (kind1) {  // u0 (float32 in m.u) into the first 16-bit buffer
-            const size_t n3 = (size_t)3 * m.H * m.W;
+    }
+    // warm start: u0 = net(I, t, A, Phi) / lambda into each image's u, one network
+    // forward per group of same-shape images (the network's workspace is reused
+    // group after group)
+    int warm_launches = 0;
+    if (warm) {
+        for (const auto &g : warm_groups(n, imgs)) {
+            const int cnt = (int)g.size();
+            std::vector<const float *> I(cnt), t(cnt), A(cnt), phi(cnt), lam(cnt);
+            std::vector<float *> u0(cnt);
+            for (int k = 0; k < cnt; ++k) {
+                const dh_image &m = imgs[g[k]];
+                I[k] = m.I;
+                t[k] = m.t;
+                A[k] = m.A;
+                phi[k] = recs[g[k]].d.phi;
+                lam[k] = recs[g[k]].d.lam;
+                u0[k] = m.u;
+            }
+            const int rc = warm_u0_group(warm->params, warm->base, cnt, I.data(), t.data(), A.data(), phi.data(),
+                                         lam.data(), u0.data(), imgs[g[0]].H, imgs[g[0]].W, warm->ws, warm->ws_bytes,
+                                         s);
+            if (rc) return rc;
+            warm_launches += kWarmForwardLaunches + cnt;
+        }
+    }
+    if (kind1) {  // u0 (float32 in u) into each image's first 16-bit buffer
+        for (int i = 0; i < n; ++i) {
+            const size_t n3 = (size_t)3 * imgs[i].H * imgs[i].W;
             if (kind1 == 1)
-                k_b_to16<__nv_bfloat16><<<grid_for_n(n3), 256, 0, s>>>(m.u, (__nv_bfloat16 *)d.u[0], n3);
+                k_b_to16<__nv_bfloat16><<<grid_for_n(n3), 256, 0, s>>>(imgs[i].u, (__nv_bfloat16 *)recs[i].d.u[0], n3);
             else
-                k_b_to16<__half><<<grid_for_n(n3), 256, 0, s>>>(m.u, (__half *)d.u[0], n3);
+                k_b_to16<__half><<<grid_for_n(n3), 256, 0, s>>>(imgs[i].u, (__half *)recs[i].d.u[0], n3);
         }
     }
     BImg *dimgs = (BImg *)(ws + B.imgs);
@@ -733,12 +780,12 @@ static int batch_run(int n, const dh_image *imgs, const dh_params *p, void *work
         DH_CUDA_TRY(cudaMemcpy(r.A, imgs[i].A, 3 * sizeof(float), cudaMemcpyDeviceToHost));
         r.a_index = sel.best;
         r.ms = ms;  // the whole batch
-        r.launches = 18 + 1 + (warm ? kWarmLaunches : 0);  // front end (+ network) + output of this image
+        r.launches = 18 + 1;  // front end + output of this image
         if (st.n_final > max_n) max_n = st.n_final;
         if (r.status < 0 && worst >= 0) worst = r.status;
         else if (worst == DH_OK && r.status > 0) worst = r.status;
     }
-    reports[0].launches += (p->use_graph ? max_n + 1 : launches) + 1 + (n + kPutChunk - 1) / kPutChunk;
+    reports[0].launches += (p->use_graph ? max_n + 1 : launches) + 1 + (n + kPutChunk - 1) / kPutChunk + warm_launches;
     return worst;
 }
 
@@ -749,9 +796,11 @@ int dh_dehaze_batch(int n, const dh_image *imgs, const dh_params *p, void *works
 
 size_t dh_batch_net_workspace_bytes(int base, int n, const dh_image *imgs) {
     if (n < 1 || n > kMaxBatch || !imgs) return 0;
+    for (int i = 0; i < n; ++i)
+        if (!shape_ok(imgs[i].H, imgs[i].W)) return 0;
     size_t most = 0;
-    for (int i = 0; i < n; ++i) {
-        const size_t b = warm_net_bytes(base, imgs[i].H, imgs[i].W);
+    for (const auto &g : warm_groups(n, imgs)) {
+        const size_t b = warm_net_bytes(base, (int)g.size(), imgs[g[0]].H, imgs[g[0]].W);
         if (b == 0) return 0;
         if (b > most) most = b;
     }
@@ -763,7 +812,8 @@ int dh_dehaze_batch_warm(const float *params, int base, int n, const dh_image *i
                          void *stream, dh_report *reports) {
     if (!params || n < 1 || n > kMaxBatch || !imgs) return DH_EINVAL;
     for (int i = 0; i < n; ++i)
-        if (imgs[i].u0 || warm_net_bytes(base, imgs[i].H, imgs[i].W) == 0) return DH_EINVAL;
+        if (imgs[i].u0 || !shape_ok(imgs[i].H, imgs[i].W) || warm_net_bytes(base, 1, imgs[i].H, imgs[i].W) == 0)
+            return DH_EINVAL;
     const size_t need = dh_batch_net_workspace_bytes(base, n, imgs);
     if (!net_workspace || ((uintptr_t)net_workspace % kAlign) || net_workspace_bytes < need) return DH_EWORKSPACE;
     const WarmNet w{params, base, net_workspace, net_workspace_bytes};

@@ -869,24 +869,75 @@ static int net_backward(const float *params, int b, const float *target, int N, 
 
 #undef BF
 
-// Workspace one network forward over a single HxW image needs (0: shape
-// the network does not take).
-size_t warm_net_bytes(int base, int H, int W) {
-    if (!unet_shape_ok(base, 1, H, W)) return 0;
-    return net_layout(base, 1, H, W, false).total;
+// Warm start of a batched solve: images of one shape go through the network
+// together, up to kWarmGroupPixels pixels per forward (small images leave most
+// SMs idle in the deep levels when run one at a time).
+constexpr long long kWarmGroupPixels = 4200000;
+
+int warm_group_size(int H, int W) {
+    const long long n = kWarmGroupPixels / ((long long)H * W);
+    return n < 1 ? 1 : (n > 64 ? 64 : (int)n);
 }
 
-// u0 = net(I, t, A, Phi) / lambda for one image, queued on s: the warm start of
-// the batched solve.  nws: warm_net_bytes(base, H, W) bytes, 256-byte aligned.
-int warm_u0(const float *params, int base, const float *I, const float *t, const float *A, const float *phi,
-            const float *lam, int H, int W, void *nws, size_t nws_bytes, float *u0, cudaStream_t s) {
-    if (!unet_shape_ok(base, 1, H, W)) return DH_EINVAL;
-    const NetLayout NL = net_layout(base, 1, H, W, false);
-    if (!nws || ((uintptr_t)nws % kAlign) || nws_bytes < NL.total) return DH_EWORKSPACE;
+// Workspace of one grouped forward over n images of HxW: the gathered inputs
+// (I and Phi 3HW floats, t HW floats, A 3 floats per image; none for n = 1)
+// followed by the network's own workspace.  0: a shape the network does not take.
+struct WarmGather {
+    size_t I, Phi, t, A, net;
+};
+static WarmGather warm_gather(int n, int H, int W) {
+    const size_t HW = (size_t)H * W;
+    WarmGather g{};
+    size_t o = 0;
+    if (n > 1) {
+        g.I = o; o = align_up(o + (size_t)n * 3 * HW * sizeof(float));
+        g.Phi = o; o = align_up(o + (size_t)n * 3 * HW * sizeof(float));
+        g.t = o; o = align_up(o + (size_t)n * HW * sizeof(float));
+        g.A = o; o = align_up(o + (size_t)n * 3 * sizeof(float));
+    }
+    g.net = o;
+    return g;
+}
+
+size_t warm_net_bytes(int base, int n, int H, int W) {
+    if (n < 1 || !unet_shape_ok(base, n, H, W)) return 0;
+    return warm_gather(n, H, W).net + net_layout(base, n, H, W, false).total;
+}
+
+// u0[k] = net(I[k], t[k], A[k], Phi[k]) / lam[k] for n images of one shape in
+// one forward, queued on s.  nws: warm_net_bytes(base, n, H, W) bytes, 256-byte
+// aligned.  Every image's result equals its own single-image forward (the
+// kernels work per pixel, per row segment or per image).
+int warm_u0_group(const float *params, int base, int n, const float *const *I, const float *const *t,
+                  const float *const *A, const float *const *phi, const float *const *lam, float *const *u0, int H,
+                  int W, void *nws, size_t nws_bytes, cudaStream_t s) {
+    if (n < 1 || !unet_shape_ok(base, n, H, W)) return DH_EINVAL;
+    const WarmGather g = warm_gather(n, H, W);
+    const NetLayout NL = net_layout(base, n, H, W, false);
+    if (!nws || ((uintptr_t)nws % kAlign) || nws_bytes < g.net + NL.total) return DH_EWORKSPACE;
     char *ws = (char *)nws;
-    RUN(net_forward(params, base, I, t, A, phi, 1, H, W, ws, NL, false, s));
-    k_warm_start<<<gs((size_t)3 * H * W), 256, 0, s>>>(reinterpret_cast<const float *>(ws + NL.y), lam,
-                                                      (size_t)H * W, u0);
+    const size_t HW = (size_t)H * W;
+    const float *gI = I[0], *gPhi = phi[0], *gt = t[0], *gA = A[0];
+    if (n > 1) {  // gather the group's inputs into contiguous N x ... arrays
+        float *dI = reinterpret_cast<float *>(ws + g.I), *dPhi = reinterpret_cast<float *>(ws + g.Phi);
+        float *dt = reinterpret_cast<float *>(ws + g.t), *dA = reinterpret_cast<float *>(ws + g.A);
+        for (int k = 0; k < n; ++k) {
+            DH_CUDA_TRY(cudaMemcpyAsync(dI + (size_t)k * 3 * HW, I[k], 3 * HW * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            DH_CUDA_TRY(cudaMemcpyAsync(dPhi + (size_t)k * 3 * HW, phi[k], 3 * HW * sizeof(float),
+                                        cudaMemcpyDeviceToDevice, s));
+            DH_CUDA_TRY(cudaMemcpyAsync(dt + (size_t)k * HW, t[k], HW * sizeof(float), cudaMemcpyDeviceToDevice, s));
+            DH_CUDA_TRY(cudaMemcpyAsync(dA + 3 * k, A[k], 3 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+        }
+        gI = dI;
+        gPhi = dPhi;
+        gt = dt;
+        gA = dA;
+    }
+    char *nw = ws + g.net;
+    RUN(net_forward(params, base, gI, gt, gA, gPhi, n, H, W, nw, NL, false, s));
+    const float *y = reinterpret_cast<const float *>(nw + NL.y);
+    for (int k = 0; k < n; ++k)
+        k_warm_start<<<gs(3 * HW), 256, 0, s>>>(y + (size_t)k * 3 * HW, lam[k], HW, u0[k]);
     DH_CUDA_TRY(cudaGetLastError());
     return DH_OK;
 }

@@ -99,6 +99,40 @@ def test_invalid_arguments_rejected_on_host():
     assert N.dh_tune_set(8, 8, 0, 999) == N.DH_EINVAL
 
 
+def test_batch_net_workspace_groups_by_shape():
+    """dh_dehaze_batch_warm runs one network forward per group of same-shape
+    images (up to about 4.2 million pixels a group): its workspace is the
+    largest group's gathered inputs (I and Phi 3HW, t HW floats, A 3 floats per
+    image, none for a group of one) plus that group's network workspace."""
+    fake = 1 << 20
+
+    def img(H, W):
+        return N.dh_image(fake, H, W, None, fake, fake, fake, fake)
+
+    def gathered(n, H, W):
+        al = lambda b: (b + 255) // 256 * 256
+        return 2 * al(n * 3 * H * W * 4) + al(n * H * W * 4) + al(n * 12) if n > 1 else 0
+
+    def net(n, H, W):
+        return N.dh_unet_workspace_bytes(32, n, H, W, 0)
+
+    a, b = (64, 128), (56, 96)
+    assert N.dh_batch_net_workspace_bytes(32, 1, [img(*a)]) == net(1, *a)
+    assert N.dh_batch_net_workspace_bytes(32, 2, [img(*a), img(*b)]) == max(net(1, *a), net(1, *b))
+    assert N.dh_batch_net_workspace_bytes(32, 5, [img(*a), img(*b), img(*a), img(*b), img(*a)]) == max(
+        gathered(3, *a) + net(3, *a), gathered(2, *b) + net(2, *b))
+    # 1080p: two images a group, so a third image adds nothing
+    hd = (1080, 1920)
+    two = N.dh_batch_net_workspace_bytes(32, 2, [img(*hd)] * 2)
+    assert two == gathered(2, *hd) + net(2, *hd)
+    assert N.dh_batch_net_workspace_bytes(32, 3, [img(*hd)] * 3) == two
+    # 64 images a group at most
+    tiny = (16, 16)
+    assert N.dh_batch_net_workspace_bytes(32, 70, [img(*tiny)] * 70) == gathered(64, *tiny) + net(64, *tiny)
+    assert N.dh_batch_net_workspace_bytes(32, 1, [img(60, 100)]) == 0  # sides not multiples of 8
+    assert N.dh_batch_net_workspace_bytes(24, 1, [img(*a)]) == 0  # no such network
+
+
 def test_semi_implicit_arguments_rejected_on_host():
     p = N.dh_params_default(N.DH_PRESET_PAPER)
     fake = 1 << 20  # never dereferenced

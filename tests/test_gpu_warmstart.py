@@ -85,6 +85,28 @@ def test_warm_batch_matches_single_image_warm_start(trained):
         assert torch.equal(torch.clamp(o["u"], 0, 1), o["J"])
 
 
+def test_warm_batch_groups_of_one_shape(trained):
+    """Images of one shape share a network forward (1080p: two a forward, so
+    three 1080p images make a group of two and one of one; three 64x128
+    images interleaved with other shapes make one group of three).  Every
+    image still ends where its single-image warm solve ends."""
+    from paper_2506_08793_gb300 import api
+
+    WS, net, _ = trained
+    shapes = [(1080, 1920), (64, 128), (1080, 1920), (56, 96), (64, 128), (1080, 1920), (64, 128)]
+    imgs = [torch.from_numpy(scenes.hazy_scene(6_500_000 + k, H, W)["I"]).cuda() for k, (H, W) in enumerate(shapes)]
+    b = api.BatchDehazer(shapes, api.params("stable"), net=net)
+    reps = b(imgs)
+    for k, ((H, W), I, r, o) in enumerate(zip(shapes, imgs, reps, b.out)):
+        wd = WS.WarmDehazer(net, H, W)
+        one = wd(I)
+        assert r.status == 0 and max(r.rho) <= 1e-4, k
+        assert abs(r.n_iter - one.n_iter) <= 1, (k, r.n_iter, one.n_iter)
+        if r.n_iter == one.n_iter:
+            assert torch.allclose(o["u"], wd.dz.u, rtol=1e-6, atol=1e-6), k
+        del wd
+
+
 @pytest.mark.parametrize("storage", [0, 3, 4])  # DH_STORE_F32, DH_STORE_BF16_F32, DH_STORE_F16_F32
 def test_warm_batch_reaches_tolerance_with_cold_accuracy(trained, orc, storage):
     """The warm-started batched form (network u0, then the batched loop in
