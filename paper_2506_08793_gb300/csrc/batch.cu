@@ -209,7 +209,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
     using P = TmaPlan<kBTH, true, T>;
     constexpr int SW = P::SW, SH = P::SH, HALO = Store<T>::HALO;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *sb = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sb = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t bar;
     __shared__ float2 red[kBNW];
     __shared__ int s_last, s_img_last;

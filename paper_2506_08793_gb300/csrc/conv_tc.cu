@@ -119,7 +119,7 @@ k_conv3x3_tc(const bf16 *__restrict__ x, int ldx, int C, int Nimg, int H, int W,
     using P = TcPlan<NT>;
     constexpr int S = P::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t mma_bar[S];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_slot;
@@ -256,7 +256,7 @@ k_conv3x3_tma(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ C
     using P = TcPlan<NT>;
     constexpr int S = P::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t full[S], empty[S], done_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail, s_issued, s_consumed;
@@ -488,7 +488,7 @@ k_wgrad_tc(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ CUte
     using P = WgPlan<NT>;
     constexpr int S = P::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t full[S], empty[S], done_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_fail, s_issued, s_consumed;
@@ -759,7 +759,7 @@ k_conv3x3_halo(const __grid_constant__ CUtensorMap tmx, const __grid_constant__ 
     using P = HaloPlan<C, CO>;
     constexpr int QC = P::QC;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t tma_bar[P::NST], mma_bar[2], stage_free[P::NST], acc_free[2];
     __shared__ uint32_t tmem_slot;
     __shared__ float s_bias[CO];

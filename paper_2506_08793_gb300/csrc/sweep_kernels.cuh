@@ -122,7 +122,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     constexpr int SW = P::SW, SH = P::SH;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned base (the launch adds 1 KiB of slack)
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t bar[STAGES];
     __shared__ float2 red[NW];
     __shared__ int s_last, s_timeout;
@@ -437,7 +437,7 @@ k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     using P = Tb2Plan<R2, NW>;
     constexpr int TH = P::TH, R1 = P::R1, SW = P::SW;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t bar;
     __shared__ float2 red[2][NW];
     __shared__ int s_last, s_timeout;
@@ -660,7 +660,7 @@ k_sweep_stream(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant_
                const SolveDesc *__restrict__ d, int seg) {
     static_assert(NSLOT >= 4 && (NSLOT & (NSLOT - 1)) == 0, "NSLOT: power of two >= 4");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t bars[NW][NSLOT];
     __shared__ int s_last;
 
@@ -1050,7 +1050,7 @@ k_sweep_tbk(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     using P = TbkPlan<K, RO, NW>;
     constexpr int TH = P::TH, WO = P::WO, SW = P::SW;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t bar;
     __shared__ float2 red[K][NW];
     __shared__ int s_last, s_timeout;
@@ -1273,7 +1273,7 @@ k_sweep_ws(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CU
     using P = TmaPlan<TH, PL_SMEM, T>;
     constexpr int SW = P::SW, SH = P::SH;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
     __shared__ float2 slot[STAGES][NW];
     __shared__ int s_last, s_timeout;

@@ -13,6 +13,16 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// The dynamic shared buffer `raw` advanced to the next 1024-byte boundary.
+// The result is `raw` plus an offset, so the compiler still knows that it
+// points into shared memory and accesses through it stay shared-memory
+// loads and stores (rounding the address through an integer would leave only
+// a generic pointer).
+__device__ __forceinline__ unsigned char *smem_align1024(unsigned char *raw) {
+    const uint32_t a = smem_addr(raw);
+    return raw + (((a + 1023u) & ~1023u) - a);
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
