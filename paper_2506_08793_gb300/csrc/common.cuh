@@ -47,6 +47,10 @@ struct SolveState {
     unsigned gen;
     unsigned launches;  // sweep launches since the last reset (counted by CTA 0 of each)
     int pad_gen[30];
+    // Item counters of the multi-iteration sweep (iteration n uses work[n & 1]),
+    // in their own line: every CTA takes its items from them.
+    unsigned work[2];
+    int pad_work[30];
 };
 
 // status a 16-bit phase ends with when its residual stalls (internal)

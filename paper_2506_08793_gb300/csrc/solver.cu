@@ -23,6 +23,7 @@ __global__ void k_set_desc(SolveDesc *dst, SolveDesc v, int reset) {
     *dst = v;
     SolveState *st = v.st;
     st->depth = v.depth;
+    st->work[0] = st->work[1] = 0u;
     if (!reset) return;
     st->arrive = 0;
     st->n = 0;

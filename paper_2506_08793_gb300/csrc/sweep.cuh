@@ -48,14 +48,32 @@ __device__ __forceinline__ int ld_state_int(const int *p) { return __ldcg(p); }
 
 // Reduces the per-tile partials of the launch (last CTA only), decides whether
 // to stop, advances the state and sets the graph's while condition.  Every
-// thread of the CTA keeps 8 partial loads per channel in flight; the sums are
-// merged in a fixed order (thread stride, then lanes, then warps).
-static __device__ void finish_iteration(const SolveDesc *d, SolveState *st) {
-    constexpr int U = 8;
+// thread of the CTA keeps U partial loads per channel in flight; the sums are
+// merged in a fixed order (thread stride, then lanes, then warps).  Thread 0
+// loads the state fields it decides with before the partials, so that their
+// latency overlaps the reduction; it returns the index of the next iterate
+// (n + 1 when the loop goes on, n when it stops; other threads: unspecified).
+// A multi-iteration launch sets the while condition only at its last
+// iteration (last_in_launch); a caller whose arrival was an acquire-release
+// atomic skips the opening fence (acquired), and one that publishes the state
+// with a release store itself skips the closing fence (fence = false).
+template <int U = 8>  // partial loads per channel in flight per thread
+static __device__ int finish_iteration(const SolveDesc *d, SolveState *st, bool last_in_launch = true,
+                                       bool fence = true, bool acquired = false) {
     __shared__ float2 wsum[3][32];
     __shared__ float sq[3];
     const int tid = threadIdx.x, nt = blockDim.x, w = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    __threadfence();
+    if (!acquired) fence_acq_rel_gpu();  // the partials of every CTA that arrived before this one
+    int n = 0, cur = 0, err = 0, max_iter = 0;
+    float phin2[3] = {0.f, 0.f, 0.f}, tol = 0.f;
+    if (tid == 0) {
+        n = ld_state_int(&st->n);
+        cur = ld_state_int(&st->cur);
+        err = ld_state_int(&st->err);
+        for (int c = 0; c < 3; ++c) phin2[c] = __ldcg(&st->phin2[c]);
+        tol = d->tol;
+        max_iter = d->max_iter;
+    }
     const int nblk = d->nblk;
     const float2 *part = d->part;
     float s[3] = {0.f, 0.f, 0.f}, cc[3] = {0.f, 0.f, 0.f};
@@ -89,44 +107,48 @@ static __device__ void finish_iteration(const SolveDesc *d, SolveState *st) {
         sq[tid] = a + b;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    const int n = st->n;
+    if (tid != 0) return 0;
+    float *rho_hist = d->rho_hist;
     float worst = 0.f;
     bool finite = true;
     float rho[3];
     for (int c = 0; c < 3; ++c) {
-        const float pn = st->phin2[c];
+        const float pn = phin2[c];
         rho[c] = pn > 0.f ? sqrtf(sq[c] / pn) : sqrtf(sq[c]);
         if (!isfinite(rho[c])) finite = false;
         else worst = fmaxf(worst, rho[c]);
-        if (d->rho_hist) d->rho_hist[3 * n + c] = rho[c];
+        if (rho_hist) rho_hist[3 * n + c] = rho[c];
     }
-    const int err = __ldcg(&st->err);
-    const bool conv = finite && worst <= d->tol;
+    const bool conv = finite && worst <= tol;
     // a 16-bit phase ends once its residual falls by less than 2 % over
     // kStallWindow iterations (the storage quantum has been reached)
     bool stall = false;
     if (d->phase_stop && finite) {
         const int slot = n % kStallWindow;
-        if (n - st->phase_start >= kStallWindow && worst > 0.98f * st->rmax[slot]) stall = true;
+        if (n - ld_state_int(&st->phase_start) >= kStallWindow && worst > 0.98f * __ldcg(&st->rmax[slot])) stall = true;
         st->rmax[slot] = worst;
     }
     unsigned cont = 1;
-    if (err || conv || !finite || n >= d->max_iter || stall) {
+    int next = n + 1;
+    if (err || conv || !finite || n >= max_iter || stall) {
         st->done = 1;
         st->n_final = n;
         st->status = err ? err
                          : (!finite ? DH_ENONFINITE
-                                    : (conv ? DH_OK : (n >= d->max_iter ? DH_WNOCONV : kStatusSwitch)));
+                                    : (conv ? DH_OK : (n >= max_iter ? DH_WNOCONV : kStatusSwitch)));
         for (int c = 0; c < 3; ++c) st->rho[c] = rho[c];
         cont = 0;
+        next = n;
     } else {
         st->n = n + 1;
-        st->cur ^= 1;
+        st->cur = cur ^ 1;
     }
     st->arrive = 0;
-    __threadfence();
-    if (d->use_cond) cudaGraphSetConditional(d->cond, cont);
+    if (fence) __threadfence();
+    // the condition was cleared when the launch began: only a launch that goes
+    // on after its last iteration sets it
+    if (d->use_cond && cont && last_in_launch) cudaGraphSetConditional(d->cond, 1u);
+    return next;
 }
 
 // The loop ends unless a launch's last CTA sets the condition back to 1, so a

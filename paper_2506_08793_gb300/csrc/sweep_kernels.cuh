@@ -125,7 +125,8 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t bar[STAGES];
     __shared__ float2 red[NW];
-    __shared__ int s_last, s_timeout;
+    __shared__ int s_last, s_timeout, s_next;
+    constexpr bool DYN = MULTI && STAGES == 1;  // items from a grid-wide counter
 
     SolveState *st = d->st;
     clear_condition(d);
@@ -137,7 +138,6 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     const int ntx = (W + kTW - 1) / kTW, nty = (H + TH - 1) / TH;
     const int ntiles = ntx * nty, nitems = 3 * ntiles;
     const int G = gridDim.x;
-    const int m = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;  // items of this CTA
 
     if (threadIdx.x == 0) {
         for (int k = 0; k < STAGES; ++k) mbar_init(&bar[k], 1);
@@ -157,10 +157,12 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     bool failed = false;
     for (int it = 0; it < iters; ++it) {
         const int cur = __ldcg(&st->cur);
-        const bool rev = (__ldcg(&st->n) & 1) != 0;
+        const int n_it = __ldcg(&st->n);
+        const bool rev = (n_it & 1) != 0;
         const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
         T *__restrict__ ubase = static_cast<T *>(d->u[cur ^ 1]);
-        auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
+        // position q in the iteration's walk order -> item (odd iterations walk backwards)
+        auto item_of = [&](int q) { return rev ? nitems - 1 - q : q; };
         auto tile_xy = [&](int item, int &c, int &x0, int &y0) {
             const int tile = item / 3;
             c = item - 3 * tile;
@@ -168,9 +170,9 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             y0 = (tile / ntx) * TH;
             return tile;
         };
-        auto issue = [&](int j, int stage) {
+        auto issue = [&](int q, int stage) {
             int c, x0, y0;
-            tile_xy(item_at(j), c, x0, y0);
+            tile_xy(item_of(q), c, x0, y0);
             unsigned char *sb = smem + stage * P::STAGE;
             mbar_arrive_expect_tx(&bar[stage], P::TX);
             tma_load_3d(sb + P::U_OFF, tm_u, &bar[stage], x0 - HALO, y0 - 2, c);
@@ -179,30 +181,44 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
                 tma_load_2d(sb + P::LAM_OFF, &tm_lam, &bar[stage], x0, y0);
             }
         };
-        auto prefetch = [&](int j) {
+        auto prefetch = [&](int q) {
             int c, x0, y0;
-            tile_xy(item_at(j), c, x0, y0);
+            tile_xy(item_of(q), c, x0, y0);
             tma_prefetch_3d(tm_u, x0 - HALO, y0 - 2, c);
-            if (PL_SMEM) {
-                tma_prefetch_3d(&tm_phi, x0, y0, c);
-                tma_prefetch_2d(&tm_lam, x0, y0);
-            }
+            tma_prefetch_3d(&tm_phi, x0, y0, c);
+            tma_prefetch_2d(&tm_lam, x0, y0);
         };
+        // Walk positions of this CTA: blockIdx.x, blockIdx.x + G, and then
+        // (DYN) 2G + the values of a counter the grid shares for this
+        // iteration, so that CTAs that run faster take more items and all
+        // reach the grid barrier at about the same time; otherwise
+        // blockIdx.x + jG.  Thread 0 takes the position two items ahead
+        // while the current one is walked and publishes the next one in
+        // s_next before the walk's closing barrier.
+        unsigned *ctr = &st->work[n_it & 1];
+        int q = (int)blockIdx.x;  // current position (every thread)
+        int qn = q + G;           // next position (thread 0)
+        int j = 0;                // items of this CTA in this iteration
         if (threadIdx.x == 0) {
             if (MULTI && it > 0) fence_proxy_async_global();
-            for (int j = 0; j < STAGES && j < m; ++j) issue(j, (k + j) % STAGES);
+            for (int jj = 0; jj < STAGES && q + jj * G < nitems; ++jj) issue(q + jj * G, (k + jj) % STAGES);
         }
-        int j = 0;
-        for (; j < m; ++j, ++k) {
+        for (; q < nitems; ++j, ++k) {
             const int stage = k % STAGES;
             const uint32_t parity = (k / STAGES) & 1;
             int c, x0, y0;
-            const int tile = tile_xy(item_at(j), c, x0, y0);
+            const int tile = tile_xy(item_of(q), c, x0, y0);
             unsigned char *sb = smem + stage * P::STAGE;
             T *s = reinterpret_cast<T *>(sb + P::U_OFF);
             const float *sphi = reinterpret_cast<const float *>(sb + P::PHI_OFF);
             const float *slam = reinterpret_cast<const float *>(sb + P::LAM_OFF);
-            if (threadIdx.x == 0 && j + STAGES < m) prefetch(j + STAGES);
+            if (threadIdx.x == 0) {
+                if (DYN) {
+                    if (qn < nitems) prefetch(qn);
+                } else if (q + STAGES * G < nitems) {
+                    prefetch(q + STAGES * G);
+                }
+            }
 
             const bool ok = mbar_wait_bounded(&bar[stage], parity, kWaitLimitCycles);
             if (__syncthreads_or(!ok)) {
@@ -217,6 +233,11 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
                 fence_proxy_async_smem();  // these writes precede the stage's next TMA load
                 __syncthreads();
             }
+
+            // (DYN, thread 0) the position after the next one, taken here so that
+            // no block barrier waits for the atomic before the walk's closing one
+            int qa = nitems;
+            if (DYN && threadIdx.x == 0 && qn < nitems) qa = 2 * G + (int)atomicAdd(ctr, 1u);
 
             T *__restrict__ un = ubase + c * N;
             const int x = x0 + 4 * lane;
@@ -241,50 +262,58 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             auto sink = [&](int ty, const float *nu, const float *F) {
                 const int y = y0 + ty;
                 if (y >= H || x >= W) return;  // W % 4 == 0: x < W covers all 4 columns
-                float q = 0.f;
+                float q2 = 0.f;
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) q = fmaf(F[jj], F[jj], q);
-                neumaier_add(rs, rc, q);
+                for (int jj = 0; jj < 4; ++jj) q2 = fmaf(F[jj], F[jj], q2);
+                neumaier_add(rs, rc, q2);
                 Store<T>::write4(un + (size_t)y * W + x, nu[0], nu[1], nu[2], nu[3]);
             };
             walk_rows<R, SW, T, EDGE>(s, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
 
             // every thread is past its walk once block_pair_sum's barrier is
-            // passed, so the stage can be refilled; red[] is rewritten only after
-            // the next item's wait barrier, which every reader of it reaches first
+            // passed, so the stage can be refilled; red[] and s_next are
+            // rewritten only after the next item's wait barrier, which every
+            // reader of them reaches first
+            if (DYN && threadIdx.x == 0) s_next = qn;
             const float2 tot = block_pair_sum<NW>(rs, rc, red);
+            const int qnext = DYN ? s_next : q + G;
             if (threadIdx.x == 0) {
                 part[(size_t)c * nblk + tile] = tot;
-                if (j + STAGES < m) {
+                const int qi = DYN ? qn : q + STAGES * G;  // the position whose load goes into this stage
+                if (qi < nitems) {
                     fence_proxy_async_smem();
-                    issue(j + STAGES, stage);
+                    issue(qi, stage);
                 }
+                if (DYN) qn = qa;
             }
+            q = qnext;
         }
         if (failed) {
             // let every load already issued land (bounded) before going on
-            for (int q = 0; q < STAGES && j + q < m; ++q) {
-                const int kk = k + q;
+            for (int jj = 0; jj < STAGES && q + jj * G < nitems; ++jj) {
+                const int kk = k + jj;
                 mbar_wait_bounded(&bar[kk % STAGES], (kk / STAGES) & 1, kWaitLimitCycles);
             }
             if (threadIdx.x == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
         }
         if (!MULTI) break;
 
-        // grid barrier; the last CTA to arrive finishes the iteration
+        // grid barrier; the last CTA to arrive finishes the iteration (the
+        // arrival is an acquire-release atomic: it publishes this CTA's
+        // partials and u^{n+1} tiles, and the last arrival sees everyone's)
         fence_proxy_async_global();
         __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(&st->arrive, 1u);
+            const unsigned prev = atom_add_acq_rel_gpu(&st->arrive, 1u);
             s_last = prev == (unsigned)G - 1u;
             s_timeout = 0;
         }
         __syncthreads();
         if (s_last) {
-            finish_iteration(d, st);
+            const int next = finish_iteration<(MINB >= 6 ? 8 : 11)>(d, st, it == iters - 1, false, true);
             if (threadIdx.x == 0) {
-                __threadfence();
+                // the counter of the next iteration was last used two iterations ago
+                if (DYN) st->work[next & 1] = 0u;
                 st_release_gpu(&st->gen, gen + 1u);
             }
         } else if (threadIdx.x == 0) {

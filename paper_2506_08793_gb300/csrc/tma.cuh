@@ -114,6 +114,20 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+// Acquire-release fence at GPU scope (lighter than the sequentially
+// consistent __threadfence): orders this thread's earlier and later memory
+// accesses against those of other threads synchronised through atomics.
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// atomicAdd with acquire-release semantics at GPU scope: publishes what this
+// CTA wrote before it (after a CTA barrier) and, for the thread that sees the
+// final count, makes every earlier arrival's writes visible.
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 __device__ __forceinline__ void st_release_gpu(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
