@@ -145,7 +145,7 @@ static uint32_t tma_smem_bytes(int th, int stages, int tma, int esize) {
 // tma: 0 generic gather, 1 TMA tiles with Phi/lambda staged, 2 TMA u tile with
 // Phi/lambda vector loads, 3 per-warp row streams (R = ring slots).
 static const SweepCfg kVariants[] = {
-    {6, 4, 1, 1, true, 5, 1},  // 0: library default: 24-row tiles, 5 CTAs/SM, multi-iteration launches
+    {6, 4, 1, 1, true, 0, 1},  // 0: library default: 24-row tiles, multi-iteration launches
     {8, 4, 1, 1, true},  {8, 4, 2, 1, true},  {4, 8, 2, 1, true},  {4, 8, 1, 1, true},
     {8, 4, 1, 2, true},  {8, 4, 2, 2, true},  {4, 8, 1, 2, true},  {16, 4, 1, 2, true},
     {8, 8, 1, 2, true},  {16, 2, 2, 2, true}, {8, 4, 1, 3, true},  {8, 8, 1, 3, true},
@@ -207,8 +207,8 @@ static SweepCfg pick_cfg(const dh_params *p, bool tma_ok, bool is16, int H, int 
     const bool edge = !(p->variant & DH_VAR_NO_EDGE);
     SweepCfg c = kVariants[0];
     c.edge = edge;
-    if (is16) {  // 16-bit storage: the default multi-iteration tiling (variant 1: single-iteration)
-        if (tma_ok && p->sweep_variant != 1) c = SweepCfg{6, 4, 1, 1, edge, 5, 1};
+    if (is16) {  // 16-bit storage: 32-row tiles, multi-iteration launches (variant 1: single-iteration)
+        if (tma_ok && p->sweep_variant != 1) c = SweepCfg{8, 4, 1, 1, edge, 0, 1};
         else c = SweepCfg{8, 4, 1, tma_ok ? 1 : 0, edge};
         return c;
     }

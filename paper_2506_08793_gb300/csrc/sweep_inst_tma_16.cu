@@ -7,6 +7,7 @@ template <class T>
 static SweepTmaFn tma16(int R, int NW, int stages, int tma, bool edge, int minb, int multi) {
     DH_STX_T(T, 8, 4, 1, true, 0, false)
     DH_STX_T(T, 6, 4, 1, true, 5, true)
+    DH_STX_T(T, 8, 4, 1, true, 0, true)
     return nullptr;
 }
 
