@@ -63,6 +63,7 @@ static std::vector<std::vector<int>> warm_groups(int n, const dh_image *imgs) {
 
 constexpr int kMaxBatch = 256;
 constexpr int kBR = 6, kBNW = 4, kBTH = kBR * kBNW;  // 128 x 24 tiles, 4 warps, 5 CTAs per SM
+constexpr int kBChunk = 3;  // items a CTA takes at a time: the three channels of one tile
 
 // Per-image loop data in device memory.
 struct __align__(128) BImg {
@@ -77,6 +78,7 @@ struct BatchHdr {
     int nactive;
     int iter;          // loop iterations so far (odd ones walk the items in reverse)
     unsigned arrive;
+    unsigned work;     // chunks handed out in the current launch beyond the first G
     int use_cond;
     unsigned long long cond;
     int active[kMaxBatch];
@@ -143,6 +145,7 @@ __global__ void k_batch_init(BatchHdr *h, BImg *imgs, int n, int use_cond, unsig
     h->nactive = n;
     h->iter = 0;
     h->arrive = 0;
+    h->work = 0;
     h->use_cond = use_cond;
     h->cond = cond;
     int acc = 0, k = 0;
@@ -233,7 +236,6 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
     __syncthreads();
     const int total = s_prefix[nact];
     BImg *imgs = hb->imgs;
-    const int G = gridDim.x;
     T *s = reinterpret_cast<T *>(sb + P::U_OFF);
     float *sphi = reinterpret_cast<float *>(sb + P::PHI_OFF);
     float *slam = reinterpret_cast<float *>(sb + P::LAM_OFF);
@@ -252,25 +254,25 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         tile = j / 3;
         c = j - 3 * tile;
     };
-    // this CTA's items: one channel of a contiguous run [lo, hi) of the active
-    // tile list (G is a multiple of 3; CTAs 3k, 3k+1, 3k+2 take channels 0, 1, 2
-    // of run k, so the lambda tile the three share is loaded while it is in
-    // L2).  Consecutive items mostly belong to one image: one tensor-map acquire
-    // and one arrival atomic per image, not per item.  Odd loop iterations walk
-    // the run in reverse, starting on the tiles this CTA touched last.
-    const int runs = G / 3, run = (int)blockIdx.x / 3, ch = (int)blockIdx.x - 3 * run, ntiles = total / 3;
-    const int lo = (int)((long long)run * ntiles / runs), hi = (int)((long long)(run + 1) * ntiles / runs);
-    const int m = hi - lo;
+    // Items in walk order: position q -> item (odd loop iterations walk
+    // backwards, starting on the tiles touched last).  The positions are
+    // handed out in chunks of kBChunk (one tile's three channels; the next
+    // chunk is the tile below): chunk blockIdx.x first, then G + the values of
+    // a counter the grid shares for the launch, so that CTAs that run faster
+    // take more chunks and all finish at about the same time.  Thread 0 takes
+    // the next chunk while the first item of the current one is walked and
+    // publishes each next position in s_next before the walk's closing
+    // barrier.  Consecutive items of a CTA mostly belong to one image: one
+    // tensor-map acquire and one arrival atomic per image change.
     const bool rev = (__ldcg(&hb->iter) & 1) != 0;
-    const int base = 3 * (rev ? hi - 1 : lo) + ch, step = rev ? -3 : 3;
-    auto item_at = [&](int j) { return base + step * j; };
+    const int G = gridDim.x, nch = (total + kBChunk - 1) / kBChunk;
+    auto item_of = [&](int q) { return rev ? total - 1 - q : q; };
     // thread 0, TMA images only: load an item's tiles.  (No L2 prefetch of the
-    // next item: a run walks down a column of tiles, so the next tile's rows are
-    // already coming in as this tile's halo; prefetching one item ahead cost 7 %
-    // on the 64-image batch, two items ahead 22 %.)
+    // next item: the next tile down a column arrives as this tile's halo;
+    // prefetching one item ahead cost 7 % on the 64-image batch.)
     // The maps were written on the device (k_batch_put): acquire them for the
     // tensor-map proxy when the image changes from the previous use by this CTA.
-    __shared__ int s_acq_img, s_arr_cnt;  // thread 0's state, kept out of the walk's registers
+    __shared__ int s_acq_img, s_arr_cnt, s_next;  // thread 0's state, kept out of the walk's registers
     if (threadIdx.x == 0) {
         s_acq_img = -1;
         s_arr_cnt = 0;  // finished items of the current image not yet counted
@@ -298,7 +300,9 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         tma_load_2d(sb + P::LAM_OFF, &im->tm[3], &bar, x0, y0);
         return img;
     };
-    if (threadIdx.x == 0 && m > 0) issue(item_at(0));
+    int q = (int)blockIdx.x < nch ? (int)blockIdx.x * kBChunk : total;  // current position (every thread)
+    int cn = nch;  // (thread 0) the chunk after the current one
+    if (threadIdx.x == 0 && q < total) issue(item_of(q));
 
     // An image whose last item of this iteration a CTA has just finished is
     // finished (residual, stop rule) by that CTA at its next barrier, so the
@@ -315,8 +319,8 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
 
     int kt = 0;  // TMA items waited for so far (barrier phase)
     bool failed = false;
-    for (int j = 0; j < m; ++j) {
-        const int item = item_at(j);
+    while (q < total) {
+        const int item = item_of(q);
         int slot, img, tile, c;
         locate(item, slot, img, tile, c);
         BImg *im = imgs + img;
@@ -364,6 +368,9 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
             fence_proxy_async_smem();
         }
         __syncthreads();
+        // first item of a chunk: take the next one (its value is needed only
+        // after this chunk's last walk)
+        if (threadIdx.x == 0 && q % kBChunk == 0) cn = G + (int)atomicAdd(&hb->work, 1u);
 
         T *__restrict__ un = static_cast<T *>(d->u[cur ^ 1]) + c * N;
         const int x = x0 + 4 * lane;
@@ -394,12 +401,18 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         };
         walk_rows<kBR, SW, T, EDGE>(s, w * kBR, lane, d->eps, d->tau, d->wg0, d->wg1, d->wg2, pl, sink);
 
+        if (threadIdx.x == 0) {  // the position after q: within the chunk, else the next chunk's first
+            int qn = q + 1;
+            if (qn % kBChunk == 0 || qn >= total) qn = cn < nch ? cn * kBChunk : total;
+            s_next = qn;
+        }
         const float2 tot = block_pair_sum<kBNW>(rs, rc, red);  // every thread is past its walk
+        const int qnext = s_next;  // rewritten only after the next item's first barrier
         if (threadIdx.x == 0) {
             int next_img = -1;
-            if (j + 1 < m) {  // the stage is free: start the next load first
+            if (qnext < total) {  // the stage is free: start the next load first
                 fence_proxy_async_smem();
-                next_img = issue(item_at(j + 1));
+                next_img = issue(item_of(qnext));
             }
             d->part[(size_t)c * d->nblk + tile] = tot;
             const unsigned cnt = (unsigned)++s_arr_cnt;
@@ -410,6 +423,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
                 s_arr_cnt = 0;
             }
         }
+        q = qnext;
     }
     __syncthreads();
     finish_pending();
@@ -419,38 +433,53 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
             for (int k = 0; k < nact; ++k) atomicCAS(&imgs[s_active[k]].d.st->err, 0, DH_ETIMEOUT);
         }
     }
-    // last CTA: compact the active list, keep the loop going while it is not empty
+    // last CTA: compact the active list, keep the loop going while it is not
+    // empty.  The arrival is an acquire-release atomic (it publishes this CTA's
+    // work; the last arrival sees everyone's).  The images' states are read by
+    // all threads at once, then thread 0 scans the flags in shared memory.
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned prev = atomicAdd(&hb->arrive, 1u);
+        const unsigned prev = atom_add_acq_rel_gpu(&hb->arrive, 1u);
         s_last = prev == gridDim.x - 1u;
     }
     __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        int k = 0, acc = 0;
-        for (int i = 0; i < hb->nimg; ++i) {
+    if (s_last) {
+        const int nimg = hb->nimg;
+        int *s_keep = s_active, *s_items = s_prefix;  // free again: reused for the compaction
+        for (int i = threadIdx.x; i < nimg; i += blockDim.x) {
             SolveState *st = imgs[i].d.st;
-            if (__ldcg(&st->done)) continue;
-            const int err = __ldcg(&st->err);
-            if (err) {  // a bounded wait gave up: this image stops with the error
-                st->done = 1;
-                st->status = err;
-                st->n_final = st->n;
-                continue;
+            int keep = 0;
+            if (!__ldcg(&st->done)) {
+                const int err = __ldcg(&st->err);
+                if (err) {  // a bounded wait gave up: this image stops with the error
+                    st->done = 1;
+                    st->status = err;
+                    st->n_final = __ldcg(&st->n);
+                } else {
+                    keep = 1;
+                }
             }
-            hb->active[k] = i;
-            hb->prefix[k] = acc;
-            acc += imgs[i].items;
-            ++k;
+            s_keep[i] = keep;
+            s_items[i] = keep ? imgs[i].items : 0;
         }
-        hb->prefix[k] = acc;
-        hb->nactive = k;
-        hb->iter = hb->iter + 1;
-        hb->arrive = 0;
-        __threadfence();
-        if (hb->use_cond && k > 0) cudaGraphSetConditional(hb->cond, 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int k = 0, acc = 0;
+            for (int i = 0; i < nimg; ++i) {
+                if (!s_keep[i]) continue;
+                hb->active[k] = i;
+                hb->prefix[k] = acc;
+                acc += s_items[i];
+                ++k;
+            }
+            hb->prefix[k] = acc;
+            hb->nactive = k;
+            hb->iter = hb->iter + 1;
+            hb->arrive = 0;
+            hb->work = 0;
+            __threadfence();
+            if (hb->use_cond && k > 0) cudaGraphSetConditional(hb->cond, 1);
+        }
     }
 }
 
