@@ -232,9 +232,9 @@ def test_sweep_variants_agree(N, api, orc, H, W, monkeypatch):
     applies the same float32 operations to each pixel, but the PTX
     approximate square root and reciprocal of the face flux are not specified
     to the bit: their results can differ by an ulp from one code location to
-    another (measured: at the rows where a warp's walk starts).  After 12
-    iterations the variants agree to 1e-6 relative; each variant is
-    deterministic run to run."""
+    another, and kernels with another split of rows over warps differ at a few
+    pixels in the row above a warp's first row.  After 12 iterations the
+    variants agree to 1e-6 relative; each variant is deterministic run to run."""
     _, _, Phi, lam = _problem(orc, 31 + H, H, W, "stable")
     outs = {}
     for cfg in ("8,4,2,0", "8,4,2,1", "8,4,1,1", "4,8,2,1", "8,4,1,2", "4,8,2,2", "16,4,1,2", "16,4,2,0",
