@@ -373,12 +373,24 @@ struct Tb2Plan {
 };
 
 // Last CTA of a two-iteration sweep: residuals of both levels, decision.
-static __device__ void finish_tb2(const SolveDesc *d, SolveState *st) {
-    constexpr int U = 4;
+// Called after an acquire-release arrival; thread 0 loads the state it
+// decides with before the partials and returns the next iterate's index (the
+// caller publishes the state with a release store).  The while condition is
+// set only by a launch that goes on after its last iteration.
+static __device__ int finish_tb2(const SolveDesc *d, SolveState *st, bool last_in_launch) {
+    constexpr int U = 6;
     __shared__ float2 wsum[6][32];
     __shared__ float sq[6];
     const int tid = threadIdx.x, nt = blockDim.x, w = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    __threadfence();
+    int n = 0, two = 0, cur = 0, err = 0;
+    float phin2[3] = {0.f, 0.f, 0.f};
+    if (tid == 0) {
+        n = ld_state_int(&st->n);
+        two = ld_state_int(&st->tb2);
+        cur = ld_state_int(&st->cur);
+        err = ld_state_int(&st->err);
+        for (int c = 0; c < 3; ++c) phin2[c] = __ldcg(&st->phin2[c]);
+    }
     const int nblk = d->nblk;
     const float2 *part = d->part;
     float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, cc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -412,13 +424,12 @@ static __device__ void finish_tb2(const SolveDesc *d, SolveState *st) {
         sq[tid] = a + b;
     }
     __syncthreads();
-    if (tid != 0) return;
-    const int n = st->n, two = st->tb2;
+    if (tid != 0) return 0;
     auto rho_of = [&](int lv, float *rho, float &worst) {
         bool finite = true;
         worst = 0.f;
         for (int c = 0; c < 3; ++c) {
-            const float pn = st->phin2[c], q = sq[3 * lv + c];
+            const float pn = phin2[c], q = sq[3 * lv + c];
             rho[c] = pn > 0.f ? sqrtf(q / pn) : sqrtf(q);
             if (!isfinite(rho[c])) finite = false;
             else worst = fmaxf(worst, rho[c]);
@@ -429,9 +440,9 @@ static __device__ void finish_tb2(const SolveDesc *d, SolveState *st) {
     const bool fin0 = rho_of(0, rho0, w0);
     if (d->rho_hist)
         for (int c = 0; c < 3; ++c) d->rho_hist[3 * n + c] = rho0[c];
-    const int err = __ldcg(&st->err);
     const bool conv = fin0 && w0 <= d->tol;
     unsigned cont = 1;
+    int next = n;
     if (err || conv || !fin0 || n >= d->max_iter) {
         st->done = 1;
         st->n_final = n;
@@ -439,8 +450,8 @@ static __device__ void finish_tb2(const SolveDesc *d, SolveState *st) {
         for (int c = 0; c < 3; ++c) st->rho[c] = rho0[c];
         cont = 0;
     } else if (!two) {
-        st->n = n + 1;
-        st->cur ^= 1;
+        st->n = next = n + 1;
+        st->cur = cur ^ 1;
     } else {
         float rho1[3], w1;
         const bool fin1 = rho_of(1, rho1, w1);
@@ -449,13 +460,13 @@ static __device__ void finish_tb2(const SolveDesc *d, SolveState *st) {
         } else {
             if (d->rho_hist)
                 for (int c = 0; c < 3; ++c) d->rho_hist[3 * (n + 1) + c] = rho1[c];
-            st->n = n + 2;
-            st->cur ^= 1;
+            st->n = next = n + 2;
+            st->cur = cur ^ 1;
         }
     }
     st->arrive = 0;
-    __threadfence();
-    if (d->use_cond) cudaGraphSetConditional(d->cond, cont);
+    if (d->use_cond && cont && last_in_launch) cudaGraphSetConditional(d->cond, 1u);
+    return next;
 }
 
 template <int R2, int NW, bool EDGE, int MINB>
@@ -469,7 +480,7 @@ k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t bar;
     __shared__ float2 red[2][NW];
-    __shared__ int s_last, s_timeout;
+    __shared__ int s_last, s_timeout, s_next;
     float *s0 = reinterpret_cast<float *>(smem + P::U0_OFF);
     const float *sphi = reinterpret_cast<const float *>(smem + P::PHI_OFF);
     const float *slam = reinterpret_cast<const float *>(smem + P::LAM_OFF);
@@ -484,7 +495,6 @@ k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     const int ntx = (W + kTW2 - 1) / kTW2, nty = (H + TH - 1) / TH;
     const int nitems = 3 * ntx * nty;
     const int G = gridDim.x;
-    const int m = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -497,13 +507,19 @@ k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     const int nblk = d->nblk;
     int k = 0;
     bool failed = false;
-    for (int it = 0; it < d->depth; ++it) {
+    const int iters = d->depth;
+    for (int it = 0; it < iters; ++it) {
         const int cur = __ldcg(&st->cur);
-        const bool rev = (__ldcg(&st->n) & 1) != 0;
+        const int n_it = __ldcg(&st->n);
+        const bool rev = (n_it & 1) != 0;
         const bool two = __ldcg(&st->tb2) != 0;
         const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
         float *__restrict__ uout = static_cast<float *>(d->u[cur ^ 1]);
-        auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
+        // position q in the iteration's walk order -> item (odd n walk backwards);
+        // the positions are handed out as in k_sweep_tma: blockIdx.x, blockIdx.x
+        // + G, then 2G + a counter the grid shares for the iteration
+        auto item_at = [&](int q) { return rev ? nitems - 1 - q : q; };
+        unsigned *ctr = &st->work[n_it & 1];
         auto tile_xy = [&](int item, int &c, int &x0, int &y0) {
             const int tile = item / 3;
             c = item - 3 * tile;
@@ -526,15 +542,16 @@ k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             tma_prefetch_3d(&tm_phi, x0 - 4, y0 - 2, c);
             tma_prefetch_2d(&tm_lam, x0 - 4, y0 - 2);
         };
+        int q = (int)blockIdx.x;  // current position (every thread)
+        int qn = q + G;           // next position (thread 0)
         if (threadIdx.x == 0) {
             if (it > 0) fence_proxy_async_global();
-            if (m > 0) issue(0);
+            if (q < nitems) issue(q);
         }
-        int j = 0;
-        for (; j < m; ++j, ++k) {
+        for (; q < nitems; ++k) {
             int c, x0, y0;
-            const int tile = tile_xy(item_at(j), c, x0, y0);
-            if (threadIdx.x == 0 && j + 1 < m) prefetch(j + 1);
+            const int tile = tile_xy(item_at(q), c, x0, y0);
+            if (threadIdx.x == 0 && qn < nitems) prefetch(qn);
             const bool ok = mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);
             if (__syncthreads_or(!ok)) {
                 failed = true;
@@ -546,6 +563,10 @@ k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
                 fence_proxy_async_smem();  // these writes precede the next TMA load into this buffer
             }
             __syncthreads();
+            // (thread 0) the position after the next one, taken here so that no
+            // block barrier waits for the atomic before the end of step 1
+            int qa = nitems;
+            if (threadIdx.x == 0 && qn < nitems) qa = 2 * G + (int)atomicAdd(ctr, 1u);
 
             // step 1: region rows y0-2 .. y0+TH+1, columns x0-4 .. x0+123 (frame row t, column 4*lane + j)
             float rs0 = 0.f, rc0 = 0.f, rs1 = 0.f, rc1 = 0.f;
@@ -612,35 +633,39 @@ k_sweep_tb2(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
                 };
                 walk_rows<R2, SW, float, EDGE>(s1, w * R2, lane, eps, tau, wg0, wg1, wg2, pl, sink);
             }
+            if (threadIdx.x == 0) s_next = qn;  // read after the barrier below
             const float2 t0 = block_pair_sum<NW>(rs0, rc0, red[0]);  // ends with a barrier
             const float2 t1 = block_pair_sum<NW>(rs1, rc1, red[1]);
+            const int qnext = s_next;
             if (threadIdx.x == 0) {
                 part[(size_t)c * nblk + tile] = t0;
                 part[(size_t)(3 + c) * nblk + tile] = t1;
-                if (j + 1 < m) {
+                if (qn < nitems) {
                     fence_proxy_async_smem();
-                    issue(j + 1);
+                    issue(qn);
                 }
+                qn = qa;
             }
             __syncthreads();
+            q = qnext;
         }
         if (failed) {
-            if (j < m) mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);  // the load in flight
+            if (q < nitems) mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);  // the load in flight
             if (threadIdx.x == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
         }
-        // grid barrier; the last CTA to arrive decides
+        // grid barrier; the last CTA to arrive decides (an acquire-release
+        // arrival: it publishes this CTA's tiles, the last one sees everyone's)
         fence_proxy_async_global();
         __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
-            s_last = atomicAdd(&st->arrive, 1u) == (unsigned)G - 1u;
+            s_last = atom_add_acq_rel_gpu(&st->arrive, 1u) == (unsigned)G - 1u;
             s_timeout = 0;
         }
         __syncthreads();
         if (s_last) {
-            finish_tb2(d, st);
+            const int next = finish_tb2(d, st, it == iters - 1);
             if (threadIdx.x == 0) {
-                __threadfence();
+                st->work[next & 1] = 0u;  // every CTA is past its last take of this iteration
                 st_release_gpu(&st->gen, gen + 1u);
             }
         } else if (threadIdx.x == 0) {
@@ -924,24 +949,43 @@ struct TbkPlan {
 };
 
 // Last CTA of a depth-K sweep: residuals of the K levels, decision.
+// Called after an acquire-release arrival; thread 0 loads the state it
+// decides with before the partials and returns the next iterate's index (the
+// caller publishes the state with a release store).  The while condition is
+// set only by a launch that goes on after its last iteration.
 template <int K>
-static __device__ void finish_tbk(const SolveDesc *d, SolveState *st) {
-    constexpr int L3 = 3 * K;
+static __device__ int finish_tbk(const SolveDesc *d, SolveState *st, bool last_in_launch) {
+    constexpr int L3 = 3 * K, U = K >= 4 ? 2 : 4;  // partial loads per level in flight per thread
     __shared__ float2 wsum[L3][32];
     __shared__ float sq[L3];
     const int tid = threadIdx.x, nt = blockDim.x, w = tid >> 5, lane = tid & 31, nw = nt >> 5;
-    __threadfence();
+    int n = 0, deep = 0, cur = 0, err = 0;
+    float phin2[3] = {0.f, 0.f, 0.f};
+    if (tid == 0) {
+        n = ld_state_int(&st->n);
+        deep = ld_state_int(&st->tb2);
+        cur = ld_state_int(&st->cur);
+        err = ld_state_int(&st->err);
+        for (int c = 0; c < 3; ++c) phin2[c] = __ldcg(&st->phin2[c]);
+    }
     const int nblk = d->nblk;
     const float2 *part = d->part;
     float s[L3], cc[L3];
 #pragma unroll
     for (int q = 0; q < L3; ++q) s[q] = cc[q] = 0.f;
-    for (int b = tid; b < nblk; b += nt) {
+    for (int b0 = tid; b0 < nblk; b0 += U * nt) {
+        float2 v[L3][U];
 #pragma unroll
-        for (int q = 0; q < L3; ++q) {
-            const float2 v = __ldcg(part + (size_t)q * nblk + b);
-            neumaier_merge(s[q], cc[q], v.x, v.y);
-        }
+        for (int q = 0; q < L3; ++q)
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int b = b0 + j * nt;
+                v[q][j] = b < nblk ? __ldcg(part + (size_t)q * nblk + b) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int q = 0; q < L3; ++q)
+#pragma unroll
+            for (int j = 0; j < U; ++j) neumaier_merge(s[q], cc[q], v[q][j].x, v[q][j].y);
     }
 #pragma unroll
     for (int q = 0; q < L3; ++q) {
@@ -959,13 +1003,12 @@ static __device__ void finish_tbk(const SolveDesc *d, SolveState *st) {
         sq[tid] = a + b;
     }
     __syncthreads();
-    if (tid != 0) return;
-    const int n = st->n, deep = st->tb2;
+    if (tid != 0) return 0;
     auto rho_of = [&](int lv, float *rho, float &worst) {
         bool finite = true;
         worst = 0.f;
         for (int c = 0; c < 3; ++c) {
-            const float pn = st->phin2[c], q = sq[3 * lv + c];
+            const float pn = phin2[c], q = sq[3 * lv + c];
             rho[c] = pn > 0.f ? sqrtf(q / pn) : sqrtf(q);
             if (!isfinite(rho[c])) finite = false;
             else worst = fmaxf(worst, rho[c]);
@@ -976,9 +1019,9 @@ static __device__ void finish_tbk(const SolveDesc *d, SolveState *st) {
     const bool fin0 = rho_of(0, rho0, w0);
     if (d->rho_hist)
         for (int c = 0; c < 3; ++c) d->rho_hist[3 * n + c] = rho0[c];
-    const int err = __ldcg(&st->err);
     const bool conv = fin0 && w0 <= d->tol;
     unsigned cont = 1;
+    int next = n;
     if (err || conv || !fin0 || n >= d->max_iter) {
         st->done = 1;
         st->n_final = n;
@@ -986,8 +1029,8 @@ static __device__ void finish_tbk(const SolveDesc *d, SolveState *st) {
         for (int c = 0; c < 3; ++c) st->rho[c] = rho0[c];
         cont = 0;
     } else if (!deep) {
-        st->n = n + 1;
-        st->cur ^= 1;
+        st->n = next = n + 1;
+        st->cur = cur ^ 1;
     } else {
         // u^{n+l}, 0 < l < K, is the answer if its residual meets tol, is not
         // finite or n + l reaches max_iter: then redo it one iteration at a time
@@ -1006,13 +1049,13 @@ static __device__ void finish_tbk(const SolveDesc *d, SolveState *st) {
                     rho_of(l, rl, wl);
                     for (int c = 0; c < 3; ++c) d->rho_hist[3 * (n + l) + c] = rl[c];
                 }
-            st->n = n + K;
-            st->cur ^= 1;
+            st->n = next = n + K;
+            st->cur = cur ^ 1;
         }
     }
     st->arrive = 0;
-    __threadfence();
-    if (d->use_cond) cudaGraphSetConditional(d->cond, cont);
+    if (d->use_cond && cont && last_in_launch) cudaGraphSetConditional(d->cond, 1u);
+    return next;
 }
 
 // Step S of a depth-K item: walks the step's frame rows from `src` (row 0 =
@@ -1082,7 +1125,7 @@ k_sweep_tbk(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     unsigned char *smem = smem_align1024(smem_raw);
     __shared__ __align__(8) uint64_t bar;
     __shared__ float2 red[K][NW];
-    __shared__ int s_last, s_timeout;
+    __shared__ int s_last, s_timeout, s_next;
     float *s0 = reinterpret_cast<float *>(smem + P::U0_OFF);
     const float *sphi = reinterpret_cast<const float *>(smem + P::PHI_OFF);
     const float *slam = reinterpret_cast<const float *>(smem + P::LAM_OFF);
@@ -1098,7 +1141,6 @@ k_sweep_tbk(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     const int ntx = (W + WO - 1) / WO, nty = (H + TH - 1) / TH;
     const int nitems = 3 * ntx * nty;
     const int G = gridDim.x;
-    const int m = (int)blockIdx.x < nitems ? (nitems - 1 - (int)blockIdx.x) / G + 1 : 0;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         fence_mbar_init();
@@ -1111,13 +1153,19 @@ k_sweep_tbk(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     const int nblk = d->nblk;
     int k = 0;
     bool failed = false;
-    for (int it = 0; it < d->depth; ++it) {
+    const int iters = d->depth;
+    for (int it = 0; it < iters; ++it) {
         const int cur = __ldcg(&st->cur);
-        const bool rev = (__ldcg(&st->n) & 1) != 0;
+        const int n_it = __ldcg(&st->n);
+        const bool rev = (n_it & 1) != 0;
         const bool deep = __ldcg(&st->tb2) != 0;
         const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
         float *__restrict__ uout = static_cast<float *>(d->u[cur ^ 1]);
-        auto item_at = [&](int j) { return (int)blockIdx.x + (rev ? m - 1 - j : j) * G; };
+        // position q in the iteration's walk order -> item (odd n walk backwards);
+        // the positions are handed out as in k_sweep_tma: blockIdx.x, blockIdx.x
+        // + G, then 2G + a counter the grid shares for the iteration
+        auto item_at = [&](int q) { return rev ? nitems - 1 - q : q; };
+        unsigned *ctr = &st->work[n_it & 1];
         auto tile_xy = [&](int item, int &c, int &x0, int &y0) {
             const int tile = item / 3;
             c = item - 3 * tile;
@@ -1140,15 +1188,16 @@ k_sweep_tbk(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             tma_prefetch_3d(&tm_phi, x0 - 4 * (K - 1), y0 - 2 * (K - 1), c);
             tma_prefetch_2d(&tm_lam, x0 - 4 * (K - 1), y0 - 2 * (K - 1));
         };
+        int q = (int)blockIdx.x;  // current position (every thread)
+        int qn = q + G;           // next position (thread 0)
         if (threadIdx.x == 0) {
             if (it > 0) fence_proxy_async_global();
-            if (m > 0) issue(0);
+            if (q < nitems) issue(q);
         }
-        int j = 0;
-        for (; j < m; ++j, ++k) {
+        for (; q < nitems; ++k) {
             int c, x0, y0;
-            const int tile = tile_xy(item_at(j), c, x0, y0);
-            if (threadIdx.x == 0 && j + 1 < m) prefetch(j + 1);
+            const int tile = tile_xy(item_at(q), c, x0, y0);
+            if (threadIdx.x == 0 && qn < nitems) prefetch(qn);
             const bool ok = mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);
             if (__syncthreads_or(!ok)) {
                 failed = true;
@@ -1161,6 +1210,10 @@ k_sweep_tbk(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
                 fence_proxy_async_smem();  // these writes precede the next TMA load into this buffer
             }
             __syncthreads();
+            // (thread 0) the position after the next one, taken here so that no
+            // block barrier waits for the atomic before the end of step 1
+            int qa = nitems;
+            if (threadIdx.x == 0 && qn < nitems) qa = 2 * G + (int)atomicAdd(ctr, 1u);
             float rs[K], rc[K];
 #pragma unroll
             for (int l = 0; l < K; ++l) rs[l] = rc[l] = 0.f;
@@ -1194,36 +1247,40 @@ k_sweep_tbk(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
                                                  wg0, wg1, wg2, rs[3], rc[3]);
                 }
             }
+            if (threadIdx.x == 0) s_next = qn;  // read after the barriers below
             float2 tot[K];
 #pragma unroll
             for (int l = 0; l < K; ++l) tot[l] = block_pair_sum<NW>(rs[l], rc[l], red[l]);  // each ends with a barrier
+            const int qnext = s_next;
             if (threadIdx.x == 0) {
 #pragma unroll
                 for (int l = 0; l < K; ++l) part[(size_t)(3 * l + c) * nblk + tile] = tot[l];
-                if (j + 1 < m) {
+                if (qn < nitems) {
                     fence_proxy_async_smem();
-                    issue(j + 1);
+                    issue(qn);
                 }
+                qn = qa;
             }
             __syncthreads();
+            q = qnext;
         }
         if (failed) {
-            if (j < m) mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);  // the load in flight
+            if (q < nitems) mbar_wait_bounded(&bar, k & 1, kWaitLimitCycles);  // the load in flight
             if (threadIdx.x == 0) atomicCAS(&st->err, 0, DH_ETIMEOUT);
         }
-        // grid barrier; the last CTA to arrive decides
+        // grid barrier; the last CTA to arrive decides (an acquire-release
+        // arrival: it publishes this CTA's tiles, the last one sees everyone's)
         fence_proxy_async_global();
         __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
-            s_last = atomicAdd(&st->arrive, 1u) == (unsigned)G - 1u;
+            s_last = atom_add_acq_rel_gpu(&st->arrive, 1u) == (unsigned)G - 1u;
             s_timeout = 0;
         }
         __syncthreads();
         if (s_last) {
-            finish_tbk<K>(d, st);
+            const int next = finish_tbk<K>(d, st, it == iters - 1);
             if (threadIdx.x == 0) {
-                __threadfence();
+                st->work[next & 1] = 0u;  // every CTA is past its last take of this iteration
                 st_release_gpu(&st->gen, gen + 1u);
             }
         } else if (threadIdx.x == 0) {
