@@ -91,7 +91,7 @@ struct BatchLayout {
 };
 
 static WsLayout img_layout(int H, int W, const dh_params *p) {
-    return ws_layout(H, W, 1, sweep_tile_h(1), refine_bytes(H, W, p));
+    return ws_layout(H, W, 1, sweep_tile_h(1), refine_bytes(H, W, p), false);
 }
 
 static BatchLayout batch_layout(int n, const dh_image *im, const dh_params *p) {

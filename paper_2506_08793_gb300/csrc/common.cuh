@@ -30,7 +30,7 @@ constexpr int kStallWindow = 16;  // residual-stall test of a 16-bit phase: iter
 struct SolveState {
     unsigned arrive;   // CTAs of the current sweep launch that have finished
     int n;             // index of the current iterate u^n
-    int cur;           // buffer (0 = caller's u, 1 = workspace) holding u^n
+    int cur;           // buffer (0 = caller's u, 1 and 2 = workspace) holding u^n
     int done;          // 1 once the loop has stopped
     int status;        // DH_OK / DH_WNOCONV / DH_ENONFINITE
     int n_final;       // n of the returned iterate
@@ -41,6 +41,14 @@ struct SolveState {
     int depth;         // sweeps per launch of the current loop (SolveDesc::depth)
     int tb2;           // temporally blocked sweep: 1 while two iterations per tile load are taken
     float rmax[kStallWindow];  // max_c rho_n of the last iterations (ring)
+    // Deferred decision of the multi-iteration float32 sweep (three iterate
+    // buffers): the iteration after n starts before the residual of u^n is
+    // reduced; u^{n-1} stays in buffer cprev until that decision is known.
+    int cprev;         // buffer holding u^{n-1} (3-buffer rotation)
+    int pend;          // 1: the decision on u^{n-1} is being reduced
+    int dstop;         // that decision: 1 = stop at n - 1
+    int dstatus;       // its status when it stops
+    float drho[3];     // its residual
     // Grid-barrier generation of the multi-iteration sweep, alone in its
     // 128-byte line so that the CTAs polling it do not contend with the
     // arrivals and state updates above.  Never reset: kernels read it first.
@@ -59,7 +67,7 @@ constexpr int kStatusSwitch = 100;
 // Everything the loop kernels need; written to the workspace by one tiny
 // kernel per call so that a cached CUDA graph can be relaunched unchanged.
 struct SolveDesc {
-    void *u[2];          // iterate buffers, float or 16-bit (storage)
+    void *u[3];          // iterate buffers, float or 16-bit (storage); u[2]: third float buffer or null
     const float *phi;
     const float *lam;
     float *rho_hist;     // [3*(max_iter+1)] or nullptr
@@ -71,6 +79,7 @@ struct SolveDesc {
     int storage;         // element type of u[]: 0 float, 1 bf16, 2 f16
     int phase_stop;      // 1: stop this phase when the residual stalls
     int dirichlet;       // 1: u = 0 outside the image, else reflecting boundary
+    int defer;           // 1: u[2] is set, the multi-iteration float32 sweep may defer its decisions
     int H, W;
     int max_iter;
     int depth;           // iterations per launch of the multi-iteration sweep (1 otherwise)
@@ -93,7 +102,7 @@ struct SelectState {
 };
 
 struct WsLayout {
-    size_t state, desc, sel, hist, blk, phin_part, part, dc, lam, phi, ub, refine, total;
+    size_t state, desc, sel, hist, blk, phin_part, part, dc, lam, phi, ub, uc, refine, total;
     int nblk_sweep, nblk_dcp, nblk_sel, depth, tile_h;
 };
 
@@ -109,7 +118,9 @@ constexpr int kSelBlocks = 1024;
 // filter) for these parameters; 0 when both are off.
 size_t refine_bytes(int H, int W, const dh_params *p);
 
-static inline WsLayout ws_layout(int H, int W, int depth, int tile_h, size_t refine = 0) {
+// third: a third float32 iterate buffer (uc) for the single-image sweep's
+// deferred decisions (the batched solve has none).
+static inline WsLayout ws_layout(int H, int W, int depth, int tile_h, size_t refine = 0, bool third = true) {
     WsLayout L;
     const size_t N = (size_t)H * W;
     L.depth = depth;
@@ -131,6 +142,7 @@ static inline WsLayout ws_layout(int H, int W, int depth, int tile_h, size_t ref
     L.lam = o; o = align_up(o + N * sizeof(float));
     L.phi = o; o = align_up(o + 3 * N * sizeof(float));
     L.ub = o; o = align_up(o + 3 * N * sizeof(float) + kAlign);  // f32 buffer, or two 16-bit ones
+    L.uc = third ? o : 0; o = third ? align_up(o + 3 * N * sizeof(float)) : o;
     L.refine = o; o = align_up(o + refine);
     L.total = o;
     return L;

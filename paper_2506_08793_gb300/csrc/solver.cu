@@ -24,7 +24,10 @@ __global__ void k_set_desc(SolveDesc *dst, SolveDesc v, int reset) {
     SolveState *st = v.st;
     st->depth = v.depth;
     st->work[0] = st->work[1] = 0u;
+    st->pend = 0;
+    st->dstop = 0;
     if (!reset) return;
+    st->cprev = 2;
     st->arrive = 0;
     st->n = 0;
     st->cur = 0;
@@ -72,6 +75,8 @@ __global__ void k_phase_convert(const SolveDesc *__restrict__ d, float *dst) {
 // stalled phase continues from the same n, any other outcome stays final.
 __global__ void k_phase_state(SolveState *st) {
     st->cur = 0;
+    st->cprev = 2;
+    st->pend = 0;
     st->arrive = 0;
     if (st->status == kStatusSwitch) {
         st->done = 0;
@@ -290,7 +295,7 @@ static int encode_map(CUtensorMap *m, CUtensorMapDataType dt, int esize, const v
 struct GraphKey {
     int dev;
     const void *desc;
-    const void *ptrs[4];
+    const void *ptrs[5];
     int H, W, R, NW, stages, tma, edge, storage, minb, multi;
     bool operator==(const GraphKey &o) const {
         return dev == o.dev && desc == o.desc && std::memcmp(ptrs, o.ptrs, sizeof(ptrs)) == 0 && H == o.H &&
@@ -404,17 +409,19 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
     const int H = v.H, W = v.W;
     constexpr int esize = (int)sizeof(T);
     auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
-    const bool aligned = a16(v.u[0]) && a16(v.u[1]) && a16(v.phi) && a16(v.lam);
+    const bool aligned = a16(v.u[0]) && a16(v.u[1]) && a16(v.phi) && a16(v.lam) && (!v.defer || a16(v.u[2]));
     // float4 Phi/lambda loads need W % 4; TMA rows of T need W * esize % 16
     v.vec = (W % 4 == 0) && aligned;
     const bool tma_ok = v.vec && (W * esize) % 16 == 0;
     v.storage = esize == 4 ? 0 : (Store<T>::TMA_TYPE == CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 ? 1 : 2);
     const SweepCfg cfg = pick_cfg(p, tma_ok, esize != 4, H, W);
     const int ntx = (W + kTW - 1) / kTW;
-    CUtensorMap maps[4];
+    CUtensorMap maps[5];
     const SolveDesc *dptr = desc_dev;
     int seg = 0;
     void *args_tma[5] = {&maps[0], &maps[1], &maps[2], &maps[3], (void *)&dptr};
+    // k_sweep_tma: u buffers 0, 1, 2 (the third only with deferred decisions), Phi, lambda
+    void *args_tma3[6] = {&maps[0], &maps[1], &maps[4], &maps[2], &maps[3], (void *)&dptr};
     void *args_stream[6] = {&maps[0], &maps[1], &maps[2], &maps[3], (void *)&dptr, (void *)&seg};
     void *args_gen[1] = {(void *)&dptr};
     LaunchSpec ls;
@@ -507,6 +514,8 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
         if (!rc) rc = encode_map(&maps[1], dt, esize, v.u[1], 3, W, H, 3, kTW + 2 * halo, TH + 4);
         if (!rc) rc = encode_f32_map(&maps[2], v.phi, 3, W, H, 3, kTW, TH);
         if (!rc) rc = encode_f32_map(&maps[3], v.lam, 2, W, H, 1, kTW, TH);
+        if (!rc && v.defer) rc = encode_map(&maps[4], dt, esize, v.u[2], 3, W, H, 3, kTW + 2 * halo, TH + 4);
+        if (!v.defer) maps[4] = maps[1];  // never read
         if (rc) return rc;
         SweepTmaFn fn = sweep_tma_fn<T>(cfg.R, cfg.NW, cfg.stages, cfg.tma, cfg.edge, cfg.minb, cfg.multi);
         if (!fn) return DH_EINVAL;
@@ -514,7 +523,7 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
         const int gmax = persistent_grid((void *)fn, cfg.NW * 32, smem);
         if (gmax <= 0) return DH_ECUDA;
         const int items = 3 * v.nblk;
-        ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(cfg.NW * 32), smem, args_tma};
+        ls = LaunchSpec{(void *)fn, dim3(items < gmax ? items : gmax), dim3(cfg.NW * 32), smem, args_tma3};
         if (cfg.multi) {
             ls.coop = 1;
             v.depth = kItersPerLaunch;
@@ -532,7 +541,7 @@ static int queue_loop(SolveDesc v, SolveDesc *desc_dev, bool reset, const dh_par
     if (p->use_graph) {
         int dev = 0;
         DH_CUDA_TRY(cudaGetDevice(&dev));
-        GraphKey key{dev, desc_dev, {v.u[0], v.u[1], v.phi, v.lam}, H, W, cfg.R, cfg.NW, cfg.stages, cfg.tma,
+        GraphKey key{dev, desc_dev, {v.u[0], v.u[1], v.phi, v.lam, v.u[2]}, H, W, cfg.R, cfg.NW, cfg.stages, cfg.tma,
                      cfg.edge ? 1 : 0, v.storage, cfg.minb, cfg.multi};
         GraphEntry ge;
         int rc = get_loop_graph(key, ls, &ge);
@@ -602,9 +611,12 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
     const bool switched = storage == DH_STORE_BF16_F32 || storage == DH_STORE_F16_F32;
     int rc = DH_OK;
     if (loop_begin) DH_CUDA_TRY(cudaEventRecord(loop_begin, s));
+    float *uc32 = L.uc ? (float *)(ws + L.uc) : nullptr;  // third float32 buffer (deferred decisions)
     if (!is16) {
         v.u[0] = u_caller;
         v.u[1] = ub32;
+        v.u[2] = uc32;
+        v.defer = uc32 != nullptr;
         v.phase_stop = 0;
         rc = queue_loop<float>(v, desc1, true, p, L, s, launches);
         if (rc) return rc;
@@ -634,6 +646,8 @@ int run_solve(float *u_caller, const float *phi, const float *lam, int H, int W,
             SolveDesc v2 = v;
             v2.u[0] = u_caller;
             v2.u[1] = ub32;
+            v2.u[2] = uc32;
+            v2.defer = uc32 != nullptr;
             v2.phase_stop = 0;
             rc = queue_loop<float>(v2, desc2, false, p, L, s, launches);
             if (rc) return rc;

@@ -46,6 +46,9 @@ __device__ __forceinline__ float gauss5(float vm2, float vm1, float v0, float vp
 
 __device__ __forceinline__ int ld_state_int(const int *p) { return __ldcg(p); }
 
+// stop_status' value for "the residual meets tol" (internal; reported as DH_OK)
+constexpr int kStatusConverged = 101;
+
 // Reduces the per-tile partials of the launch (last CTA only), decides whether
 // to stop, advances the state and sets the graph's while condition.  Every
 // thread of the CTA keeps U partial loads per channel in flight; the sums are
@@ -149,6 +152,159 @@ static __device__ int finish_iteration(const SolveDesc *d, SolveState *st, bool 
     // on after its last iteration sets it
     if (d->use_cond && cont && last_in_launch) cudaGraphSetConditional(d->cond, 1u);
     return next;
+}
+
+// ---------------------------------------------------------------- deferred decisions
+// The multi-iteration float32 sweep with a third iterate buffer: the last CTA
+// at the grid barrier of iteration n lets iteration n + 1 start at once and
+// reduces the residual of u^n while the others sweep; the decision on u^n is
+// read at the next barrier.  Iteration n + 1 writes u^{n+2} into the buffer
+// that holds neither u^n nor u^{n+1}, so u^n is still there when that decision
+// stops the loop at n (one sweep is then spent in vain).  The partials of
+// iteration n go to part + (n & 1) * 3 * nblk, so those being reduced are
+// never overwritten by the iteration running meanwhile.  The last iteration of
+// a launch decides at once (a launch leaves no decision pending).
+
+// sq[c] = the residual's sum of squares of channel c over the nblk tile
+// partials at `part` (layout [3][nblk]), in a fixed order; every thread of
+// the CTA takes part; sq (shared) is valid for all of them on return.
+template <int U>
+static __device__ void block_residual_sq(const float2 *part, int nblk, float *sq) {
+    __shared__ float2 wsum[3][32];
+    const int tid = threadIdx.x, nt = blockDim.x, w = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    float s[3] = {0.f, 0.f, 0.f}, cc[3] = {0.f, 0.f, 0.f};
+    for (int b0 = tid; b0 < nblk; b0 += U * nt) {
+        float2 p[3][U];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < U; ++j) {
+                const int b = b0 + j * nt;
+                p[c][j] = b < nblk ? __ldcg(part + (size_t)c * nblk + b) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < U; ++j) neumaier_merge(s[c], cc[c], p[c][j].x, p[c][j].y);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        for (int off = 16; off; off >>= 1) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s[c], off);
+            const float c2 = __shfl_down_sync(0xffffffffu, cc[c], off);
+            neumaier_merge(s[c], cc[c], s2, c2);
+        }
+        if (lane == 0) wsum[c][w] = make_float2(s[c], cc[c]);
+    }
+    __syncthreads();
+    if (tid < 3) {
+        float a = wsum[tid][0].x, b = wsum[tid][0].y;
+        for (int k = 1; k < nw; ++k) neumaier_merge(a, b, wsum[tid][k].x, wsum[tid][k].y);
+        sq[tid] = a + b;
+    }
+    __syncthreads();
+}
+
+// The stop rule on u^n from its sums of squares (thread 0): residual per
+// channel, finiteness, tolerance, max_iter, a sweep's error.  Returns the
+// status to stop with, or 0 to go on.
+__device__ __forceinline__ int stop_status(const SolveDesc *d, const SolveState *st, int n, const float *sq,
+                                           const float *phin2, float *rho) {
+    float worst = 0.f;
+    bool finite = true;
+    for (int c = 0; c < 3; ++c) {
+        const float pn = phin2[c];
+        rho[c] = pn > 0.f ? sqrtf(sq[c] / pn) : sqrtf(sq[c]);
+        if (!isfinite(rho[c])) finite = false;
+        else worst = fmaxf(worst, rho[c]);
+        if (d->rho_hist) d->rho_hist[3 * n + c] = rho[c];
+    }
+    const int err = ld_state_int(&st->err);
+    if (err) return err;
+    if (!finite) return DH_ENONFINITE;
+    if (worst <= d->tol) return kStatusConverged;
+    if (n >= d->max_iter) return DH_WNOCONV;
+    return 0;
+}
+
+// Grid barrier of the deferring sweep, last CTA (every thread).  partn: the
+// partials of the iteration just finished (the residual of u^n).  Returns 0
+// when the loop stops here, 1 when it goes on with no decision pending (the
+// launch's last iteration, decided at once), 2 when it goes on and the caller
+// must reduce partn with defer_reduce after releasing the others.
+template <int U>
+static __device__ int defer_barrier(const SolveDesc *d, SolveState *st, bool last_in_launch, const float2 *partn) {
+    __shared__ int s_mode;
+    __shared__ float sq[3];
+    int n = 0, cur = 0, cprev = 0;
+    float phin2[3] = {0.f, 0.f, 0.f};
+    if (threadIdx.x == 0) {
+        n = ld_state_int(&st->n);
+        cur = ld_state_int(&st->cur);
+        cprev = ld_state_int(&st->cprev);
+        for (int c = 0; c < 3; ++c) phin2[c] = __ldcg(&st->phin2[c]);
+        int mode;
+        if (ld_state_int(&st->pend) && ld_state_int(&st->dstop)) {
+            // the decision on u^{n-1} stops the loop: u^{n-1} is still in cprev
+            const int status = ld_state_int(&st->dstatus);
+            st->done = 1;
+            st->n = st->n_final = n - 1;
+            st->status = status == kStatusConverged ? DH_OK : status;
+            for (int c = 0; c < 3; ++c) st->rho[c] = __ldcg(&st->drho[c]);
+            st->cur = cprev;
+            st->pend = 0;
+            mode = 0;
+        } else if (last_in_launch) {
+            mode = 1;
+        } else {  // go on with u^{n+1}; u^n stays in cur until its decision is read
+            st->cprev = cur;
+            st->cur = 3 - cur - cprev;
+            st->n = n + 1;
+            st->pend = 1;
+            mode = 2;
+        }
+        st->arrive = 0;
+        s_mode = mode;
+    }
+    __syncthreads();
+    const int mode = s_mode;
+    if (mode != 1) return mode;
+    block_residual_sq<U>(partn, d->nblk, sq);
+    if (threadIdx.x != 0) return 1;
+    float rho[3];
+    const int status = stop_status(d, st, n, sq, phin2, rho);
+    st->pend = 0;
+    if (status) {
+        st->done = 1;
+        st->n_final = n;
+        st->status = status == kStatusConverged ? DH_OK : status;
+        for (int c = 0; c < 3; ++c) st->rho[c] = rho[c];
+        return 0;
+    }
+    st->cprev = cur;
+    st->cur = 3 - cur - cprev;
+    st->n = n + 1;
+    if (d->use_cond) cudaGraphSetConditional(d->cond, 1u);  // the launch ends, the loop goes on
+    return 1;
+}
+
+// The deferred half (every thread of the CTA that returned 2 from
+// defer_barrier, after the release): the stop rule on u^{n_done} from partn,
+// published for the next barrier in st->dstop / dstatus / drho.
+template <int U>
+static __device__ void defer_reduce(const SolveDesc *d, SolveState *st, int n_done, const float2 *partn) {
+    __shared__ float sq[3];
+    float phin2[3] = {0.f, 0.f, 0.f};
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) phin2[c] = __ldcg(&st->phin2[c]);
+    block_residual_sq<U>(partn, d->nblk, sq);
+    if (threadIdx.x == 0) {
+        float rho[3];
+        const int status = stop_status(d, st, n_done, sq, phin2, rho);
+        st->dstatus = status;
+        for (int c = 0; c < 3; ++c) st->drho[c] = rho[c];
+        st->dstop = status != 0;
+    }
 }
 
 // The loop ends unless a launch's last CTA sets the condition back to 1, so a

@@ -114,8 +114,8 @@ k_sweep(const SolveDesc *__restrict__ d) {
 template <int R, int NW, int STAGES, bool PL_SMEM, class T, bool EDGE, int MINB = 0, bool MULTI = false>
 __global__ void __launch_bounds__(NW * 32, MINB > 0 ? MINB : 16 / NW)
 k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
-            const __grid_constant__ CUtensorMap tm_phi, const __grid_constant__ CUtensorMap tm_lam,
-            const SolveDesc *__restrict__ d) {
+            const __grid_constant__ CUtensorMap tm_uc, const __grid_constant__ CUtensorMap tm_phi,
+            const __grid_constant__ CUtensorMap tm_lam, const SolveDesc *__restrict__ d) {
     constexpr int TH = R * NW;
     constexpr int HALO = Store<T>::HALO;
     using P = TmaPlan<TH, PL_SMEM, T>;
@@ -127,6 +127,9 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     __shared__ float2 red[NW];
     __shared__ int s_last, s_timeout, s_next;
     constexpr bool DYN = MULTI && STAGES == 1;  // items from a grid-wide counter
+    // deferred decisions (float32 iterates, a third buffer): see defer_barrier
+    constexpr bool DEFER = DYN && sizeof(T) == 4;
+    constexpr int UR = MINB >= 6 ? 8 : 11;  // partial loads per channel in flight in the reduction
 
     SolveState *st = d->st;
     clear_condition(d);
@@ -153,14 +156,19 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     float2 *__restrict__ part = d->part;
     const int nblk = d->nblk;
     const int iters = MULTI ? d->depth : 1;
+    const bool defer = DEFER && d->defer != 0 && d->phase_stop == 0;
     int k = 0;  // items this CTA has started in the launch (stage and parity)
     bool failed = false;
     for (int it = 0; it < iters; ++it) {
         const int cur = __ldcg(&st->cur);
         const int n_it = __ldcg(&st->n);
         const bool rev = (n_it & 1) != 0;
-        const CUtensorMap *tm_u = cur ? &tm_ub : &tm_ua;
-        T *__restrict__ ubase = static_cast<T *>(d->u[cur ^ 1]);
+        // u^n is read from buffer cur; u^{n+1} goes to the other one, or with
+        // deferred decisions to the one holding neither u^n nor u^{n-1}
+        const int wb = defer ? 3 - cur - __ldcg(&st->cprev) : cur ^ 1;
+        const CUtensorMap *tm_u = cur == 0 ? &tm_ua : (cur == 1 ? &tm_ub : &tm_uc);
+        T *__restrict__ ubase = static_cast<T *>(d->u[wb]);
+        float2 *__restrict__ partn = defer ? part + (size_t)(n_it & 1) * 3 * nblk : part;
         // position q in the iteration's walk order -> item (odd iterations walk backwards)
         auto item_of = [&](int q) { return rev ? nitems - 1 - q : q; };
         auto tile_xy = [&](int item, int &c, int &x0, int &y0) {
@@ -278,7 +286,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             const float2 tot = block_pair_sum<NW>(rs, rc, red);
             const int qnext = DYN ? s_next : q + G;
             if (threadIdx.x == 0) {
-                part[(size_t)c * nblk + tile] = tot;
+                partn[(size_t)c * nblk + tile] = tot;
                 const int qi = DYN ? qn : q + STAGES * G;  // the position whose load goes into this stage
                 if (qi < nitems) {
                     fence_proxy_async_smem();
@@ -310,11 +318,20 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
         }
         __syncthreads();
         if (s_last) {
-            const int next = finish_iteration<(MINB >= 6 ? 8 : 11)>(d, st, it == iters - 1, false, true);
-            if (threadIdx.x == 0) {
-                // the counter of the next iteration was last used two iterations ago
-                if (DYN) st->work[next & 1] = 0u;
-                st_release_gpu(&st->gen, gen + 1u);
+            if (defer) {
+                const int mode = defer_barrier<UR>(d, st, it == iters - 1, partn);
+                if (threadIdx.x == 0) {
+                    st->work[0] = st->work[1] = 0u;  // every CTA is past its last take of this iteration
+                    st_release_gpu(&st->gen, gen + 1u);
+                }
+                if (mode == 2) defer_reduce<UR>(d, st, n_it, partn);  // while the others sweep
+            } else {
+                const int next = finish_iteration<UR>(d, st, it == iters - 1, false, true);
+                if (threadIdx.x == 0) {
+                    // the counter of the next iteration was last used two iterations ago
+                    if (DYN) st->work[next & 1] = 0u;
+                    st_release_gpu(&st->gen, gen + 1u);
+                }
             }
         } else if (threadIdx.x == 0) {
             const long long t0 = clock64();
