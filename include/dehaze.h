@@ -132,7 +132,11 @@ int dh_version(void);
 
 /* Bytes of device workspace dh_dehaze / dh_fixed_point / dh_atmospheric_light
  * need for an HxW image under *p (p may be NULL for the defaults); 0 when the
- * shape or parameters are invalid. */
+ * shape or parameters are invalid.  About 44 bytes per pixel: the dark
+ * channel, lambda, Phi and two iterate buffers besides the caller's u (the
+ * multi-iteration sweep rotates u^n over three buffers so that it can start
+ * the next iteration before the stop rule on u^n is decided), plus the
+ * refinements' scratch when they are on. */
 size_t dh_workspace_bytes(int H, int W, const dh_params *p);
 
 /* Sec. II-D dark channel:

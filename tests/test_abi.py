@@ -64,7 +64,8 @@ def test_workspace_bytes():
     p = N.dh_params_default(N.DH_PRESET_STABLE)
     b = N.dh_workspace_bytes(1080, 1920, p)
     n = 1080 * 1920
-    assert b >= 4 * (8 * n) and b < 4 * (8 * n) + (1 << 22)
+    # per pixel: dark channel, lambda, Phi (3) and two float32 iterate buffers (3 each)
+    assert b >= 4 * (11 * n) and b < 4 * (11 * n) + (1 << 22)
     assert N.dh_workspace_bytes(0, 5, p) == 0
     assert N.dh_workspace_bytes(5, 40000, p) == 0
     assert N.dh_workspace_bytes(4, 4, p.replace(patch=4)) == 0
