@@ -375,7 +375,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
         T *__restrict__ un = static_cast<T *>(d->u[cur ^ 1]) + c * N;
         const int x = x0 + 4 * lane;
         const bool vec = im->tma != 0;  // aligned planes, W % 4 == 0 (W % 8 == 0 for 16-bit storage)
-        float rs = 0.f, rc = 0.f;
+        float2 facc = make_float2(0.f, 0.f);  // this lane's sum of F^2 over the item, in pairs
         auto pl = [&](int ty, float *ph, float *la) {
             const float4 p4 = *reinterpret_cast<const float4 *>(sphi + ty * kTW + 4 * lane);
             const float4 l4 = *reinterpret_cast<const float4 *>(slam + ty * kTW + 4 * lane);
@@ -386,11 +386,14 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
             const int y = y0 + ty;
             if (y >= H || x >= W) return;
             const size_t ro = (size_t)y * W;
-            float q = 0.f;
+            if (x + 3 < W) {
+                const float2 fa = make_float2(F[0], F[1]), fb = make_float2(F[2], F[3]);
+                facc = fma2(fb, fb, fma2(fa, fa, facc));
+            } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (x + j < W) q = fmaf(F[j], F[j], q);
-            neumaier_add(rs, rc, q);
+                for (int j = 0; j < 4; ++j)
+                    if (x + j < W) facc.x = fmaf(F[j], F[j], facc.x);
+            }
             if (vec) {
                 Store<T>::write4(un + ro + x, nu[0], nu[1], nu[2], nu[3]);
             } else {
@@ -406,7 +409,7 @@ k_sweep_batch(BatchHdr *__restrict__ hb) {
             if (qn % kBChunk == 0 || qn >= total) qn = cn < nch ? cn * kBChunk : total;
             s_next = qn;
         }
-        const float2 tot = block_pair_sum<kBNW>(rs, rc, red);  // every thread is past its walk
+        const float2 tot = block_pair_sum<kBNW>(facc.x + facc.y, 0.f, red);  // every thread is past its walk
         const int qnext = s_next;  // rewritten only after the next item's first barrier
         if (threadIdx.x == 0) {
             int next_img = -1;

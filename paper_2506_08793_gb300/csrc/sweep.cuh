@@ -484,7 +484,6 @@ __device__ __forceinline__ void walk_rows(const T *__restrict__ s, int r0, int l
     const int sc = 4 * lane + (Store<T>::HALO - 4);  // smem column of x-4
     const float2 W0 = make_float2(wg0, wg0), W1 = make_float2(wg1, wg1), W2 = make_float2(wg2, wg2);
     const float2 E2 = make_float2(eps, eps), HALF = make_float2(0.5f, 0.5f), TAU = make_float2(tau, tau);
-    const float2 MONE = make_float2(-1.f, -1.f);
     RowU uu[4];       // u at tile rows r0-1+k (mod 4)
     float2 gh[5][2];  // horizontal Gaussian at tile rows r0-2+k (mod 5), columns (x, x+1), (x+2, x+3)
     float2 fyu[2];    // y-face fluxes above the current row
@@ -536,14 +535,17 @@ __device__ __forceinline__ void walk_rows(const T *__restrict__ s, int r0, int l
         const float fx4 = face_flux<EDGE>(__fsub_rn(u0.o2.y, u0.o2.x), half_diff(up.o2.x, um.o2.x), eps);
         float2 fyd[2];
         yfaces(u0, up, fyd);
-        const float2 dxA = make_float2(__fsub_rn(fxA.y, fxA.x), __fsub_rn(fxB.x, fxA.y));
-        const float2 dxB = make_float2(__fsub_rn(fxB.y, fxB.x), __fsub_rn(fx4, fxB.y));
-        const float2 dvA = add2(dxA, sub2(fyd[0], fyu[0]));
-        const float2 dvB = add2(dxB, sub2(fyd[1], fyu[1]));
+        // the negated divergence -div(D grad u), by swapping the operands of
+        // every difference (exact: round-to-nearest is odd-symmetric)
+        const float2 ndxA = make_float2(__fsub_rn(fxA.x, fxA.y), __fsub_rn(fxA.y, fxB.x));
+        const float2 ndxB = make_float2(__fsub_rn(fxB.x, fxB.y), __fsub_rn(fxB.y, fx4));
+        const float2 ndvA = add2(ndxA, sub2(fyu[0], fyd[0]));
+        const float2 ndvB = add2(ndxB, sub2(fyu[1], fyd[1]));
         const float2 GA = gauss(g_m2[0], g_m1[0], g_0[0], g_p1[0], g_p2[0]);
         const float2 GB = gauss(g_m2[1], g_m1[1], g_0[1], g_p1[1], g_p2[1]);
-        const float2 FA = add2(fma2(mul2(MONE, make_float2(la[0], la[1])), GA, dvA), make_float2(ph[0], ph[1]));
-        const float2 FB = add2(fma2(mul2(MONE, make_float2(la[2], la[3])), GB, dvB), make_float2(ph[2], ph[3]));
+        // F = Phi - (lambda G - div): the same roundings as (div - lambda G) + Phi
+        const float2 FA = sub2(make_float2(ph[0], ph[1]), fma2(make_float2(la[0], la[1]), GA, ndvA));
+        const float2 FB = sub2(make_float2(ph[2], ph[3]), fma2(make_float2(la[2], la[3]), GB, ndvB));
         const float2 nA = fma2(TAU, FA, u0.e1);
         const float2 nB = fma2(TAU, FB, u0.e2);
         fyu[0] = fyd[0];

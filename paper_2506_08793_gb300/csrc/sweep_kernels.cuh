@@ -249,7 +249,9 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
 
             T *__restrict__ un = ubase + c * N;
             const int x = x0 + 4 * lane;
-            float rs = 0.f, rc = 0.f;
+            // this lane's sum of F^2 over the item, in pairs (the lanes' sums are
+            // then merged with compensation in a fixed order)
+            float2 facc = make_float2(0.f, 0.f);
             const float *__restrict__ gphi = phi_all + c * N;
             auto pl = [&](int ty, float *ph, float *la) {
                 float4 p4, l4;
@@ -270,10 +272,8 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             auto sink = [&](int ty, const float *nu, const float *F) {
                 const int y = y0 + ty;
                 if (y >= H || x >= W) return;  // W % 4 == 0: x < W covers all 4 columns
-                float q2 = 0.f;
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) q2 = fmaf(F[jj], F[jj], q2);
-                neumaier_add(rs, rc, q2);
+                const float2 fa = make_float2(F[0], F[1]), fb = make_float2(F[2], F[3]);
+                facc = fma2(fb, fb, fma2(fa, fa, facc));
                 Store<T>::write4(un + (size_t)y * W + x, nu[0], nu[1], nu[2], nu[3]);
             };
             walk_rows<R, SW, T, EDGE>(s, w * R, lane, eps, tau, wg0, wg1, wg2, pl, sink);
@@ -283,7 +283,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             // rewritten only after the next item's wait barrier, which every
             // reader of them reaches first
             if (DYN && threadIdx.x == 0) s_next = qn;
-            const float2 tot = block_pair_sum<NW>(rs, rc, red);
+            const float2 tot = block_pair_sum<NW>(facc.x + facc.y, 0.f, red);
             const int qnext = DYN ? s_next : q + G;
             if (threadIdx.x == 0) {
                 partn[(size_t)c * nblk + tile] = tot;
