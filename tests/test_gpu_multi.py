@@ -93,6 +93,25 @@ def test_max_iter_on_a_launch_boundary(api, orc):
         assert rel(u, uref) <= 1e-6, m
 
 
+def test_deferred_decisions_return_the_exact_iterate(api, orc):
+    """The multi-iteration float32 sweep decides on u^n one iteration late
+    (three iterate buffers): stopping at n must still return u^n itself.  With
+    the same split of rows over warps as the single-iteration kernel (variant
+    25: 8 rows a warp, like variant 1) the iterate, the residual history and
+    the stopping n are bit-identical, at and around launch boundaries and for
+    a residual stop in the middle of a launch."""
+    _, Phi, lam = problem(orc, 7252, 72, 136)
+    for kw in [dict(tol=0.0, max_iter=m) for m in (0, 1, 2, 62, 63, 64, 65, 126, 127, 128)] + [
+            dict(tol=1e-3, max_iter=2000), dict(tol=1e-3, max_iter=2000, use_graph=0)]:
+        ref, uref, href = run(api, Phi, lam, SINGLE, **kw)
+        rep, u, hist = run(api, Phi, lam, 25, **kw)
+        assert rep.n_iter == ref.n_iter and rep.status == ref.status, kw
+        assert np.array_equal(u, uref), kw
+        n = rep.n_iter
+        assert np.array_equal(hist[: n + 1], href[: n + 1]), kw
+        assert np.allclose(rep.rho, ref.rho, rtol=0, atol=0), kw
+
+
 def test_host_queued_launches_equal_graph_loop(api, orc):
     _, Phi, lam = problem(orc, 7303, 80, 200)
     a, ua, ha = run(api, Phi, lam, MULTI[1], tol=1e-3, max_iter=700)
