@@ -101,16 +101,20 @@ k_sweep(const SolveDesc *__restrict__ d) {
 // lambda tiles when PL_SMEM (otherwise the walk reads those with vector
 // loads); the border halo is reflected in shared memory afterwards.  Each
 // item's tiles are first pulled into L2 one item before their load is issued.
-// Odd iterations walk a CTA's items in reverse order, so that an iteration
-// starts on the tiles the previous one touched last (still in L2).
+// Odd iterations walk the items in reverse order, so that an iteration starts
+// on the tiles the previous one touched last (still in L2).
 //
 // MULTI: a cooperative launch runs up to d->depth iterations.  Between two
-// iterations the CTAs meet at a grid barrier whose last arrival reduces the
-// residual and decides (finish_iteration), then bumps st->gen; the others
-// wait for the bump (bounded, DH_ETIMEOUT).  The u^{n+1} tiles that the next
-// iteration loads by TMA were written by generic stores of other CTAs: the
-// writers fence them to the async proxy before arriving and the issuing
-// thread fences again after the barrier.
+// iterations the CTAs meet at a grid barrier (an acquire-release arrival
+// count) whose last arrival reduces the residual and decides
+// (finish_iteration), then bumps st->gen; the others wait for the bump
+// (bounded, DH_ETIMEOUT).  With one stage, a CTA's first two items are static
+// and the others come from a grid-wide counter (DYN).  With float32 iterates
+// and a third buffer the decision is deferred (defer_barrier): the last CTA
+// bumps st->gen at once and reduces while the next iteration runs.  The
+// u^{n+1} tiles that the next iteration loads by TMA were written by generic
+// stores of other CTAs: the writers fence them to the async proxy before
+// arriving and the issuing thread fences again after the barrier.
 template <int R, int NW, int STAGES, bool PL_SMEM, class T, bool EDGE, int MINB = 0, bool MULTI = false>
 __global__ void __launch_bounds__(NW * 32, MINB > 0 ? MINB : 16 / NW)
 k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ CUtensorMap tm_ub,
