@@ -161,6 +161,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
     const int nblk = d->nblk;
     const int iters = MULTI ? d->depth : 1;
     const bool defer = DEFER && d->defer != 0 && d->phase_stop == 0;
+    const bool ahead2 = nitems >= 6 * G;  // DYN: take items two ahead (see the item loop)
     int k = 0;  // items this CTA has started in the launch (stage and parity)
     bool failed = false;
     for (int it = 0; it < iters; ++it) {
@@ -200,16 +201,19 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             tma_prefetch_3d(&tm_phi, x0, y0, c);
             tma_prefetch_2d(&tm_lam, x0, y0);
         };
-        // Walk positions of this CTA: blockIdx.x, blockIdx.x + G, and then
-        // (DYN) 2G + the values of a counter the grid shares for this
-        // iteration, so that CTAs that run faster take more items and all
-        // reach the grid barrier at about the same time; otherwise
-        // blockIdx.x + jG.  Thread 0 takes the position two items ahead
-        // while the current one is walked and publishes the next one in
-        // s_next before the walk's closing barrier.
+        // Walk positions of this CTA: blockIdx.x, then (DYN) positions from a
+        // counter the grid shares for this iteration, so that CTAs that run
+        // faster take more items and all reach the grid barrier at about the
+        // same time; otherwise blockIdx.x + jG.  With many items per CTA
+        // (ahead2) the second position is blockIdx.x + G and thread 0 takes
+        // the one two items ahead (2G + counter) while the current one is
+        // walked, so the next item can be pulled into L2 first; with few, it
+        // takes only the next one (G + counter), which leaves at most one
+        // item queued per CTA when the counter runs out.  The next position
+        // is published in s_next before the walk's closing barrier.
         unsigned *ctr = &st->work[n_it & 1];
-        int q = (int)blockIdx.x;  // current position (every thread)
-        int qn = q + G;           // next position (thread 0)
+        int q = (int)blockIdx.x;           // current position (every thread)
+        int qn = ahead2 ? q + G : nitems;  // next position (thread 0)
         int j = 0;                // items of this CTA in this iteration
         if (threadIdx.x == 0) {
             if (MULTI && it > 0) fence_proxy_async_global();
@@ -226,7 +230,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             const float *slam = reinterpret_cast<const float *>(sb + P::LAM_OFF);
             if (threadIdx.x == 0) {
                 if (DYN) {
-                    if (qn < nitems) prefetch(qn);
+                    if (ahead2 && qn < nitems) prefetch(qn);
                 } else if (q + STAGES * G < nitems) {
                     prefetch(q + STAGES * G);
                 }
@@ -249,7 +253,10 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
             // (DYN, thread 0) the position after the next one, taken here so that
             // no block barrier waits for the atomic before the walk's closing one
             int qa = nitems;
-            if (DYN && threadIdx.x == 0 && qn < nitems) qa = 2 * G + (int)atomicAdd(ctr, 1u);
+            if (DYN && threadIdx.x == 0) {
+                if (!ahead2) qn = G + (int)atomicAdd(ctr, 1u);
+                else if (qn < nitems) qa = 2 * G + (int)atomicAdd(ctr, 1u);
+            }
 
             T *__restrict__ un = ubase + c * N;
             const int x = x0 + 4 * lane;
@@ -296,7 +303,7 @@ k_sweep_tma(const __grid_constant__ CUtensorMap tm_ua, const __grid_constant__ C
                     fence_proxy_async_smem();
                     issue(qi, stage);
                 }
-                if (DYN) qn = qa;
+                if (DYN && ahead2) qn = qa;
             }
             q = qnext;
         }
