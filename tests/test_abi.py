@@ -66,6 +66,11 @@ def test_workspace_bytes():
     n = 1080 * 1920
     # per pixel: dark channel, lambda, Phi (3) and two float32 iterate buffers (3 each)
     assert b >= 4 * (11 * n) and b < 4 * (11 * n) + (1 << 22)
+    # a batched solve keeps no third iterate buffer (its sweep decides at once)
+    fake = 1 << 20
+    img = N.dh_image(fake, 1080, 1920, None, fake, fake, fake, fake)
+    bb = N.dh_batch_workspace_bytes(1, [img], p)
+    assert 4 * (8 * n) <= bb < b - 4 * (3 * n) + (1 << 22)
     assert N.dh_workspace_bytes(0, 5, p) == 0
     assert N.dh_workspace_bytes(5, 40000, p) == 0
     assert N.dh_workspace_bytes(4, 4, p.replace(patch=4)) == 0
