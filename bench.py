@@ -50,7 +50,8 @@ def measured_peaks():
 
 
 SWEEP_SOURCES = ("paper_2506_08793_gb300/csrc/sweep.cuh", "paper_2506_08793_gb300/csrc/sweep_kernels.cuh",
-                 "paper_2506_08793_gb300/csrc/solver.cu", "paper_2506_08793_gb300/csrc/tma.cuh")
+                 "paper_2506_08793_gb300/csrc/solver.cu", "paper_2506_08793_gb300/csrc/tma.cuh",
+                 "paper_2506_08793_gb300/csrc/common.cuh")
 
 
 def sweep_source_hash() -> str:

@@ -2,6 +2,8 @@
 // solver state, reflection, compensated sums and error plumbing.
 #pragma once
 
+#include <cstddef>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,14 +43,6 @@ struct SolveState {
     int depth;         // sweeps per launch of the current loop (SolveDesc::depth)
     int tb2;           // temporally blocked sweep: 1 while two iterations per tile load are taken
     float rmax[kStallWindow];  // max_c rho_n of the last iterations (ring)
-    // Deferred decision of the multi-iteration float32 sweep (three iterate
-    // buffers): the iteration after n starts before the residual of u^n is
-    // reduced; u^{n-1} stays in buffer cprev until that decision is known.
-    int cprev;         // buffer holding u^{n-1} (3-buffer rotation)
-    int pend;          // 1: the decision on u^{n-1} is being reduced
-    int dstop;         // that decision: 1 = stop at n - 1
-    int dstatus;       // its status when it stops
-    float drho[3];     // its residual
     // Grid-barrier generation of the multi-iteration sweep, alone in its
     // 128-byte line so that the CTAs polling it do not contend with the
     // arrivals and state updates above.  Never reset: kernels read it first.
@@ -59,7 +53,17 @@ struct SolveState {
     // in their own line: every CTA takes its items from them.
     unsigned work[2];
     int pad_work[30];
+    // Deferred decision of the multi-iteration float32 sweep (three iterate
+    // buffers): the iteration after n starts before the residual of u^n is
+    // reduced; u^{n-1} stays in buffer cprev until that decision is known.
+    int cprev;         // buffer holding u^{n-1} (3-buffer rotation)
+    int pend;          // 1: the decision on u^{n-1} is being reduced
+    int dstop;         // that decision: 1 = stop at n - 1
+    int dstatus;       // its status when it stops
+    float drho[3];     // its residual
 };
+static_assert(offsetof(SolveState, gen) % 128 == 0 && offsetof(SolveState, work) % 128 == 0,
+              "the barrier generation and the item counters each start a 128-byte line");
 
 // status a 16-bit phase ends with when its residual stalls (internal)
 constexpr int kStatusSwitch = 100;
