@@ -738,7 +738,9 @@ static int batch_run(int n, const dh_image *imgs, const dh_params *p, void *work
         int per_sm = 0;
         DH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         DH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBNW * 32, smem));
-        // a multiple of 3 (one CTA per channel of each run of tiles)
+        // every CTA resident at once (the chunks come from a counter, so any
+        // grid size works; the multiple of 3 is kept from the earlier
+        // one-CTA-per-channel assignment and costs nothing)
         int grid = total_items < per_sm * sms ? total_items : per_sm * sms;
         grid = grid < 3 ? 3 : grid - grid % 3;
         if (p->use_graph) {
