@@ -1,5 +1,6 @@
-"""Pins of the network oracle (oracle/unet.py): the convolution against a
-brute-force loop, the hand-written backward against central differences."""
+"""Pins of the network oracle (oracle/unet.py): the convolution, pooling and
+upsampling against brute-force loops, the hand-written backward against
+central differences and as the transpose of the forward."""
 import numpy as np
 
 from oracle import unet as U
@@ -26,6 +27,28 @@ def test_conv3x3_brute_force():
                             if 0 <= ii < 5 and 0 <= jj < 6:
                                 s += np.dot(x[n, ii, jj], w[co, dy, dx])
                     assert abs(y[n, i, j, co] - s) < 1e-12
+
+
+def test_pool_and_upsample_brute_force_and_adjoints():
+    """2x2 average pooling and nearest upsampling against loops, and each
+    backward as the transpose of its forward (<f(x), g> = <x, f'(g)>)."""
+    x = rnd(4, 2, 6, 8, 3)
+    p = U.pool(x)
+    for n in range(2):
+        for i in range(3):
+            for j in range(4):
+                want = (x[n, 2 * i, 2 * j] + x[n, 2 * i + 1, 2 * j] + x[n, 2 * i, 2 * j + 1]
+                        + x[n, 2 * i + 1, 2 * j + 1]) / 4.0
+                assert np.allclose(p[n, i, j], want, rtol=0, atol=1e-15)
+    z = rnd(5, 2, 3, 4, 3)
+    u = U.up(z)
+    for i in range(6):
+        for j in range(8):
+            assert np.array_equal(u[:, i, j], z[:, i // 2, j // 2])
+    gp = rnd(6, *p.shape)
+    assert abs(np.sum(p * gp) - np.sum(x * U.pool_backward(gp, x.shape))) < 1e-12
+    gu = rnd(7, *u.shape)
+    assert abs(np.sum(u * gu) - np.sum(z * U.up_backward(gu))) < 1e-12
 
 
 def test_conv_backward_finite_differences():
