@@ -650,7 +650,7 @@ def main():
                    "images_per_step": len(imgs) * world, "l2": "inputs larger than L2 (about 0.7 GB touched per step)",
                    "parallelism": f"replicas x{world}", "per_image": per_img, "sweep_variant": tuned,
                    "images_per_s_1080p": per_img[0]["images_per_s"]},
-        "roofline": {"kernel": "k_sweep", "bound": "hbm", "achieved": achieved, "peak": peak,
+        "roofline": {"kernel": "k_sweep_tma", "bound": "hbm", "achieved": achieved, "peak": peak,
                      "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None if tr is None else tr * sweep_px_iter / sweep_launches,
                      "per": "sweep (one fixed-point iteration of one image; up to 64 per launch)",
