@@ -1,5 +1,5 @@
 // Tensor maps for the kernels outside the single-image sweep (the batched
-// sweep's 16-bit iterates, the convolutions' activations): the driver's
+// sweep's 16-bit iterates, the convolutions' activations): the CUDA driver API's
 // cuTensorMapEncodeTiled, looked up once at run time, with no interleave,
 // 256-byte L2 promotion, zero fill outside the tensor, and no swizzle unless
 // asked for.
