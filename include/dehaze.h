@@ -183,8 +183,11 @@ int dh_transmission_ws(const float *I, const float *A, int H, int W, const dh_pa
  * Boundary: half-sample symmetric reflection for both the flux stencil (zero
  * flux across the border) and the Gaussian.
  * u, Phi: 3xHxW; lam: HxW; rho_hist: device float[3*(max_iter+1)] or NULL,
- * receives rho_n for every evaluated n.  Returns DH_WNOCONV when max_iter was
- * reached (only known with a report), DH_ENONFINITE on a non-finite residual. */
+ * receives rho_n for n = 0 .. the returned n.  Returns DH_WNOCONV when max_iter
+ * was reached (only known with a report), DH_ENONFINITE on a non-finite
+ * residual.  (The float32 multi-iteration sweep decides the stop rule one
+ * update late, computing u^{n+2} into a scratch buffer it then discards; the
+ * returned u, n and rho are those of the rule above.) */
 int dh_fixed_point(float *u, const float *Phi, const float *lam, int H, int W,
                    const dh_params *p, float *rho_hist, void *workspace, size_t workspace_bytes,
                    void *stream, dh_report *report);
